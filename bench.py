@@ -1,0 +1,324 @@
+"""Benchmark: FFTPL objective-gradient evaluations per second on one GB300.
+
+Workload (default): the precision instance -- 2.2M movable cells, 2.3M nets
+(~8.15M pins), 150 macros covering 12 %, 2048 x 2048 bins -- seeded and
+synthetic (it stands in for a BIGBLUE4-sized ISPD 2005 circuit).  One step =
+one full objective-gradient evaluation: density scatter, spectral Poisson
+solve (psi, E_x, E_y), field gather, WA wirelength and its gradient, and the
+FP64 sums (N, W~, HPWL, tau, gradient norms).  Inputs are resident in HBM; L2
+is flushed (256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun each rank evaluates its own replica
+(weak scaling: no data-path collective; the problem does not shard).
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "gradient evals/s at 2M cells, 2048² bins; served jobs/s with p50/p99 latency"
+UNIT = "evals/s"
+WORKLOAD = "precision"
+
+# algorithmic bytes per launch of each stage (float32 arrays read or written
+# once; m movable cells, n bins per side, P pins, E nets)
+def stage_bytes(m, n, P, E):
+    nn = n * n
+    return {
+        "scatter": 16 * m + 8 * nn,           # x, y, w, h; zero + write D
+        "rows_fwd": 12 * nn,                  # read D, M; write T1
+        "cols": 12 * nn,                      # read T1; write PT, RT
+        "rows_inv": 20 * nn,                  # read PT, RT; write psi, E_x, E_y
+        "wa": 12 * P + 4 * E + 16 * m,        # pins, net_ptr, x, y; gradient out
+        "cells": 16 * m + 8 * nn + 16 * m,    # x, y, w, h, E_x, E_y; read gW, write gN
+    }
+
+
+STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "cells": 5}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value, ws):
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import synth
+    inst = synth.make_instance(WORKLOAD)
+    oracle.build()
+    cores = oracle.num_threads()
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.eval_instance(inst)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "precision: 2.2M cells, 2.3M nets, 150 macros, 2048x2048 bins",
+                   "sample": "one full FP64 oracle evaluation per step"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one full evaluation of the 2.2M-cell / 2048^2 instance per step"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(inst):
+    """The oracle as it stands, one evaluation of the same instance."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.eval_instance(inst)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one full FP64 evaluation of the same instance ({dt:.1f} s)"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1312_4587_gb300 import fftpl as F
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    inst = synth.make_instance(args.workload)
+    m, n, P, E = inst.m_mov, inst.n, inst.P, inst.E
+    prob = F.Problem(inst, use_graphs=0 if args.no_graphs else 1)
+    h = prob.h
+    x = torch.from_numpy(inst.x).to(dev)
+    y = torch.from_numpy(inst.y).to(dev)
+    g = [torch.empty_like(x) for _ in range(4)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        F.fftpl_eval(h, x, y, inst.gamma, *g, sync=False)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    rep = F.fftpl_report(h)
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches0 = F.fftpl_launch_count(h)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t_wall = time.perf_counter() - t_wall
+    launches = F.fftpl_launch_count(h) - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms_total = sum(step_ms)
+    ms_max = max_over_ranks(ms_total, ws)
+    clk = clocks.stop()
+
+    # per-stage times (CUDA events on each stage's own stream), same steps
+    F.fftpl_set_profiling(h, True)
+    F.fftpl_stage_times(h, reset=True)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        step()
+    torch.cuda.synchronize()
+    ms, nl = F.fftpl_stage_times(h, reset=True)
+    F.fftpl_set_profiling(h, False)
+    sb = stage_bytes(m, n, P, E)
+    hbm, bf16, peak_kind = load_peaks()
+    stages = {}
+    for name, sid in STAGE_IDS.items():
+        if nl[sid] == 0:
+            continue
+        per = ms[sid] / nl[sid]
+        gbs = sb[name] / (per * 1e-3) / 1e9
+        stages[name] = {"ms": round(per, 5), "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4),
+                        "bytes": sb[name]}
+    dom = max(stages, key=lambda k: stages[k]["ms"]) if stages else None
+
+    # end to end through the C ABI with host buffers (pinned)
+    hx = torch.from_numpy(inst.x).pin_memory()
+    hy = torch.from_numpy(inst.y).pin_memory()
+    hg = [torch.empty(m, dtype=torch.float32).pin_memory() for _ in range(4)]
+    F.fftpl_eval_host(h, hx, hy, inst.gamma, *hg)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        F.fftpl_eval_host(h, hx, hy, inst.gamma, *hg)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+
+    value = ws * args.steps / (ms_max * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{inst.name}: {m} cells, {E} nets, {P} pins, {inst.m_fix} macros, "
+                               f"{n}x{n} bins", "solve_path": "fft", "graphs": not args.no_graphs,
+                   "l2": "flushed before each timed step (256 MiB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": int(launches),
+        "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * m,
+                "d2h_bytes_per_step": 16 * m + 64},
+        "clocks": clk,
+        "stages": stages,
+        "report": {k: rep[k] for k in ("N", "W", "hpwl", "tau")},
+    }
+    if dom:
+        st = stages[dom]
+        line["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": st["GB/s"], "peak": hbm,
+                            "unit": "GB/s", "frac": st["frac"], "traffic": None,
+                            "peak_kind": peak_kind}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(inst)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    prob.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, ws, rank)
+        return run_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

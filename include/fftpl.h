@@ -1,0 +1,281 @@
+/*
+ * fftpl.h -- C ABI of the GB300 FFTPL objective-gradient library (libfftpl.so).
+ *
+ * The library evaluates, on one GPU, the per-iteration objective and gradient
+ * of the FFTPL electrostatic placement method (Lu et al., "FFTPL: An Analytic
+ * Placement Algorithm Using Fast Fourier Transform for Density Equalization"):
+ *
+ *   f(v) = W~(v) + lambda N(v)                                   (Eq. 7)
+ *
+ * with W~ the weighted-average wirelength (Eq. 3) and N the electrostatic
+ * potential energy (Eq. 6) of the bin density rho.  The potential psi and the
+ * field E solve Poisson's equation with Neumann boundary (Eq. 8) through the
+ * cosine/sine series of Eqs. 9-12.  fftpl_step runs Algorithm 1's loop with a
+ * Nesterov step in place of the conjugate-gradient solver and the parameter
+ * control of Section IV-A.
+ *
+ * Conventions (they define the results; the oracle used by the tests states
+ * the same):
+ *   - Region R = [x0, x1] x [y0, y1] split into n x n bins (Section II);
+ *     bin (j, k) is row j (y) and column k (x); all maps are float32 row-major
+ *     [n][n] with x fastest.  Bins are half-open [e_k, e_k+1) with
+ *     e_k = x0 + k (x1 - x0) / n; every edge must be exact in float32.
+ *   - Cells are given by centre (x, y) and size (w, h); the edges used are
+ *     fl32(x -/+ w/2).  Charge q_i = w_i h_i (Section III).  Fixed cells
+ *     (macros) enter rho scaled by the target density (Section III-B).
+ *   - rho_b = (rho_t F_b + D_b) / A_b with D_b, F_b the movable and fixed
+ *     overlap areas.  Coefficients a_vu = eps_u eps_v / n^2 sum rho cos cos
+ *     (bin-centre DCT-II), w_u = pi u / (x1 - x0), w_v = pi v / (y1 - y0),
+ *     the (0,0) mode dropped (DC removal, Section III-A).
+ *   - N = 1/2 sum_b A_b rho_b psi_b; the density gradient is
+ *     dN/dx_i = -sum_b ov(i,b) E_x[b] (the q.E of Eq. 7).
+ *   - Pin coordinate = fl32(cell centre + pin offset); W~ is Eq. 3 per net and
+ *     axis, summed over nets (weight 1); degree-1 nets contribute 0.
+ *   - HPWL is Eq. 1 on pin coordinates.  Overflow
+ *     tau = sum_b max(0, D_b - rho_t (A_b - F_b)) / sum_i q_i.
+ *
+ * Memory and ownership: fftpl_create deep-copies every host array it is given
+ * into device memory owned by the handle.  Position and gradient arguments of
+ * the evaluation calls are caller-owned DEVICE pointers (float32, contiguous,
+ * m_mov entries) unless the name ends in _host.  Returned map views are
+ * borrowed device pointers, valid until the next call on the handle.
+ *
+ * Streams: every call enqueues its work on the stream given to fftpl_create
+ * and, where it says so, synchronises it.  With NULL the handle creates a
+ * blocking stream of its own, which the legacy default stream orders with
+ * implicitly.  A handle is not thread-safe; use one handle per host thread.
+ *
+ * Errors: every call returns fftpl_status and never throws.  FFTPL_EINVAL
+ * comes from host-side validation before any device work is queued.  The
+ * text of the last error is fftpl_last_error(handle) (or
+ * fftpl_last_error(NULL) for a failed fftpl_create).  Kernels that wait
+ * (bounded spin-waits only) record a device error word instead of trapping;
+ * fftpl_check reads it as FFTPL_ETIMEOUT / FFTPL_ECUDA.
+ */
+#ifndef FFTPL_H
+#define FFTPL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FFTPL_VERSION 100
+#define FFTPL_MIN_N 16
+#define FFTPL_MAX_N 4096
+
+typedef struct fftpl_ctx* fftpl_t; /* opaque, library-owned */
+
+typedef enum {
+    FFTPL_OK = 0,
+    FFTPL_EINVAL = 1,      /* invalid argument (host-side validation) */
+    FFTPL_ENOMEM = 2,      /* device or host allocation failed */
+    FFTPL_ECUDA = 3,       /* CUDA runtime or kernel error */
+    FFTPL_ETIMEOUT = 4,    /* a bounded device wait gave up */
+    FFTPL_ESTATE = 5,      /* call not valid in the handle's state */
+    FFTPL_EUNSUPPORTED = 6 /* option not available in this build */
+} fftpl_status;
+
+/* Placement region R (Section II); bounding box of the placeable area. */
+typedef struct { double x0, y0, x1, y1; } fftpl_region;
+
+/* Cells (Section II: movable V_m first, then fixed V_f).  Host arrays.
+ *   w, h:          m_mov + m_fix sizes (> 0, finite)
+ *   fix_x, fix_y:  m_fix centres of the fixed cells (may be NULL if m_fix 0) */
+typedef struct {
+    int32_t m_mov, m_fix;
+    const float* w;
+    const float* h;
+    const float* fix_x;
+    const float* fix_y;
+} fftpl_cells;
+
+/* Nets as CSR over pins: net e owns pins [net_ptr[e], net_ptr[e+1]).
+ * Host array of E + 1 non-decreasing entries, net_ptr[0] = 0. */
+typedef struct {
+    int32_t E;
+    const int32_t* net_ptr;
+} fftpl_nets;
+
+/* Pins (host arrays of P entries): pin_cell in [0, m_mov + m_fix) (an index
+ * >= m_mov names fixed cell pin_cell - m_mov); dx, dy offsets from the cell
+ * centre. */
+typedef struct {
+    int64_t P;
+    const int32_t* pin_cell;
+    const float* dx;
+    const float* dy;
+} fftpl_pins;
+
+/* Spectral solve paths (Section III-E). */
+enum {
+    FFTPL_SOLVE_FFT = 0,      /* real-to-real transforms built on FP32 FFTs */
+    FFTPL_SOLVE_TC_BF16X3 = 1 /* dense DCT matrices on tcgen05 tensor cores,
+                                 operands split into bf16 hi+lo, 3 products,
+                                 FP32 accumulation */
+};
+
+typedef struct {
+    double target_density;  /* rho_t (Section III-B, Section V: 1.0) */
+    int32_t solve_path;     /* FFTPL_SOLVE_* */
+    int32_t deterministic;  /* 1: int64 fixed-point density (ov rounded to
+                               float32 then to units of 2^-32) and an
+                               atomic-free pin-to-cell reduction, so results
+                               do not depend on scheduling */
+    /* placement loop (Section IV-A constants) */
+    double lambda0;         /* <= 0: ||grad W~||_1 / ||grad N||_1 at start */
+    double gamma_fixed;     /* > 0: fixed WA gamma; <= 0: gamma(tau) schedule */
+    double dw_ref;          /* reference HPWL variation, 3.5e5 */
+    double alpha_max0_bins; /* initial step bound in bin widths, 0.044 */
+    double tau_stop;        /* stop threshold for the overflow, 0.1 */
+    int32_t stop_on_tau;    /* 1: fftpl_step stops when tau <= tau_stop */
+    int32_t use_graphs;     /* 1: replay captured CUDA graphs for repeated
+                               calls with the same buffers */
+    int32_t reserved[6];
+} fftpl_options;
+
+/* FP64 scalars of one evaluation. */
+typedef struct {
+    double N;              /* energy, 1/2 sum A_b rho_b psi_b (Eq. 6) */
+    double W;              /* weighted-average wirelength (Eq. 3) */
+    double hpwl;           /* Eq. 1 */
+    double tau;            /* density overflow */
+    double gN_l1, gW_l1;   /* ||grad N||_1, ||grad W~||_1 over movable cells */
+    double charge;         /* sum_b A_b rho_b (in-region charge incl. rho_t F) */
+    double mov_area;       /* sum_i q_i of movable cells */
+} fftpl_eval_report;
+
+/* One iteration of fftpl_step (values at the evaluated point v_k). */
+typedef struct {
+    double W, hpwl, N, tau, lambda, gamma, alpha, step_max;
+} fftpl_iter_record;
+
+/* ---------------------------------------------------------------- setup */
+
+int32_t fftpl_version(void);
+void fftpl_default_options(fftpl_options* opt);
+
+/* Creates a handle for one placement instance (Section II: G = (V, E, R),
+ * n x n bins).  n is a power of two in [FFTPL_MIN_N, FFTPL_MAX_N]; every bin
+ * edge must be exact in float32; all sizes > 0 and finite; pin_cell in range;
+ * net_ptr valid CSR.  Builds on the device: the fixed-cell map rho_t F
+ * (Section III-B), transform tables, and the pin layouts.  cuda_stream is a
+ * cudaStream_t (NULL: default stream).  On failure *out is NULL and nothing
+ * is leaked. */
+fftpl_status fftpl_create(const fftpl_region* region, int32_t n, const fftpl_cells* cells,
+                          const fftpl_nets* nets, const fftpl_pins* pins,
+                          const fftpl_options* opt, void* cuda_stream, fftpl_t* out);
+
+/* Frees every device and host resource of the handle (NULL is a no-op). */
+void fftpl_destroy(fftpl_t h);
+
+/* Text of the last error on the handle (NULL: of the last failed create on
+ * this thread).  Owned by the library. */
+const char* fftpl_last_error(fftpl_t h);
+
+/* Synchronises the handle's stream and reads the device error word. */
+fftpl_status fftpl_check(fftpl_t h);
+
+/* Device memory the handle holds, in bytes. */
+size_t fftpl_device_bytes(fftpl_t h);
+
+/* ----------------------------------------------------- evaluation calls */
+
+/* Density energy and gradient (Section III; Algorithm 1 "compute density",
+ * "FFTsolver" and the density part of the gradient): scatter, spectral
+ * solve, gather.  x, y: device positions (m_mov).  gx, gy: device outputs
+ * dN/dx, dN/dy (m_mov), may be NULL.  N: host output; if non-NULL the call
+ * synchronises, otherwise it stays asynchronous (read with fftpl_report). */
+fftpl_status fftpl_density(fftpl_t h, const float* x, const float* y, double* N,
+                           float* gx, float* gy);
+
+/* As fftpl_density, but the gradient is the exact derivative of the binned
+ * energy (edge difference of psi: d ov(i,b)/dx is +1 at the bin holding the
+ * right edge and -1 at the bin holding the left edge, times the row overlap)
+ * instead of the paper's q.E gather. */
+fftpl_status fftpl_density_adjoint(fftpl_t h, const float* x, const float* y, double* N,
+                                   float* gx, float* gy);
+
+/* Weighted-average wirelength (Eq. 3) and its gradient; HPWL (Eq. 1) as a
+ * by-product.  gx, gy device outputs (m_mov), may be NULL.  W host output:
+ * non-NULL synchronises. */
+fftpl_status fftpl_wa(fftpl_t h, const float* x, const float* y, float gamma, double* W,
+                      float* gx, float* gy);
+
+/* One full objective-gradient evaluation: density energy and gradient, WA
+ * wirelength and gradient (the two run concurrently on the device), and the
+ * FP64 sums of fftpl_eval_report.  Outputs are device arrays (any may be
+ * NULL).  rep: host; non-NULL synchronises. */
+fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma,
+                        float* gNx, float* gNy, float* gWx, float* gWy,
+                        fftpl_eval_report* rep);
+
+/* fftpl_eval on HOST buffers: copies x, y to the device, evaluates, copies
+ * the four gradients back and synchronises.  Pinned host memory is fastest. */
+fftpl_status fftpl_eval_host(fftpl_t h, const float* x_host, const float* y_host, float gamma,
+                             float* gNx_host, float* gNy_host, float* gWx_host,
+                             float* gWy_host, fftpl_eval_report* rep);
+
+/* Synchronises and returns the scalars of the last evaluation call. */
+fftpl_status fftpl_report(fftpl_t h, fftpl_eval_report* rep);
+
+/* Borrowed device views of the maps of the last density evaluation: bin
+ * density rho, potential psi (Eq. 11), field E_x, E_y (Eq. 12).  Any pointer
+ * may be NULL.  rho is formed on demand. */
+fftpl_status fftpl_fields(fftpl_t h, const float** rho, const float** psi,
+                          const float** ex, const float** ey);
+
+/* Movable-cell area map of the last density call in deterministic mode, in
+ * int64 units of 2^-32 (borrowed device view); FFTPL_ESTATE otherwise. */
+fftpl_status fftpl_fields_q(fftpl_t h, const int64_t** movable_area_q);
+
+/* Bin bookkeeping: for each movable cell the clamped bin range
+ * (ilo, ihi, jlo, jhi) into ranges (device, 4 m_mov int32; empty: ilo > ihi)
+ * and the total number of (cell, bin) pairs into *pairs (host; syncs). */
+fftpl_status fftpl_bin_ranges(fftpl_t h, const float* x, const float* y, int32_t* ranges,
+                              int64_t* pairs);
+
+/* ------------------------------------------------------ placement loop */
+
+/* Starts a placement run at (x0, y0) (device, m_mov): u = v = clamp(x0),
+ * Nesterov a = 1, lambda, gamma and alpha_max from the options. */
+fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0);
+
+/* Runs up to iters iterations of the loop (Algorithm 1 with the Nesterov
+ * step; Section IV-A control).  recs: host array of iters records (may be
+ * NULL).  *ran: iterations done (host).  Synchronises at the end only. */
+fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32_t* ran);
+
+/* Copies the current major iterate u to device arrays x, y (m_mov). */
+fftpl_status fftpl_place_positions(fftpl_t h, float* x, float* y);
+
+/* Serialises the loop state (positions, Nesterov state, lambda, gamma,
+ * alpha_max, k) to host memory.  With buf NULL, *bytes receives the size. */
+fftpl_status fftpl_state_save(fftpl_t h, void* buf, size_t* bytes);
+fftpl_status fftpl_state_load(fftpl_t h, const void* buf, size_t bytes);
+
+/* --------------------------------------------------------- measurement */
+
+/* Stage timing with CUDA events on the stream each stage runs on.  Stages:
+ * 0 scatter, 1 forward rows, 2 spectral columns, 3 inverse rows, 4 WA,
+ * 5 cells (gather + pin sums), 6 step.  Times accumulate (ms) until reset. */
+#define FFTPL_NUM_STAGES 8
+fftpl_status fftpl_set_profiling(fftpl_t h, int32_t on);
+fftpl_status fftpl_stage_times(fftpl_t h, double* ms, int64_t* launches, int32_t reset);
+
+/* Number of kernels this handle has launched (all stages). */
+int64_t fftpl_launch_count(fftpl_t h);
+
+/* ------------------------------------------------------- test hooks */
+
+/* Host-side fault injection: the k-th device allocation from now fails with
+ * FFTPL_ENOMEM (k <= 0 disables). */
+void fftpl_debug_fail_alloc_after(int32_t k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTPL_H */

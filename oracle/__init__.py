@@ -178,6 +178,18 @@ def potential_field(a, Lx, Ly):
     return psi, ex, ey
 
 
+def potential_at(a, Lx, Ly, xs, ys):
+    """psi, E_x, E_y (Eqs. 11-12) at bins (ys[k], xs[k]) from coefficients a."""
+    a = _f64(a)
+    n = a.shape[0]
+    xs = _i32(xs); ys = _i32(ys)
+    k = xs.shape[0]
+    psi = np.zeros(k); ex = np.zeros(k); ey = np.zeros(k)
+    lib().orc_potential_at(C.c_int(n), C.c_double(Lx), C.c_double(Ly), _ptr(a), C.c_int(k),
+                           _ptr(xs), _ptr(ys), _ptr(psi), _ptr(ex), _ptr(ey))
+    return psi, ex, ey
+
+
 def solve(rho, Lx, Ly):
     """rho -> (a, psi, E_x, E_y) by the explicit cosine sums of Eqs. 9-12."""
     a = dct_coeffs(rho)

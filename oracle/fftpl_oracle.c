@@ -324,6 +324,40 @@ void orc_potential_field(int n, double Lx, double Ly, const double* a,
     free(hat); free(Ct); free(St); free(pc); free(ps); free(pcT); free(psT);
 }
 
+/* Eqs. 11 and 12 at chosen bin centres only: for each k < count the sums
+ * over all (u, v) at bin (ys[k], xs[k]).  Same definition as
+ * orc_potential_field, O(n^2) per point, for spot checks of large grids. */
+void orc_potential_at(int n, double Lx, double Ly, const double* a, int count,
+                      const int32_t* xs, const int32_t* ys, double* psi, double* ex, double* ey) {
+#pragma omp parallel
+    {
+        double* cu = (double*)malloc((size_t)n * sizeof(double));
+        double* su = (double*)malloc((size_t)n * sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+        for (int k = 0; k < count; ++k) {
+            int x = xs[k], y = ys[k];
+            for (int u = 0; u < n; ++u) { cu[u] = cos_b(u, x, n); su[u] = sin_b(u, x, n); }
+            double s_psi = 0.0, s_ex = 0.0, s_ey = 0.0;
+            for (int v = 0; v < n; ++v) {
+                double cv = cos_b(v, y, n), sv = sin_b(v, y, n), wv = M_PI * v / Ly;
+                for (int u = 0; u < n; ++u) {
+                    if (u == 0 && v == 0) continue;
+                    double wu = M_PI * u / Lx;
+                    double hat = a[(size_t)v * n + u] / (wu * wu + wv * wv);
+                    s_psi += hat * cu[u] * cv;
+                    s_ex += hat * wu * su[u] * cv;
+                    s_ey += hat * wv * cu[u] * sv;
+                }
+            }
+            psi[k] = s_psi;
+            ex[k] = s_ex;
+            ey[k] = s_ey;
+        }
+        free(cu);
+        free(su);
+    }
+}
+
 /* Potential energy, Eq. 6 over all charges (movable and fixed) with the factor
  * 1/2:  N = 1/2 sum_b A_b rho_b psi_b. */
 double orc_energy(int n, double Ab, const double* rho, const double* psi) {

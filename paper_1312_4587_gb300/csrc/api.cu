@@ -1,0 +1,859 @@
+// C ABI of libfftpl (include/fftpl.h): validation, resource management and
+// the orchestration of one objective-gradient evaluation.
+//
+// One evaluation (Algorithm 1: f, density, FFT solve, gradient) runs as
+//   main stream: zero sums, zero D, scatter -> rows_fwd -> cols -> rows_inv
+//   side stream: (zero gW) -> WA                       (forked, concurrent)
+//   main stream: join -> cells (gather + pin sums + norms)
+// and, when use_graphs is set, is replayed from a captured CUDA graph.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "fftpl_internal.cuh"
+#include "loop_ctrl.cuh"
+
+using namespace fftpl;
+
+namespace {
+
+thread_local std::string g_create_error;
+std::atomic<int> g_fail_after{0};
+
+struct Fail {
+    fftpl_status st;
+};
+
+#define CK(call)                                                                    \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            c.last_error = std::string(#call) + ": " + cudaGetErrorString(e_);      \
+            return (e_ == cudaErrorMemoryAllocation) ? FFTPL_ENOMEM : FFTPL_ECUDA;  \
+        }                                                                           \
+    } while (0)
+
+fftpl_status set_err(Ctx& c, fftpl_status st, const std::string& msg) {
+    c.last_error = msg;
+    return st;
+}
+
+template <typename T>
+fftpl_status dalloc(Ctx& c, T** p, size_t count) {
+    *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    int k = g_fail_after.load();
+    if (k > 0) {
+        if (g_fail_after.fetch_sub(1) == 1) {
+            return set_err(c, FFTPL_ENOMEM, "injected allocation failure");
+        }
+    }
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_err(c, FFTPL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c.dev_allocs.push_back((void*)*p);
+    c.dev_bytes += bytes;
+    return FFTPL_OK;
+}
+
+#define TRY(x)                              \
+    do {                                    \
+        fftpl_status s_ = (x);              \
+        if (s_ != FFTPL_OK) return s_;      \
+    } while (0)
+
+bool finite_pos(float v) { return isfinite(v) && v > 0.0f; }
+
+void free_ctx(fftpl_ctx* c) {
+    if (!c) return;
+    if (c->stream || c->side) cudaDeviceSynchronize();
+    if (c->eval_graph) cudaGraphExecDestroy(c->eval_graph);
+    for (void* p : c->dev_allocs) cudaFree(p);
+    if (c->acc_host) cudaFreeHost(c->acc_host);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+// ---------------------------------------------------------------- validation
+fftpl_status validate(Ctx& c, const fftpl_region* R, int n, const fftpl_cells* cells,
+                      const fftpl_nets* nets, const fftpl_pins* pins, const fftpl_options* opt) {
+    if (!R || !cells || !nets || !pins) return set_err(c, FFTPL_EINVAL, "null argument");
+    if (n < FFTPL_MIN_N || n > FFTPL_MAX_N || (n & (n - 1)) != 0)
+        return set_err(c, FFTPL_EINVAL, "n must be a power of two in [16, 4096]");
+    if (!(isfinite(R->x0) && isfinite(R->y0) && isfinite(R->x1) && isfinite(R->y1)) ||
+        !(R->x1 > R->x0) || !(R->y1 > R->y0))
+        return set_err(c, FFTPL_EINVAL, "region must be finite with x1 > x0 and y1 > y0");
+    // every bin edge must be exact in float32, computed as x0 + k * wb
+    double lo[2] = {R->x0, R->y0}, hi[2] = {R->x1, R->y1};
+    for (int a = 0; a < 2; ++a) {
+        double step = (hi[a] - lo[a]) / n;
+        float lof = (float)lo[a], stf = (float)step;
+        if ((double)lof != lo[a] || (double)stf != step)
+            return set_err(c, FFTPL_EINVAL, "region corner and bin size must be exact in float32");
+        for (int k = 0; k <= n; ++k) {
+            volatile float e = lof + (float)k * stf;
+            if ((double)e != lo[a] + k * step)
+                return set_err(c, FFTPL_EINVAL, "bin edges must be exact in float32");
+        }
+        if ((double)(float)hi[a] != hi[a])
+            return set_err(c, FFTPL_EINVAL, "region corner must be exact in float32");
+    }
+    if (cells->m_mov < 0 || cells->m_fix < 0) return set_err(c, FFTPL_EINVAL, "negative cell count");
+    long long mt = (long long)cells->m_mov + cells->m_fix;
+    if (mt > 0 && (!cells->w || !cells->h)) return set_err(c, FFTPL_EINVAL, "null cell sizes");
+    if (cells->m_fix > 0 && (!cells->fix_x || !cells->fix_y))
+        return set_err(c, FFTPL_EINVAL, "null fixed-cell positions");
+    for (long long i = 0; i < mt; ++i)
+        if (!finite_pos(cells->w[i]) || !finite_pos(cells->h[i]))
+            return set_err(c, FFTPL_EINVAL, "cell sizes must be finite and > 0");
+    for (int i = 0; i < cells->m_fix; ++i)
+        if (!isfinite(cells->fix_x[i]) || !isfinite(cells->fix_y[i]))
+            return set_err(c, FFTPL_EINVAL, "fixed-cell positions must be finite");
+    if (nets->E < 0) return set_err(c, FFTPL_EINVAL, "negative net count");
+    if (pins->P < 0 || pins->P > 0x7fffffffLL) return set_err(c, FFTPL_EINVAL, "bad pin count");
+    if (!nets->net_ptr) return set_err(c, FFTPL_EINVAL, "null net_ptr");
+    if (nets->net_ptr[0] != 0 || (long long)nets->net_ptr[nets->E] != pins->P)
+        return set_err(c, FFTPL_EINVAL, "net_ptr must start at 0 and end at P");
+    for (int e = 0; e < nets->E; ++e)
+        if (nets->net_ptr[e + 1] < nets->net_ptr[e])
+            return set_err(c, FFTPL_EINVAL, "net_ptr must be non-decreasing");
+    if (pins->P > 0 && (!pins->pin_cell || !pins->dx || !pins->dy))
+        return set_err(c, FFTPL_EINVAL, "null pin arrays");
+    for (long long p = 0; p < pins->P; ++p) {
+        if (pins->pin_cell[p] < 0 || pins->pin_cell[p] >= mt)
+            return set_err(c, FFTPL_EINVAL, "pin_cell out of range");
+        if (!isfinite(pins->dx[p]) || !isfinite(pins->dy[p]))
+            return set_err(c, FFTPL_EINVAL, "pin offsets must be finite");
+    }
+    if (opt) {
+        if (!(opt->target_density > 0.0) || !isfinite(opt->target_density))
+            return set_err(c, FFTPL_EINVAL, "target_density must be > 0");
+        if (opt->solve_path != FFTPL_SOLVE_FFT && opt->solve_path != FFTPL_SOLVE_TC_BF16X3)
+            return set_err(c, FFTPL_EINVAL, "unknown solve_path");
+        if (opt->solve_path == FFTPL_SOLVE_TC_BF16X3)
+            return set_err(c, FFTPL_EUNSUPPORTED, "tensor-core solve path not built");
+        if (!(opt->dw_ref > 0.0)) return set_err(c, FFTPL_EINVAL, "dw_ref must be > 0");
+    }
+    return FFTPL_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+void prof_begin(Ctx& c, int stage, cudaStream_t s, int* slot) {
+    *slot = -1;
+    if (!c.profiling) return;
+    if (c.prof_used + 2 > (int)c.prof_ev.size()) {
+        // ring full: fold the recorded pairs into the totals
+        cudaDeviceSynchronize();
+        for (int i = 0; i + 1 < c.prof_used; i += 2) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, c.prof_ev[i], c.prof_ev[i + 1]) == cudaSuccess)
+                c.stage_ms[c.prof_stage[i / 2]] += ms;
+        }
+        c.prof_used = 0;
+    }
+    *slot = c.prof_used;
+    c.prof_stage[c.prof_used / 2] = stage;
+    c.stage_launches[stage]++;
+    cudaEventRecord(c.prof_ev[c.prof_used], s);
+    c.prof_used += 2;
+}
+
+void prof_end(Ctx& c, int slot, cudaStream_t s) {
+    if (slot < 0) return;
+    cudaEventRecord(c.prof_ev[slot + 1], s);
+}
+
+struct Stage {
+    Ctx& c;
+    cudaStream_t s;
+    int slot;
+    Stage(Ctx& c_, int id, cudaStream_t s_) : c(c_), s(s_) { prof_begin(c, id, s, &slot); }
+    ~Stage() { prof_end(c, slot, s); }
+};
+
+// ---------------------------------------------------------------- evaluation
+enum { EV_DENSITY = 1, EV_WA = 2, EV_ADJOINT = 4 };
+
+// Enqueues one evaluation; gradients must be non-null device arrays.
+fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, int what,
+                          float* gNx, float* gNy, float* gWx, float* gWy) {
+    cudaStream_t s = c.stream;
+    size_t nn = (size_t)c.n * c.n;
+    CK(cudaMemsetAsync(c.acc, 0, ACC_COUNT * sizeof(double), s));
+    bool dens = (what & EV_DENSITY) != 0, wa = (what & EV_WA) != 0;
+    if (wa) {
+        CK(cudaEventRecord(c.ev_fork, s));
+        CK(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+        Stage st(c, 4, c.side);
+        if (!c.opt.deterministic) {
+            CK(cudaMemsetAsync(gWx, 0, (size_t)c.m_mov * sizeof(float), c.side));
+            CK(cudaMemsetAsync(gWy, 0, (size_t)c.m_mov * sizeof(float), c.side));
+        }
+        CK(launch_wa(c, x, y, gamma, gWx, gWy, c.side));
+    }
+    if (wa) CK(cudaEventRecord(c.ev_join, c.side));
+    if (dens) {
+        {
+            Stage st(c, 0, s);
+            if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
+            else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
+            CK(launch_scatter(c, x, y, c.w, c.h, c.m_mov, c.D, c.Dq, s));
+        }
+        { Stage st(c, 1, s); CK(launch_rows_fwd(c, s)); }
+        { Stage st(c, 2, s); CK(launch_cols_spectral(c, s)); }
+        { Stage st(c, 3, s); CK(launch_rows_inv(c, s)); }
+    }
+    if (wa) CK(cudaStreamWaitEvent(s, c.ev_join, 0));
+    {
+        Stage st(c, 5, s);
+        if (dens && wa && !(what & EV_ADJOINT)) {
+            CK(launch_cells(c, x, y, gNx, gNy, gWx, gWy, s));
+        } else {
+            if (dens) CK(launch_gather(c, x, y, gNx, gNy, (what & EV_ADJOINT) != 0, s));
+            if (wa) CK(launch_pin_sum(c, gWx, gWy, s));
+        }
+    }
+    c.rho_valid = false;
+    c.fields_valid = dens;
+    return FFTPL_OK;
+}
+
+void fill_report(const Ctx& c, const double* acc, fftpl_eval_report* rep) {
+    rep->N = 0.5 * c.Ab * acc[ACC_N];
+    rep->W = acc[ACC_W];
+    rep->hpwl = acc[ACC_HPWL];
+    rep->tau = c.mov_area > 0 ? acc[ACC_TAU] / c.mov_area : 0.0;
+    rep->gN_l1 = acc[ACC_GN_L1];
+    rep->gW_l1 = acc[ACC_GW_L1];
+    rep->charge = acc[ACC_CHARGE];
+    rep->mov_area = c.mov_area;
+}
+
+fftpl_status read_report(Ctx& c, fftpl_eval_report* rep) {
+    CK(cudaMemcpyAsync(c.acc_host, c.acc, ACC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                       c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    if (rep) fill_report(c, c.acc_host, rep);
+    return FFTPL_OK;
+}
+
+// internal gradient scratch for NULL outputs
+float* scratch(Ctx& c, int which) { return (which < 2 ? c.gN : c.gW) + (which & 1) * c.m_mov; }
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+int32_t fftpl_version(void) { return FFTPL_VERSION; }
+
+void fftpl_default_options(fftpl_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->target_density = 1.0;
+    o->solve_path = FFTPL_SOLVE_FFT;
+    o->deterministic = 0;
+    o->lambda0 = 0.0;
+    o->gamma_fixed = 0.0;
+    o->dw_ref = 3.5e5;
+    o->alpha_max0_bins = 0.044;
+    o->tau_stop = 0.1;
+    o->stop_on_tau = 0;
+    o->use_graphs = 0;
+}
+
+void fftpl_debug_fail_alloc_after(int32_t k) { g_fail_after.store(k > 0 ? k : 0); }
+
+const char* fftpl_last_error(fftpl_t h) {
+    if (!h) return g_create_error.c_str();
+    return h->last_error.c_str();
+}
+
+static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const fftpl_cells* cells,
+                                const fftpl_nets* nets, const fftpl_pins* pins,
+                                const fftpl_options* opt, void* stream) {
+    TRY(validate(c, R, n, cells, nets, pins, opt));
+    if (opt) c.opt = *opt;
+    else fftpl_default_options(&c.opt);
+    c.n = n;
+    c.logn = 0;
+    while ((1 << c.logn) < n) c.logn++;
+    c.m_mov = cells->m_mov;
+    c.m_fix = cells->m_fix;
+    c.E = nets->E;
+    c.P = pins->P;
+    c.x0 = R->x0; c.y0 = R->y0; c.x1 = R->x1; c.y1 = R->y1;
+    c.Lx = R->x1 - R->x0;
+    c.Ly = R->y1 - R->y0;
+    c.wb = c.Lx / n;
+    c.hb = c.Ly / n;
+    c.Ab = c.wb * c.hb;
+    c.grid.n = n;
+    c.grid.x0 = (float)c.x0;
+    c.grid.y0 = (float)c.y0;
+    c.grid.wb = (float)c.wb;
+    c.grid.hb = (float)c.hb;
+    c.grid.inv_wb = (float)(1.0 / c.wb);
+    c.grid.inv_hb = (float)(1.0 / c.hb);
+    c.mov_area = 0.0;
+    for (int i = 0; i < c.m_mov; ++i) c.mov_area += (double)cells->w[i] * (double)cells->h[i];
+    for (int e = 0; e < c.E; ++e)
+        c.wa_max_degree = std::max(c.wa_max_degree, nets->net_ptr[e + 1] - nets->net_ptr[e]);
+
+    c.stream = (cudaStream_t)stream;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (!c.stream) {
+        // a blocking stream of our own: ordered with the legacy default
+        // stream (implicit synchronisation) yet capturable into graphs
+        CK(cudaStreamCreate(&c.own_stream));
+        c.stream = c.own_stream;
+    }
+    CK(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+    CK(cudaMallocHost((void**)&c.acc_host, ACC_COUNT * sizeof(double)));
+
+    size_t nn = (size_t)n * n;
+    int mt = c.m_mov + c.m_fix;
+    TRY(dalloc(c, &c.w, mt));
+    TRY(dalloc(c, &c.h, mt));
+    TRY(dalloc(c, &c.fix_x, c.m_fix));
+    TRY(dalloc(c, &c.fix_y, c.m_fix));
+    TRY(dalloc(c, &c.M, nn));
+    if (c.opt.deterministic) TRY(dalloc(c, &c.Dq, nn));
+    else TRY(dalloc(c, &c.D, nn));
+    TRY(dalloc(c, &c.T1, nn));
+    TRY(dalloc(c, &c.PT, nn));
+    TRY(dalloc(c, &c.RT, nn));
+    TRY(dalloc(c, &c.psi, nn));
+    TRY(dalloc(c, &c.ex, nn));
+    TRY(dalloc(c, &c.ey, nn));
+    TRY(dalloc(c, &c.tw, n));
+    TRY(dalloc(c, &c.ph, n + 1));
+    TRY(dalloc(c, &c.net_ptr, (size_t)c.E + 1));
+    TRY(dalloc(c, &c.pin_cell, c.P));
+    TRY(dalloc(c, &c.pin_dx, c.P));
+    TRY(dalloc(c, &c.pin_dy, c.P));
+    TRY(dalloc(c, &c.acc, ACC_COUNT));
+    TRY(dalloc(c, &c.err, 1));
+    TRY(dalloc(c, &c.gN, 2 * (size_t)c.m_mov));
+    TRY(dalloc(c, &c.gW, 2 * (size_t)c.m_mov));
+    if (c.opt.deterministic) {
+        TRY(dalloc(c, &c.pin_slot, c.P));
+        TRY(dalloc(c, &c.cell_pin_ptr, (size_t)c.m_mov + 1));
+        TRY(dalloc(c, &c.gpin, c.P));
+    }
+    cudaStream_t s = c.stream;
+    CK(cudaMemcpyAsync(c.w, cells->w, mt * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.h, cells->h, mt * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (c.m_fix) {
+        CK(cudaMemcpyAsync(c.fix_x, cells->fix_x, c.m_fix * sizeof(float), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c.fix_y, cells->fix_y, c.m_fix * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemcpyAsync(c.net_ptr, nets->net_ptr, ((size_t)c.E + 1) * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, s));
+    if (c.P) {
+        CK(cudaMemcpyAsync(c.pin_cell, pins->pin_cell, c.P * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c.pin_dx, pins->dx, c.P * sizeof(float), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c.pin_dy, pins->dy, c.P * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    // transform tables (FP64 on the host, rounded once): FFT twiddles
+    // exp(-2 pi i k / n) and cosine-transform twiddles exp(-i pi u / 2n)
+    std::vector<float2> tw(n), ph(n + 1);
+    for (int k = 0; k < n; ++k) {
+        double a = 2.0 * M_PI * k / n;
+        tw[k] = make_float2((float)cos(a), (float)-sin(a));
+    }
+    for (int u = 0; u <= n; ++u) {
+        double a = M_PI * u / (2.0 * n);
+        ph[u] = make_float2((float)cos(a), (float)-sin(a));
+    }
+    CK(cudaMemcpyAsync(c.tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.ph, ph.data(), (n + 1) * sizeof(float2), cudaMemcpyHostToDevice, s));
+    // deterministic pin-to-cell layout: pins of each movable cell made
+    // contiguous (in net order); pin_slot maps a pin to its slot
+    if (c.opt.deterministic) {
+        std::vector<int32_t> cnt((size_t)c.m_mov + 1, 0), slot(c.P);
+        for (long long p = 0; p < c.P; ++p)
+            if (pins->pin_cell[p] < c.m_mov) cnt[pins->pin_cell[p] + 1]++;
+        for (int i = 0; i < c.m_mov; ++i) cnt[i + 1] += cnt[i];
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (long long p = 0; p < c.P; ++p) {
+            int cc = pins->pin_cell[p];
+            slot[p] = cc < c.m_mov ? fill[cc]++ : -1;
+        }
+        CK(cudaMemcpyAsync(c.cell_pin_ptr, cnt.data(), cnt.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+        if (c.P)
+            CK(cudaMemcpyAsync(c.pin_slot, slot.data(), c.P * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // host vectors go out of scope
+    }
+    // fixed-cell map M = rho_t F (Section III-B), order-free int64 sums
+    {
+        long long* q = nullptr;
+        CK(cudaMalloc((void**)&q, nn * sizeof(long long)));
+        cudaError_t e = cudaMemsetAsync(q, 0, nn * sizeof(long long), s);
+        if (e == cudaSuccess && c.m_fix > 0)
+            e = launch_scatter(c, c.fix_x, c.fix_y, c.w + c.m_mov, c.h + c.m_mov, c.m_fix, nullptr, q, s);
+        if (e == cudaSuccess) e = launch_q_to_f(q, (float)c.opt.target_density, c.M, (int)nn, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(q);
+        if (e == cudaSuccess) e = e2;
+        CK(e);
+    }
+    CK(cudaMemsetAsync(c.err, 0, sizeof(int), s));
+    prepare_spectral(c.logn);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_create(const fftpl_region* region, int32_t n, const fftpl_cells* cells,
+                          const fftpl_nets* nets, const fftpl_pins* pins, const fftpl_options* opt,
+                          void* cuda_stream, fftpl_t* out) {
+    if (!out) {
+        g_create_error = "null output handle";
+        return FFTPL_EINVAL;
+    }
+    *out = nullptr;
+    fftpl_ctx* c = new (std::nothrow) fftpl_ctx();
+    if (!c) {
+        g_create_error = "host allocation failed";
+        return FFTPL_ENOMEM;
+    }
+    fftpl_status st = create_impl(*c, region, n, cells, nets, pins, opt, cuda_stream);
+    if (st != FFTPL_OK) {
+        g_create_error = c->last_error;
+        free_ctx(c);
+        return st;
+    }
+    g_create_error.clear();
+    *out = c;
+    return FFTPL_OK;
+}
+
+void fftpl_destroy(fftpl_t h) { free_ctx(h); }
+
+size_t fftpl_device_bytes(fftpl_t h) { return h ? h->dev_bytes : 0; }
+
+fftpl_status fftpl_check(fftpl_t h) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    CK(cudaStreamSynchronize(c.stream));
+    CK(cudaStreamSynchronize(c.side));
+    int err = 0;
+    CK(cudaMemcpy(&err, c.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & ERR_TIMEOUT) return set_err(c, FFTPL_ETIMEOUT, "a device wait timed out");
+    if (err) return set_err(c, FFTPL_ECUDA, "device error word set");
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_density(fftpl_t h, const float* x, const float* y, double* N, float* gx,
+                           float* gy) {
+    if (!h || (h->m_mov > 0 && (!x || !y))) return h ? set_err(*h, FFTPL_EINVAL, "null positions") : FFTPL_EINVAL;
+    Ctx& c = *h;
+    TRY(enqueue_eval(c, x, y, 0.0f, EV_DENSITY, gx ? gx : scratch(c, 0), gy ? gy : scratch(c, 1),
+                     nullptr, nullptr));
+    if (N) {
+        fftpl_eval_report r;
+        TRY(read_report(c, &r));
+        *N = r.N;
+    }
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_density_adjoint(fftpl_t h, const float* x, const float* y, double* N,
+                                   float* gx, float* gy) {
+    if (!h || (h->m_mov > 0 && (!x || !y))) return h ? set_err(*h, FFTPL_EINVAL, "null positions") : FFTPL_EINVAL;
+    Ctx& c = *h;
+    TRY(enqueue_eval(c, x, y, 0.0f, EV_DENSITY | EV_ADJOINT, gx ? gx : scratch(c, 0),
+                     gy ? gy : scratch(c, 1), nullptr, nullptr));
+    if (N) {
+        fftpl_eval_report r;
+        TRY(read_report(c, &r));
+        *N = r.N;
+    }
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_wa(fftpl_t h, const float* x, const float* y, float gamma, double* W,
+                      float* gx, float* gy) {
+    if (!h || (h->m_mov > 0 && (!x || !y))) return h ? set_err(*h, FFTPL_EINVAL, "null positions") : FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (!(gamma > 0.0f) || !isfinite(gamma)) return set_err(c, FFTPL_EINVAL, "gamma must be > 0");
+    TRY(enqueue_eval(c, x, y, gamma, EV_WA, nullptr, nullptr, gx ? gx : scratch(c, 2),
+                     gy ? gy : scratch(c, 3)));
+    if (W) {
+        fftpl_eval_report r;
+        TRY(read_report(c, &r));
+        *W = r.W;
+    }
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma, float* gNx,
+                        float* gNy, float* gWx, float* gWy, fftpl_eval_report* rep) {
+    if (!h || (h->m_mov > 0 && (!x || !y))) return h ? set_err(*h, FFTPL_EINVAL, "null positions") : FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (!(gamma > 0.0f) || !isfinite(gamma)) return set_err(c, FFTPL_EINVAL, "gamma must be > 0");
+    gNx = gNx ? gNx : scratch(c, 0);
+    gNy = gNy ? gNy : scratch(c, 1);
+    gWx = gWx ? gWx : scratch(c, 2);
+    gWy = gWy ? gWy : scratch(c, 3);
+    if (c.opt.use_graphs && !c.profiling) {
+        float gk = gamma;
+        const void* key[7] = {x, y, gNx, gNy, gWx, gWy, nullptr};
+        memcpy(&key[6], &gk, sizeof(float));
+        if (!c.eval_graph || memcmp(key, c.graph_key, sizeof(key)) != 0) {
+            if (c.eval_graph) {
+                cudaGraphExecDestroy(c.eval_graph);
+                c.eval_graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+            int64_t before = c.launches;
+            fftpl_status st = enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy);
+            cudaError_t ee = cudaStreamEndCapture(c.stream, &g);
+            if (st != FFTPL_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            CK(ee);
+            cudaError_t ie = cudaGraphInstantiate(&c.eval_graph, g, 0);
+            cudaGraphDestroy(g);
+            CK(ie);
+            memcpy(c.graph_key, key, sizeof(key));
+            c.graph_nkernels = c.launches - before;
+            c.launches = before;  // counted at replay
+        }
+        CK(cudaGraphLaunch(c.eval_graph, c.stream));
+        c.launches += c.graph_nkernels;
+        c.fields_valid = true;
+        c.rho_valid = false;
+    } else {
+        TRY(enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy));
+    }
+    if (rep) TRY(read_report(c, rep));
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_eval_host(fftpl_t h, const float* x_host, const float* y_host, float gamma,
+                             float* gNx_host, float* gNy_host, float* gWx_host, float* gWy_host,
+                             fftpl_eval_report* rep) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (c.m_mov > 0 && (!x_host || !y_host)) return set_err(c, FFTPL_EINVAL, "null positions");
+    size_t m = (size_t)c.m_mov;
+    if (!c.hx) {
+        TRY(dalloc(c, &c.hx, 2 * m));
+        TRY(dalloc(c, &c.hg, 4 * m));
+        c.hy = c.hx + m;
+    }
+    cudaStream_t s = c.stream;
+    CK(cudaMemcpyAsync(c.hx, x_host, m * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.hy, y_host, m * sizeof(float), cudaMemcpyHostToDevice, s));
+    TRY(fftpl_eval(h, c.hx, c.hy, gamma, c.hg, c.hg + m, c.hg + 2 * m, c.hg + 3 * m, nullptr));
+    float* outs[4] = {gNx_host, gNy_host, gWx_host, gWy_host};
+    for (int k = 0; k < 4; ++k)
+        if (outs[k])
+            CK(cudaMemcpyAsync(outs[k], c.hg + k * m, m * sizeof(float), cudaMemcpyDeviceToHost, s));
+    return read_report(c, rep);
+}
+
+fftpl_status fftpl_report(fftpl_t h, fftpl_eval_report* rep) {
+    if (!h || !rep) return FFTPL_EINVAL;
+    return read_report(*h, rep);
+}
+
+fftpl_status fftpl_fields(fftpl_t h, const float** rho, const float** psi, const float** ex,
+                          const float** ey) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (!c.fields_valid) return set_err(c, FFTPL_ESTATE, "no density evaluation yet");
+    if (rho) {
+        if (!c.rho) TRY(dalloc(c, &c.rho, (size_t)c.n * c.n));
+        if (!c.rho_valid) {
+            CK(launch_rho(c, c.stream));
+            c.rho_valid = true;
+        }
+        *rho = c.rho;
+    }
+    if (psi) *psi = c.psi;
+    if (ex) *ex = c.ex;
+    if (ey) *ey = c.ey;
+    CK(cudaStreamSynchronize(c.stream));
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_fields_q(fftpl_t h, const int64_t** q) {
+    if (!h || !q) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (!c.opt.deterministic || !c.fields_valid)
+        return set_err(c, FFTPL_ESTATE, "no deterministic density evaluation yet");
+    CK(cudaStreamSynchronize(c.stream));
+    *q = reinterpret_cast<const int64_t*>(c.Dq);
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_bin_ranges(fftpl_t h, const float* x, const float* y, int32_t* ranges,
+                              int64_t* pairs) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (c.m_mov > 0 && (!x || !y || !ranges)) return set_err(c, FFTPL_EINVAL, "null argument");
+    CK(cudaMemsetAsync(c.acc, 0, ACC_COUNT * sizeof(double), c.stream));
+    CK(launch_bin_ranges(c, x, y, ranges, c.acc + ACC_CHARGE, c.stream));
+    CK(cudaMemcpyAsync(c.acc_host, c.acc, ACC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                       c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    if (pairs) *pairs = (int64_t)llround(c.acc_host[ACC_CHARGE]);
+    return FFTPL_OK;
+}
+
+// ------------------------------------------------------------ placement loop
+fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (c.m_mov > 0 && (!x0 || !y0)) return set_err(c, FFTPL_EINVAL, "null positions");
+    size_t m2 = 2 * (size_t)c.m_mov;
+    if (!c.u) {
+        TRY(dalloc(c, &c.u, m2));
+        TRY(dalloc(c, &c.v, m2));
+        TRY(dalloc(c, &c.vprev, m2));
+        TRY(dalloc(c, &c.g, m2));
+        TRY(dalloc(c, &c.gprev, m2));
+        TRY(dalloc(c, &c.ctrl, C_COUNT + kCounters));
+    }
+    std::vector<double> ctrl(C_COUNT + kCounters, 0.0);
+    ctrl[C_LAMBDA] = c.opt.lambda0;
+    ctrl[C_GAMMA] = c.opt.gamma_fixed;
+    ctrl[C_ALPHA_MAX0] = c.opt.alpha_max0_bins * c.wb;
+    ctrl[C_ALPHA_MAX] = ctrl[C_ALPHA_MAX0];
+    ctrl[C_A] = 1.0;
+    ctrl[C_DW_REF] = c.opt.dw_ref;
+    ctrl[C_GAMMA_FIXED] = c.opt.gamma_fixed;
+    ctrl[C_LAMBDA0_OPT] = c.opt.lambda0;
+    ctrl[C_STOP_ON_TAU] = c.opt.stop_on_tau ? 1.0 : 0.0;
+    ctrl[C_TAU_STOP] = c.opt.tau_stop;
+    ctrl[C_WB] = c.wb;
+    ctrl[C_HALF_AB] = 0.5 * c.Ab;
+    ctrl[C_MOV_AREA] = c.mov_area > 0 ? c.mov_area : 1.0;
+    cudaStream_t s = c.stream;
+    CK(cudaMemcpyAsync(c.ctrl, ctrl.data(), ctrl.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(launch_place_init(c, x0, y0, s));
+    if (c.opt.gamma_fixed <= 0.0) {
+        // gamma_0 from the overflow at the start
+        size_t nn = (size_t)c.n * c.n;
+        CK(cudaMemsetAsync(c.acc, 0, ACC_COUNT * sizeof(double), s));
+        if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
+        else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
+        CK(launch_scatter(c, c.v, c.v + c.m_mov, c.w, c.h, c.m_mov, c.D, c.Dq, s));
+        CK(launch_rows_fwd(c, s));
+        CK(launch_gamma0(c, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    c.placing = true;
+    return FFTPL_OK;
+}
+
+static fftpl_status enqueue_iteration(Ctx& c) {
+    cudaStream_t s = c.stream;
+    size_t nn = (size_t)c.n * c.n;
+    const float* vx = c.v;
+    const float* vy = c.v + c.m_mov;
+    float* gWx = c.gW;
+    float* gWy = c.gW + c.m_mov;
+    CK(cudaMemsetAsync(c.acc, 0, ACC_COUNT * sizeof(double), s));
+    CK(cudaEventRecord(c.ev_fork, s));
+    CK(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+    {
+        Stage st(c, 4, c.side);
+        if (!c.opt.deterministic)
+            CK(cudaMemsetAsync(c.gW, 0, 2 * (size_t)c.m_mov * sizeof(float), c.side));
+        CK(launch_wa_impl(c, vx, vy, 1.0f, c.ctrl + C_GAMMA, gWx, gWy, c.ctrl + C_DONE, c.side));
+    }
+    CK(cudaEventRecord(c.ev_join, c.side));
+    {
+        Stage st(c, 0, s);
+        if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
+        else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
+        CK(launch_scatter(c, vx, vy, c.w, c.h, c.m_mov, c.D, c.Dq, s));
+    }
+    { Stage st(c, 1, s); CK(launch_rows_fwd(c, s)); }
+    { Stage st(c, 2, s); CK(launch_cols_spectral(c, s)); }
+    { Stage st(c, 3, s); CK(launch_rows_inv(c, s)); }
+    CK(cudaStreamWaitEvent(s, c.ev_join, 0));
+    { Stage st(c, 5, s); CK(launch_loop_cells(c, s)); }
+    {
+        Stage st(c, 6, s);
+        CK(launch_loop_g(c, s));
+        CK(launch_loop_update(c, s));
+    }
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32_t* ran) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (!c.placing) return set_err(c, FFTPL_ESTATE, "call fftpl_place_init first");
+    if (iters < 0) return set_err(c, FFTPL_EINVAL, "iters must be >= 0");
+    if (c.recs_cap < std::max(iters, 1)) {
+        if (c.recs) {
+            cudaFree(c.recs);
+            c.dev_allocs.erase(std::find(c.dev_allocs.begin(), c.dev_allocs.end(), (void*)c.recs));
+            c.recs = nullptr;
+        }
+        TRY(dalloc(c, &c.recs, (size_t)std::max(iters, 1) * kRecFields));
+        c.recs_cap = std::max(iters, 1);
+    }
+    double k0 = 0.0;
+    CK(cudaMemcpyAsync(&k0, c.ctrl + C_K, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    double hdr[2] = {(double)iters, k0};
+    CK(cudaMemcpyAsync(c.ctrl + C_REC_CAP, hdr, sizeof(hdr), cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    for (int it = 0; it < iters; ++it) TRY(enqueue_iteration(c));
+    double k1 = 0.0;
+    CK(cudaMemcpyAsync(&k1, c.ctrl + C_K, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    int done = (int)(k1 - k0);
+    if (ran) *ran = done;
+    if (recs && done > 0) {
+        std::vector<double> tmp((size_t)done * kRecFields);
+        CK(cudaMemcpy(tmp.data(), c.recs, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < done; ++k) {
+            const double* r = tmp.data() + (size_t)k * kRecFields;
+            recs[k].W = r[0]; recs[k].hpwl = r[1]; recs[k].N = r[2]; recs[k].tau = r[3];
+            recs[k].lambda = r[4]; recs[k].gamma = r[5]; recs[k].alpha = r[6];
+            recs[k].step_max = r[7];
+        }
+    }
+    c.fields_valid = true;
+    c.rho_valid = false;
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_place_positions(fftpl_t h, float* x, float* y) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (!c.placing) return set_err(c, FFTPL_ESTATE, "no placement run");
+    size_t m = (size_t)c.m_mov;
+    CK(cudaMemcpyAsync(x, c.u, m * sizeof(float), cudaMemcpyDeviceToDevice, c.stream));
+    CK(cudaMemcpyAsync(y, c.u + m, m * sizeof(float), cudaMemcpyDeviceToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return FFTPL_OK;
+}
+
+// state layout: magic, m, then u, v, vprev, g, gprev (2m float each), ctrl
+static const uint64_t kStateMagic = 0x4646545053544154ULL;  // "FFTPSTAT"
+
+fftpl_status fftpl_state_save(fftpl_t h, void* buf, size_t* bytes) {
+    if (!h || !bytes) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (!c.placing) return set_err(c, FFTPL_ESTATE, "no placement run");
+    size_t m2 = 2 * (size_t)c.m_mov;
+    size_t need = 2 * sizeof(uint64_t) + 5 * m2 * sizeof(float) + C_COUNT * sizeof(double);
+    if (!buf) {
+        *bytes = need;
+        return FFTPL_OK;
+    }
+    if (*bytes < need) return set_err(c, FFTPL_EINVAL, "state buffer too small");
+    char* p = (char*)buf;
+    uint64_t hdr[2] = {kStateMagic, (uint64_t)c.m_mov};
+    memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    CK(cudaStreamSynchronize(c.stream));
+    float* vecs[5] = {c.u, c.v, c.vprev, c.g, c.gprev};
+    for (float* v : vecs) {
+        CK(cudaMemcpy(p, v, m2 * sizeof(float), cudaMemcpyDeviceToHost));
+        p += m2 * sizeof(float);
+    }
+    CK(cudaMemcpy(p, c.ctrl, C_COUNT * sizeof(double), cudaMemcpyDeviceToHost));
+    *bytes = need;
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_state_load(fftpl_t h, const void* buf, size_t bytes) {
+    if (!h || !buf) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    size_t m2 = 2 * (size_t)c.m_mov;
+    size_t need = 2 * sizeof(uint64_t) + 5 * m2 * sizeof(float) + C_COUNT * sizeof(double);
+    if (bytes < need) return set_err(c, FFTPL_EINVAL, "state buffer too small");
+    const char* p = (const char*)buf;
+    uint64_t hdr[2];
+    memcpy(hdr, p, sizeof(hdr));
+    if (hdr[0] != kStateMagic || hdr[1] != (uint64_t)c.m_mov)
+        return set_err(c, FFTPL_EINVAL, "state does not match this instance");
+    p += sizeof(hdr);
+    if (!c.u) {
+        TRY(dalloc(c, &c.u, m2));
+        TRY(dalloc(c, &c.v, m2));
+        TRY(dalloc(c, &c.vprev, m2));
+        TRY(dalloc(c, &c.g, m2));
+        TRY(dalloc(c, &c.gprev, m2));
+        TRY(dalloc(c, &c.ctrl, C_COUNT + kCounters));
+    }
+    CK(cudaStreamSynchronize(c.stream));
+    float* vecs[5] = {c.u, c.v, c.vprev, c.g, c.gprev};
+    for (float* v : vecs) {
+        CK(cudaMemcpy(v, p, m2 * sizeof(float), cudaMemcpyHostToDevice));
+        p += m2 * sizeof(float);
+    }
+    CK(cudaMemcpy(c.ctrl, p, C_COUNT * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemset(c.ctrl + C_COUNT, 0, kCounters * sizeof(double)));
+    c.placing = true;
+    return FFTPL_OK;
+}
+
+// ------------------------------------------------------------ measurement
+fftpl_status fftpl_set_profiling(fftpl_t h, int32_t on) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (on && c.prof_ev.empty()) {
+        const int pairs = 4096;
+        c.prof_ev.resize(2 * pairs);
+        c.prof_stage.resize(pairs);
+        for (auto& e : c.prof_ev) CK(cudaEventCreate(&e));
+    }
+    c.profiling = on != 0;
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_stage_times(fftpl_t h, double* ms, int64_t* launches, int32_t reset) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    CK(cudaStreamSynchronize(c.stream));
+    CK(cudaStreamSynchronize(c.side));
+    for (int i = 0; i + 1 < c.prof_used; i += 2) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, c.prof_ev[i], c.prof_ev[i + 1]));
+        c.stage_ms[c.prof_stage[i / 2]] += t;
+    }
+    c.prof_used = 0;
+    for (int k = 0; k < FFTPL_NUM_STAGES; ++k) {
+        if (ms) ms[k] = c.stage_ms[k];
+        if (launches) launches[k] = c.stage_launches[k];
+        if (reset) {
+            c.stage_ms[k] = 0.0;
+            c.stage_launches[k] = 0;
+        }
+    }
+    return FFTPL_OK;
+}
+
+int64_t fftpl_launch_count(fftpl_t h) { return h ? h->launches : 0; }
+
+}  // extern "C"

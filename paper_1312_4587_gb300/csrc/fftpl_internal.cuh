@@ -1,0 +1,267 @@
+// Internal declarations shared by the libfftpl translation units.
+//
+// Layout in device memory (all float32 unless noted, row-major [n][n] maps
+// with x fastest):
+//   movable cells   w, h                       (m_mov)
+//   fixed cells     fix_x, fix_y (m_fix)       macro map M = rho_t F  [n][n]
+//   density         D (movable overlap area, float) or Dq (int64, 2^-32 units)
+//   spectral        T1 [u][y]  (rows transformed along x, stored transposed)
+//                   PT [y][u], RT [y][u]  (columns transformed and inverted)
+//                   psi, ex, ey [y][x], rho [y][x] (formed on demand)
+//   nets/pins       net_ptr (E+1), pin_cell, pin_dx, pin_dy (P, net order)
+//                   pin_slot (P), cell_pin_ptr (m_mov+1), gpin (P float2) for
+//                   the deterministic pin-to-cell reduction
+//   accumulators    acc[ACC_*] doubles, err word
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fftpl.h"
+
+namespace fftpl {
+
+// ------------------------------------------------------------------ sizes
+constexpr int kSpecThreads = 256;   // threads of the transform kernels
+constexpr int kSpecBuffers = 4;     // complex length-n buffers per CTA
+constexpr int kCellThreads = 256;
+constexpr int kWaThreads = 256;
+constexpr int kWaPinCap = 2048;     // pins staged in shared memory per WA CTA
+
+// accumulator slots (FP64 sums written by the kernels)
+enum {
+    ACC_N = 0,      // sum B * Psi (times A_b/2 on the host)
+    ACC_W,          // WA wirelength
+    ACC_HPWL,
+    ACC_TAU,        // overflow numerator
+    ACC_GN_L1,
+    ACC_GW_L1,
+    ACC_CHARGE,     // sum (D + M) (times A_b... area units already)
+    ACC_DV2,        // ||v_k - v_{k-1}||^2
+    ACC_DG2,        // ||g_k - g_{k-1}||^2
+    ACC_GINF,       // ||g_k||_inf (as ordered bits of a non-negative double)
+    ACC_STEPMAX,    // max |u_{k+1} - v_k|
+    ACC_COUNT
+};
+
+// device error word bits
+enum { ERR_TIMEOUT = 1, ERR_BOUNDS = 2 };
+
+// Bin grid along both axes.  Edges e_k = x0 + k * wb are exact in float32
+// (checked at create), so comparisons against them decide indices exactly.
+struct Grid {
+    int n;
+    float x0, y0, wb, hb, inv_wb, inv_hb;
+};
+
+__device__ __forceinline__ float edge_at(float lo, float step, int k) {
+    return __fadd_rn(lo, __fmul_rn((float)k, step));
+}
+
+// Largest k in [-1, n] with e_k <= t (strict: e_k < t).  The float estimate
+// is corrected against the exact edges, so rounding never decides an index.
+template <bool STRICT>
+__device__ __forceinline__ int last_edge(float lo, float step, float inv, int n, float t) {
+    float kf = floorf(__fmul_rn(__fsub_rn(t, lo), inv));
+    int k;
+    if (!(kf >= -1.0f)) k = -1;          // also catches NaN
+    else if (kf > (float)n) k = n;
+    else k = (int)kf;
+#pragma unroll 1
+    for (int it = 0; it < 3 && k >= 0; ++it) {
+        float e = edge_at(lo, step, k);
+        bool ok = STRICT ? (e < t) : (e <= t);
+        if (ok) break;
+        --k;
+    }
+#pragma unroll 1
+    for (int it = 0; it < 3 && k < n; ++it) {
+        float e = edge_at(lo, step, k + 1);
+        bool ok = STRICT ? (e < t) : (e <= t);
+        if (!ok) break;
+        ++k;
+    }
+    return k;
+}
+
+struct Span {
+    float xl, xh, yl, yh;   // float32 cell edges
+    int ilo, ihi, jlo, jhi; // clamped bin span (empty if ilo > ihi or jlo > jhi)
+};
+
+__device__ __forceinline__ Span cell_span(const Grid& g, float x, float y, float w, float h) {
+    Span s;
+    float hw = __fmul_rn(0.5f, w), hh = __fmul_rn(0.5f, h);
+    s.xl = __fsub_rn(x, hw);
+    s.xh = __fadd_rn(x, hw);
+    s.yl = __fsub_rn(y, hh);
+    s.yh = __fadd_rn(y, hh);
+    s.ilo = max(last_edge<false>(g.x0, g.wb, g.inv_wb, g.n, s.xl), 0);
+    s.ihi = min(last_edge<true>(g.x0, g.wb, g.inv_wb, g.n, s.xh), g.n - 1);
+    s.jlo = max(last_edge<false>(g.y0, g.hb, g.inv_hb, g.n, s.yl), 0);
+    s.jhi = min(last_edge<true>(g.y0, g.hb, g.inv_hb, g.n, s.yh), g.n - 1);
+    return s;
+}
+
+// Overlap length of [a, b) with bin k (float32 arithmetic, no contraction).
+__device__ __forceinline__ float ov_len(float lo, float step, int k, float a, float b) {
+    float e0 = edge_at(lo, step, k), e1 = edge_at(lo, step, k + 1);
+    float v = __fsub_rn(fminf(b, e1), fmaxf(a, e0));
+    return fmaxf(v, 0.0f);
+}
+
+// --------------------------------------------------- double-float sums
+// An unevaluated sum hi + lo of two floats (error-free transformations:
+// Knuth's TwoSum and Dekker's Fast2Sum).  Used to keep the grid-wide FP64
+// reductions accurate without FP64 arithmetic in the inner loops.
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_zero() { return {0.0f, 0.0f}; }
+
+__device__ __forceinline__ dfloat df_add(dfloat a, float b) {
+    float s = __fadd_rn(a.hi, b);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    float lo = __fadd_rn(a.lo, e);
+    float hi = __fadd_rn(s, lo);
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    dfloat r = df_add(a, b.hi);
+    return df_add(r, b.lo);
+}
+
+// Warp-reduces a dfloat and adds it to *dst with one FP64 atomic per warp.
+__device__ __forceinline__ void df_warp_atomic(dfloat v, double* dst) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dfloat w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    if ((threadIdx.x & 31) == 0 && (v.hi != 0.0f || v.lo != 0.0f))
+        atomicAdd(dst, (double)v.hi + (double)v.lo);
+}
+
+// Max of non-negative doubles through their ordered bit patterns.
+__device__ __forceinline__ void atomic_max_nonneg(double* dst, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(dst),
+              (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ------------------------------------------------------------ complex
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// -------------------------------------------------------- the context
+struct Ctx {
+    // problem
+    int n = 0, logn = 0, m_mov = 0, m_fix = 0, E = 0;
+    int64_t P = 0;
+    double x0 = 0, y0 = 0, x1 = 0, y1 = 0, Lx = 0, Ly = 0, wb = 0, hb = 0, Ab = 0;
+    double mov_area = 0;
+    Grid grid{};
+    fftpl_options opt{};
+    int wa_max_degree = 0;
+
+    // streams and events
+    cudaStream_t stream = nullptr, side = nullptr, own_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool profiling = false;
+    double stage_ms[FFTPL_NUM_STAGES] = {};
+    int64_t stage_launches[FFTPL_NUM_STAGES] = {};
+    int64_t launches = 0;
+
+    // device buffers
+    float *w = nullptr, *h = nullptr, *fix_x = nullptr, *fix_y = nullptr;
+    float *M = nullptr, *D = nullptr;
+    long long* Dq = nullptr;
+    float *T1 = nullptr, *PT = nullptr, *RT = nullptr;
+    float *psi = nullptr, *ex = nullptr, *ey = nullptr, *rho = nullptr;
+    float2 *tw = nullptr, *ph = nullptr;
+    int32_t *net_ptr = nullptr, *pin_cell = nullptr, *pin_slot = nullptr, *cell_pin_ptr = nullptr;
+    float *pin_dx = nullptr, *pin_dy = nullptr;
+    float2* gpin = nullptr;
+    double* acc = nullptr;
+    int* err = nullptr;
+    double* acc_host = nullptr;   // pinned mirror
+
+    // placement loop state (2 m_mov each: x then y)
+    float *u = nullptr, *v = nullptr, *vprev = nullptr, *g = nullptr, *gprev = nullptr;
+    float *gN = nullptr, *gW = nullptr;   // 2 m_mov each, loop scratch
+    double* ctrl = nullptr;              // device control scalars
+    double* recs = nullptr;              // device iteration records
+    int recs_cap = 0;
+    bool placing = false;
+    int iter = 0;
+
+    // host-side staging for fftpl_eval_host
+    float *hx = nullptr, *hy = nullptr, *hg = nullptr;  // device staging (2m, 4m)
+
+    // captured CUDA graph of fftpl_eval for one set of buffers
+    cudaGraphExec_t eval_graph = nullptr;
+    const void* graph_key[7] = {};
+    int64_t graph_nkernels = 0;
+    // profiling ring of (stage, begin, end) event records
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_stage;
+    int prof_used = 0;
+
+    bool rho_valid = false, fields_valid = false;
+    std::string last_error;
+    std::vector<void*> dev_allocs;
+    size_t dev_bytes = 0;
+};
+
+// ------------------------------------------------------------ launchers
+// (each returns the CUDA error of the launch)
+void prepare_spectral(int logn);
+cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* w,
+                           const float* h, int m, float* D, long long* Dq, cudaStream_t s);
+cudaError_t launch_bin_ranges(Ctx& c, const float* x, const float* y, int32_t* ranges,
+                              double* pairs, cudaStream_t s);
+cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s);
+cudaError_t launch_cols_spectral(Ctx& c, cudaStream_t s);
+cudaError_t launch_rows_inv(Ctx& c, cudaStream_t s);
+cudaError_t launch_rho(Ctx& c, cudaStream_t s);
+cudaError_t launch_q_to_f(const long long* q, float scale, float* out, int count, cudaStream_t s);
+cudaError_t launch_gather(Ctx& c, const float* x, const float* y, float* gx, float* gy,
+                          bool adjoint, cudaStream_t s);
+cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, float* gx,
+                      float* gy, cudaStream_t s);
+cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
+                           const double* gamma_dev, float* gx, float* gy, const double* done,
+                           cudaStream_t s);
+cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s);
+cudaError_t launch_cells(Ctx& c, const float* x, const float* y, float* gNx, float* gNy,
+                         float* gWx, float* gWy, cudaStream_t s);
+// placement loop
+cudaError_t launch_loop_cells(Ctx& c, cudaStream_t s);
+cudaError_t launch_loop_g(Ctx& c, cudaStream_t s);
+cudaError_t launch_loop_update(Ctx& c, cudaStream_t s);
+cudaError_t launch_place_init(Ctx& c, const float* x0, const float* y0, cudaStream_t s);
+cudaError_t launch_gamma0(Ctx& c, cudaStream_t s);
+
+}  // namespace fftpl
+
+// The opaque handle of the C ABI is the context.
+struct fftpl_ctx : public fftpl::Ctx {};

@@ -1,0 +1,190 @@
+// Density scatter, field gather and bookkeeping kernels.
+//
+// Scatter (Section II bin density, Section III charges q_i = A_i): every cell
+// adds its exact rectangle-bin overlap areas to the movable area map D; the
+// transform pass later forms rho = (D + rho_t F) / A_b.  Gather (the q.E of
+// Eq. 7): dN/dx_i = -sum_b ov(i,b) E_x[b], the exact transpose of the
+// scatter weights.  Adjoint: the exact derivative of the binned energy,
+// sum over rows of the row overlap times (psi at the right-edge bin - psi at
+// the left-edge bin), and likewise in y.
+#include "fftpl_internal.cuh"
+
+namespace fftpl {
+
+// One thread per cell.  FP32 mode: red.global.add.f32 of ov into D.
+// Deterministic mode: ov is formed in float32 (x and y lengths, then their
+// product), scaled by 2^32 (exact) and rounded to the nearest integer (ties to
+// even); int64 atomics make the bin sums independent of order.
+template <bool QUANT>
+__global__ void __launch_bounds__(kCellThreads)
+k_scatter(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
+          const float* __restrict__ w, const float* __restrict__ h, float* __restrict__ D,
+          unsigned long long* __restrict__ Dq) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    Span s = cell_span(g, x[i], y[i], w[i], h[i]);
+    for (int j = s.jlo; j <= s.jhi; ++j) {
+        float oy = ov_len(g.y0, g.hb, j, s.yl, s.yh);
+        for (int k = s.ilo; k <= s.ihi; ++k) {
+            float ox = ov_len(g.x0, g.wb, k, s.xl, s.xh);
+            float a = __fmul_rn(ox, oy);
+            size_t b = (size_t)j * g.n + k;
+            if (QUANT) {
+                long long q = __float2ll_rn(__fmul_rn(a, 4294967296.0f));
+                atomicAdd(Dq + b, (unsigned long long)q);
+            } else {
+                atomicAdd(D + b, a);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kCellThreads)
+k_bin_ranges(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
+             const float* __restrict__ w, const float* __restrict__ h, int4* __restrict__ out,
+             double* __restrict__ pairs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float cnt = 0.0f;
+    if (i < m) {
+        Span s = cell_span(g, x[i], y[i], w[i], h[i]);
+        bool empty = s.ilo > s.ihi || s.jlo > s.jhi;
+        if (empty) {
+            out[i] = make_int4(0, -1, 0, -1);
+        } else {
+            out[i] = make_int4(s.ilo, s.ihi, s.jlo, s.jhi);
+            cnt = (float)((s.ihi - s.ilo + 1) * (s.jhi - s.jlo + 1));
+        }
+    }
+    dfloat d = {cnt, 0.0f};
+    df_warp_atomic(d, pairs);
+}
+
+// Field gather (ADJ = false) or exact edge-difference adjoint (ADJ = true,
+// field = psi in fx).  Writes gx, gy and adds ||g||_1 to *l1.
+template <bool ADJ>
+__global__ void __launch_bounds__(kCellThreads)
+k_gather(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
+         const float* __restrict__ w, const float* __restrict__ h, const float* __restrict__ fx,
+         const float* __restrict__ fy, float* __restrict__ gx, float* __restrict__ gy,
+         double* __restrict__ l1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float sx = 0.0f, sy = 0.0f;
+    if (i < m) {
+        Span s = cell_span(g, x[i], y[i], w[i], h[i]);
+        if (!ADJ) {
+            for (int j = s.jlo; j <= s.jhi; ++j) {
+                float oy = ov_len(g.y0, g.hb, j, s.yl, s.yh);
+                const float* rx = fx + (size_t)j * g.n;
+                const float* ry = fy + (size_t)j * g.n;
+                for (int k = s.ilo; k <= s.ihi; ++k) {
+                    float o = __fmul_rn(ov_len(g.x0, g.wb, k, s.xl, s.xh), oy);
+                    sx = fmaf(o, __ldg(rx + k), sx);
+                    sy = fmaf(o, __ldg(ry + k), sy);
+                }
+            }
+            sx = -sx;
+            sy = -sy;
+        } else if (s.ilo <= s.ihi && s.jlo <= s.jhi) {
+            int n = g.n;
+            int kl = last_edge<false>(g.x0, g.wb, g.inv_wb, n, s.xl);
+            int kr = last_edge<false>(g.x0, g.wb, g.inv_wb, n, s.xh);
+            int jl = last_edge<false>(g.y0, g.hb, g.inv_hb, n, s.yl);
+            int jr = last_edge<false>(g.y0, g.hb, g.inv_hb, n, s.yh);
+            bool kr_in = kr >= 0 && kr < n, kl_in = kl >= 0 && kl < n;
+            bool jr_in = jr >= 0 && jr < n, jl_in = jl >= 0 && jl < n;
+            for (int j = s.jlo; j <= s.jhi; ++j) {
+                float oy = ov_len(g.y0, g.hb, j, s.yl, s.yh);
+                const float* r = fx + (size_t)j * n;
+                float d = (kr_in ? __ldg(r + kr) : 0.0f) - (kl_in ? __ldg(r + kl) : 0.0f);
+                sx = fmaf(oy, d, sx);
+            }
+            const float* rt = fx + (size_t)(jr_in ? jr : 0) * n;
+            const float* rb = fx + (size_t)(jl_in ? jl : 0) * n;
+            for (int k = s.ilo; k <= s.ihi; ++k) {
+                float ox = ov_len(g.x0, g.wb, k, s.xl, s.xh);
+                float d = (jr_in ? __ldg(rt + k) : 0.0f) - (jl_in ? __ldg(rb + k) : 0.0f);
+                sy = fmaf(ox, d, sy);
+            }
+        }
+        gx[i] = sx;
+        gy[i] = sy;
+    }
+    if (l1) {
+        dfloat d = {fabsf(sx) + fabsf(sy), 0.0f};
+        d = df_add(df_zero(), d);
+        df_warp_atomic(d, l1);
+    }
+}
+
+// rho = (D + M) / A_b (formed on demand for fftpl_fields).
+template <bool QUANT>
+__global__ void k_rho(int count, const float* __restrict__ D, const long long* __restrict__ Dq,
+                      const float* __restrict__ M, float inv_ab, float* __restrict__ rho) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float d = QUANT ? (float)Dq[i] * 2.3283064365386963e-10f : D[i];
+    rho[i] = (d + M[i]) * inv_ab;
+}
+
+__global__ void k_q_to_f(const long long* __restrict__ q, float scale, float* __restrict__ out,
+                         int count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = (float)q[i] * 2.3283064365386963e-10f * scale;
+}
+
+static inline int blocks_for(long long m, int t) { return (int)((m + t - 1) / t); }
+
+cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* w, const float* h,
+                           int m, float* D, long long* Dq, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    int nb = blocks_for(m, kCellThreads);
+    if (Dq)
+        k_scatter<true><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, nullptr,
+                                                   reinterpret_cast<unsigned long long*>(Dq));
+    else
+        k_scatter<false><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, D, nullptr);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_ranges(Ctx& c, const float* x, const float* y, int32_t* ranges,
+                              double* pairs, cudaStream_t s) {
+    if (c.m_mov <= 0) return cudaSuccess;
+    k_bin_ranges<<<blocks_for(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
+        c.grid, c.m_mov, x, y, c.w, c.h, reinterpret_cast<int4*>(ranges), pairs);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(Ctx& c, const float* x, const float* y, float* gx, float* gy,
+                          bool adjoint, cudaStream_t s) {
+    if (c.m_mov <= 0) return cudaSuccess;
+    int nb = blocks_for(c.m_mov, kCellThreads);
+    if (adjoint)
+        k_gather<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.psi, c.psi,
+                                                  gx, gy, c.acc + ACC_GN_L1);
+    else
+        k_gather<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.ex, c.ey,
+                                                   gx, gy, c.acc + ACC_GN_L1);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho(Ctx& c, cudaStream_t s) {
+    int count = c.n * c.n;
+    float inv_ab = (float)(1.0 / c.Ab);
+    if (c.opt.deterministic)
+        k_rho<true><<<blocks_for(count, 256), 256, 0, s>>>(count, nullptr, c.Dq, c.M, inv_ab, c.rho);
+    else
+        k_rho<false><<<blocks_for(count, 256), 256, 0, s>>>(count, c.D, nullptr, c.M, inv_ab, c.rho);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_q_to_f(const long long* q, float scale, float* out, int count,
+                          cudaStream_t st) {
+    k_q_to_f<<<blocks_for(count, 256), 256, 0, st>>>(q, scale, out, count);
+    return cudaGetLastError();
+}
+
+}  // namespace fftpl

@@ -1,0 +1,468 @@
+// Spectral solution of Poisson's equation (Section III-E, Eqs. 8-12) on FP32
+// fast Fourier transforms.
+//
+// With C(u,x) = cos(pi u (2x+1) / 2n) and S(u,x) = sin(...):
+//   a[v][u] = eps_u eps_v / n^2  sum_y sum_x rho[y][x] C(u,x) C(v,y)   (Eq. 10)
+//   Psi = a / (w_u^2 + w_v^2), Psi_00 = 0
+//   psi[y][x] = sum_u C(u,x) P[u][y],        P[u][y] = sum_v Psi[v][u] C(v,y)
+//   E_x[y][x] = sum_u w_u S(u,x) P[u][y]
+//   E_y[y][x] = sum_u C(u,x) R[u][y],        R[u][y] = sum_v w_v Psi[v][u] S(v,y)
+//
+// Three passes, each over whole rows held in shared memory:
+//   rows_fwd  : rho rows -> DCT-II along x -> T1[u][y] (written transposed)
+//   cols      : T1 rows  -> DCT-II along y -> divide -> inverse along y for P
+//               and R -> PT[y][u], RT[y][u] (written transposed); the energy
+//               N = 1/2 A_b sum B Psi (Parseval) is reduced here
+//   rows_inv  : PT, RT rows -> psi, E_x, E_y rows
+//
+// Each 1-D cosine transform of length n is one complex FFT of length n
+// (Makhoul's reordering: v[k] = r[2k], v[n-1-k] = r[2k+1]; A[u] =
+// Re(exp(-i pi u / 2n) V[u])), two real rows packed into one complex FFT.
+// The inverse cosine sum y[x] = sum_u c[u] C(u,x) is the inverse of that map;
+// a sine sum is a cosine sum of the reversed coefficients times (-1)^x.
+// The FFTs are radix-4 Stockham (plus one radix-2 stage for odd log2 n) in
+// shared memory with twiddles from a float32 table computed in FP64.
+#include "fftpl_internal.cuh"
+
+namespace fftpl {
+
+// ------------------------------------------------------------ FFT core
+// NB complex FFTs of length N = 2^LOGN, in place in buf[NB][N] (the stage
+// reads everything into registers, synchronises, then writes).  Forward:
+// X[k] = sum x[j] exp(-2 pi i jk / N); inverse: + sign, no 1/N.
+template <int LOGN, int NB>
+__device__ __forceinline__ void fft_block(float2* __restrict__ buf, const float2* __restrict__ tw,
+                                          bool inv) {
+    constexpr int N = 1 << LOGN;
+    constexpr int T = kSpecThreads;
+    constexpr int NQ = N / 4;
+    constexpr int I4 = NB * NQ;
+    constexpr int P4 = (I4 + T - 1) / T;
+    int Ns = 1;
+#pragma unroll 1
+    for (int s = 0; s + 2 <= LOGN; s += 2) {
+        float2 v[P4][4];
+        int dsti[P4];
+#pragma unroll
+        for (int i = 0; i < P4; ++i) {
+            int gi = threadIdx.x + i * T;
+            dsti[i] = -1;
+            if (I4 % T == 0 || gi < I4) {
+                int f = gi / NQ, j = gi % NQ;
+                int k = j & (Ns - 1);
+                const float2* src = buf + f * N + j;
+                int st = (NQ / Ns) * k;
+                float2 w1 = tw[st], w2 = tw[2 * st], w3 = tw[3 * st];
+                if (inv) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
+                v[i][0] = src[0];
+                v[i][1] = cmul(src[NQ], w1);
+                v[i][2] = cmul(src[2 * NQ], w2);
+                v[i][3] = cmul(src[3 * NQ], w3);
+                dsti[i] = f * N + (j - k) * 4 + k;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < P4; ++i) {
+            if (dsti[i] < 0) continue;
+            float2 a0 = v[i][0], a1 = v[i][1], a2 = v[i][2], a3 = v[i][3];
+            float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+            float2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
+            // forward: multiply d13 by -i ; inverse: by +i
+            float2 rd13 = inv ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+            float2* dst = buf + dsti[i];
+            dst[0] = cadd(s02, s13);
+            dst[Ns] = cadd(d02, rd13);
+            dst[2 * Ns] = csub(s02, s13);
+            dst[3 * Ns] = csub(d02, rd13);
+        }
+        __syncthreads();
+        Ns <<= 2;
+    }
+    if (LOGN & 1) {
+        constexpr int NH = N / 2;
+        constexpr int I2 = NB * NH;
+        constexpr int P2 = (I2 + T - 1) / T;
+        float2 v0[P2], v1[P2];
+        int dsti[P2];
+#pragma unroll
+        for (int i = 0; i < P2; ++i) {
+            int gi = threadIdx.x + i * T;
+            dsti[i] = -1;
+            if (I2 % T == 0 || gi < I2) {
+                int f = gi / NH, j = gi % NH;
+                int k = j & (Ns - 1);
+                float2 w1 = tw[(NH / Ns) * k];
+                if (inv) w1.y = -w1.y;
+                v0[i] = buf[f * N + j];
+                v1[i] = cmul(buf[f * N + j + NH], w1);
+                dsti[i] = f * N + (j - k) * 2 + k;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < P2; ++i) {
+            if (dsti[i] < 0) continue;
+            buf[dsti[i]] = cadd(v0[i], v1[i]);
+            buf[dsti[i] + Ns] = csub(v0[i], v1[i]);
+        }
+        __syncthreads();
+    }
+}
+
+// Position of sample x in Makhoul's reordering.
+__device__ __forceinline__ int mk_pos(int x, int N) { return (x & 1) ? (N - 1 - (x >> 1)) : (x >> 1); }
+// Sample of the natural order held at position k of the reordering.
+__device__ __forceinline__ int mk_src(int y, int N) { return (y & 1) ? (N - 1 - (y >> 1)) : (y >> 1); }
+
+// Spectrum of an inverse-cosine pair packed for one complex IFFT.  For the
+// sums y1 = sum c1[u] C(u,.), y2 = sum c2[u] C(u,.), with ct[0] = c[0],
+// ct[u] = c[u]/2 (u >= 1), ct[N] = 0:
+//   Z[u] = exp(i pi u / 2N) * ((ct1[u] + ct2[N-u]) + i (ct2[u] - ct1[N-u]))
+// and then y1 + i y2 = unshuffle(IFFT(Z)).
+__device__ __forceinline__ float2 pack_inv(float c1u, float c1nu, float c2u, float c2nu, float2 ph) {
+    float re = c1u + c2nu, im = c2u - c1nu;
+    // multiply by conj(ph) = exp(+i pi u / 2N)
+    return make_float2(re * ph.x + im * ph.y, im * ph.x - re * ph.y);
+}
+
+// -------------------------------------------------------- pass 1: rows
+// CTA: 8 rows of rho (2 per complex buffer).  Writes T1[u][y0..y0+7].
+template <int LOGN, bool QUANT>
+__global__ void __launch_bounds__(kSpecThreads)
+k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
+           const float* __restrict__ M, float inv_ab, float cap, float* __restrict__ T1,
+           const float2* __restrict__ tw, const float2* __restrict__ ph, double* __restrict__ acc) {
+    constexpr int N = 1 << LOGN;
+    constexpr int NB = kSpecBuffers;
+    constexpr int ROWS = 2 * NB;
+    constexpr int T = kSpecThreads;
+    extern __shared__ float2 sm[];
+    const int y0 = blockIdx.x * ROWS;
+    dfloat tau = df_zero(), charge = df_zero();
+    for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
+        int r = idx >> LOGN, x = idx & (N - 1);
+        size_t b = (size_t)(y0 + r) * N + x;
+        float d = QUANT ? (float)Dq[b] * 2.3283064365386963e-10f : D[b];
+        float mm = M[b];
+        tau = df_add(tau, fmaxf(0.0f, d - (cap - mm)));
+        charge = df_add(charge, d + mm);
+        float rho = (d + mm) * inv_ab;
+        reinterpret_cast<float*>(sm + (r >> 1) * N + mk_pos(x, N))[r & 1] = rho;
+    }
+    df_warp_atomic(tau, acc + ACC_TAU);
+    df_warp_atomic(charge, acc + ACC_CHARGE);
+    __syncthreads();
+    fft_block<LOGN, NB>(sm, tw, false);
+    // split the packed spectra and apply the post-twiddle:
+    // A_j[u] = Re(ph[u] V_j[u]), V_1 = (Z[u] + conj Z[N-u]) / 2,
+    // V_2 = (Z[u] - conj Z[N-u]) / 2i.
+    constexpr int HALF = N / 2 + 1;
+    constexpr int ITEMS = NB * HALF;
+    constexpr int PI = (ITEMS + T - 1) / T;
+    float out[PI][4];
+    int where[PI];
+#pragma unroll
+    for (int i = 0; i < PI; ++i) {
+        int gi = threadIdx.x + i * T;
+        where[i] = -1;
+        if (gi < ITEMS) {
+            int f = gi / HALF, u = gi % HALF;
+            float2 zu = sm[f * N + u];
+            float2 zn = sm[f * N + ((N - u) & (N - 1))];
+            float2 v1 = make_float2(0.5f * (zu.x + zn.x), 0.5f * (zu.y - zn.y));
+            float2 v2 = make_float2(0.5f * (zu.y + zn.y), 0.5f * (zn.x - zu.x));
+            float2 p = ph[u];
+            out[i][0] = v1.x * p.x - v1.y * p.y;   // A1[u]
+            out[i][1] = v2.x * p.x - v2.y * p.y;   // A2[u]
+            // at N-u the spectra are conjugated
+            float2 q = ph[N - u];
+            out[i][2] = v1.x * q.x + v1.y * q.y;   // A1[N-u]
+            out[i][3] = v2.x * q.x + v2.y * q.y;   // A2[N-u]
+            where[i] = f * HALF + u;
+        }
+    }
+    __syncthreads();
+    float* sf = reinterpret_cast<float*>(sm);
+#pragma unroll
+    for (int i = 0; i < PI; ++i) {
+        if (where[i] < 0) continue;
+        int f = where[i] / HALF, u = where[i] % HALF;
+        float* r1 = sf + (2 * f) * N;
+        float* r2 = sf + (2 * f + 1) * N;
+        r1[u & (N - 1)] = out[i][0];
+        r2[u & (N - 1)] = out[i][1];
+        if (u > 0 && u < N / 2) {
+            r1[N - u] = out[i][2];
+            r2[N - u] = out[i][3];
+        }
+    }
+    __syncthreads();
+    // transposed write: T1[u][y0 .. y0+7]
+    for (int u = threadIdx.x; u < N; u += T) {
+        float4 a = make_float4(sf[0 * N + u], sf[1 * N + u], sf[2 * N + u], sf[3 * N + u]);
+        float4 b = make_float4(sf[4 * N + u], sf[5 * N + u], sf[6 * N + u], sf[7 * N + u]);
+        float4* dst = reinterpret_cast<float4*>(T1 + (size_t)u * N + y0);
+        dst[0] = a;
+        dst[1] = b;
+    }
+}
+
+// ------------------------------------------------- pass 2: columns
+// CTA: 4 rows u of T1.  Forward DCT-II along y, spectral divide, energy,
+// then per row one complex IFFT carrying P (cosine sum) in the real part and
+// R (sine sum, via reversed coefficients) in the imaginary part.
+template <int LOGN>
+__global__ void __launch_bounds__(kSpecThreads)
+k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__ RT,
+       const float2* __restrict__ tw, const float2* __restrict__ ph, float pi_lx, float pi_ly,
+       double* __restrict__ acc) {
+    constexpr int N = 1 << LOGN;
+    constexpr int NB = kSpecBuffers;
+    constexpr int ROWS = NB;
+    constexpr int T = kSpecThreads;
+    extern __shared__ float2 sm[];
+    const int u0 = blockIdx.x * ROWS;
+    for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
+        int r = idx >> LOGN, y = idx & (N - 1);
+        float val = T1[(size_t)(u0 + r) * N + y];
+        reinterpret_cast<float*>(sm + (r >> 1) * N + mk_pos(y, N))[r & 1] = val;
+    }
+    __syncthreads();
+    fft_block<LOGN, NB / 2>(sm, tw, false);
+    constexpr int HALF = N / 2 + 1;
+    constexpr int ITEMS = (NB / 2) * HALF;
+    constexpr int PI = (ITEMS + T - 1) / T;
+    float2 zo[PI][4];   // [row a at v, row a at N-v, row b at v, row b at N-v]
+    int where[PI];
+    const float invn2 = 1.0f / ((float)N * (float)N);
+    dfloat energy = df_zero();
+#pragma unroll
+    for (int i = 0; i < PI; ++i) {
+        int gi = threadIdx.x + i * T;
+        where[i] = -1;
+        if (gi < ITEMS) {
+            int f = gi / HALF, v = gi % HALF;
+            int vn = (N - v) & (N - 1);
+            float2 zu = sm[f * N + v];
+            float2 zn = sm[f * N + vn];
+            float2 v1 = make_float2(0.5f * (zu.x + zn.x), 0.5f * (zu.y - zn.y));
+            float2 v2 = make_float2(0.5f * (zu.y + zn.y), 0.5f * (zn.x - zu.x));
+            float2 p = ph[v], q = ph[N - v];
+            // B[row][v] (unnormalised DCT-II along y)
+            float B[2][2];
+            B[0][0] = v1.x * p.x - v1.y * p.y;
+            B[1][0] = v2.x * p.x - v2.y * p.y;
+            B[0][1] = v1.x * q.x + v1.y * q.y;
+            B[1][1] = v2.x * q.x + v2.y * q.y;
+            float wv = pi_ly * (float)v, wvn = pi_ly * (float)(N - v);
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                int u = u0 + 2 * f + rr;
+                float wu = pi_lx * (float)u;
+                float eu = (u == 0) ? 1.0f : 2.0f;
+                // Psi at v and at N - v (v = 0 has no partner: coefficient index N is absent)
+                float ev = (v == 0) ? 1.0f : 2.0f;
+                float d0 = wu * wu + wv * wv;
+                float a0 = eu * ev * invn2 * B[rr][0];
+                float psi0 = (u == 0 && v == 0) ? 0.0f : a0 / d0;
+                float psin = 0.0f;
+                bool has_n = (v > 0 && v < N / 2);
+                if (has_n) {
+                    float dn = wu * wu + wvn * wvn;
+                    float an = eu * 2.0f * invn2 * B[rr][1];
+                    psin = an / dn;
+                    energy = df_add(energy, B[rr][1] * psin);
+                }
+                energy = df_add(energy, B[rr][0] * psi0);
+                // inverse inputs: c1 = Psi (cosine sum), c2[v'] = s[N - v'] with
+                // s[v] = w_v Psi[v] (sine sum), c2[0] = 0
+                // halved coefficients ct[k] = c[k] / 2 for k >= 1
+                float c1v = (v == 0) ? psi0 : 0.5f * psi0;
+                float c1n = 0.5f * psin;                              // index N - v (0 if v == 0)
+                float c2v = (v == 0) ? 0.0f : 0.5f * wvn * psin;      // c2[v] = s[N-v]
+                float c2n = (v == 0) ? 0.0f : 0.5f * wv * psi0;       // c2[N-v] = s[v]
+                if (v == N / 2) {
+                    // partner of N/2 is itself: c1[N/2] = Psi(N/2), c2[N/2] = s[N/2]
+                    c1n = c1v;
+                    c2v = 0.5f * wv * psi0;
+                    c2n = c2v;
+                }
+                zo[i][2 * rr + 0] = pack_inv(c1v, c1n, c2v, c2n, p);
+                zo[i][2 * rr + 1] = pack_inv(c1n, c1v, c2n, c2v, q);
+            }
+            where[i] = f * HALF + v;
+        }
+    }
+    df_warp_atomic(energy, acc + ACC_N);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PI; ++i) {
+        if (where[i] < 0) continue;
+        int f = where[i] / HALF, v = where[i] % HALF;
+        for (int rr = 0; rr < 2; ++rr) {
+            float2* row = sm + (2 * f + rr) * N;
+            row[v & (N - 1)] = zo[i][2 * rr + 0];
+            if (v > 0 && v < N / 2) row[N - v] = zo[i][2 * rr + 1];
+        }
+    }
+    __syncthreads();
+    fft_block<LOGN, NB>(sm, tw, true);
+    // unshuffle: y even <- k = y/2, y odd <- k = N-1-(y-1)/2;  P = Re, R = (-1)^y Im
+    for (int y = threadIdx.x; y < N; y += T) {
+        int k = mk_src(y, N);
+        float sgn = (y & 1) ? -1.0f : 1.0f;
+        float4 pv, rv;
+        float2 z0 = sm[0 * N + k], z1 = sm[1 * N + k], z2 = sm[2 * N + k], z3 = sm[3 * N + k];
+        pv = make_float4(z0.x, z1.x, z2.x, z3.x);
+        rv = make_float4(sgn * z0.y, sgn * z1.y, sgn * z2.y, sgn * z3.y);
+        *reinterpret_cast<float4*>(PT + (size_t)y * N + u0) = pv;
+        *reinterpret_cast<float4*>(RT + (size_t)y * N + u0) = rv;
+    }
+}
+
+// ------------------------------------------------- pass 3: inverse rows
+// CTA: 4 rows y.  Round A: psi (cosine sum of P) + i E_y (cosine sum of R),
+// one IFFT per row.  Round B: E_x (sine sum of w_u P) for rows pairwise.
+template <int LOGN>
+__global__ void __launch_bounds__(kSpecThreads)
+k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __restrict__ psi,
+           float* __restrict__ ex, float* __restrict__ ey, const float2* __restrict__ tw,
+           const float2* __restrict__ ph, float pi_lx) {
+    constexpr int N = 1 << LOGN;
+    constexpr int NB = kSpecBuffers;
+    constexpr int ROWS = NB;
+    constexpr int T = kSpecThreads;
+    constexpr int HALF = N / 2 + 1;
+    extern __shared__ float2 sm[];
+    const int y0 = blockIdx.x * ROWS;
+    // round A
+    for (int idx = threadIdx.x; idx < ROWS * HALF; idx += T) {
+        int r = idx / HALF, u = idx % HALF;
+        const float* P = PT + (size_t)(y0 + r) * N;
+        const float* R = RT + (size_t)(y0 + r) * N;
+        float pu = P[u & (N - 1)], ru = R[u & (N - 1)];
+        float pn = (u > 0) ? P[N - u] : 0.0f, rn = (u > 0) ? R[N - u] : 0.0f;
+        float c1u = (u == 0) ? pu : 0.5f * pu, c2u = (u == 0) ? ru : 0.5f * ru;
+        float c1n = 0.5f * pn, c2n = 0.5f * rn;
+        if (u == N / 2) { c1n = c1u; c2n = c2u; }
+        float2* row = sm + r * N;
+        row[u & (N - 1)] = pack_inv(c1u, c1n, c2u, c2n, ph[u]);
+        if (u > 0 && u < N / 2) row[N - u] = pack_inv(c1n, c1u, c2n, c2u, ph[N - u]);
+    }
+    __syncthreads();
+    fft_block<LOGN, NB>(sm, tw, true);
+    for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
+        int r = idx >> LOGN, x = idx & (N - 1);
+        float2 z = sm[r * N + mk_src(x, N)];
+        size_t b = (size_t)(y0 + r) * N + x;
+        psi[b] = z.x;
+        ey[b] = z.y;
+    }
+    __syncthreads();
+    // round B: E_x rows (2 per buffer).  c[u'] = s[N-u'] (u' >= 1), c[0] = 0,
+    // s[u] = w_u P[u]; E_x[x] = (-1)^x cosine-sum(c)[x].
+    for (int idx = threadIdx.x; idx < (ROWS / 2) * HALF; idx += T) {
+        int f = idx / HALF, u = idx % HALF;
+        const float* Pa = PT + (size_t)(y0 + 2 * f) * N;
+        const float* Pb = Pa + N;
+        float wu = pi_lx * (float)u, wn = pi_lx * (float)(N - u);
+        // c[u] = s[N-u] = w_{N-u} P[N-u]  (u >= 1);  c[N-u] = s[u] = w_u P[u]
+        float ca_u = (u == 0) ? 0.0f : 0.5f * wn * Pa[N - u];
+        float cb_u = (u == 0) ? 0.0f : 0.5f * wn * Pb[N - u];
+        float ca_n = (u == 0) ? 0.0f : 0.5f * wu * Pa[u];
+        float cb_n = (u == 0) ? 0.0f : 0.5f * wu * Pb[u];
+        if (u == N / 2) { ca_n = ca_u; cb_n = cb_u; }
+        float2* row = sm + f * N;
+        row[u & (N - 1)] = pack_inv(ca_u, ca_n, cb_u, cb_n, ph[u]);
+        if (u > 0 && u < N / 2) row[N - u] = pack_inv(ca_n, ca_u, cb_n, cb_u, ph[N - u]);
+    }
+    __syncthreads();
+    fft_block<LOGN, NB / 2>(sm, tw, true);
+    for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
+        int r = idx >> LOGN, x = idx & (N - 1);
+        float2 z = sm[(r >> 1) * N + mk_src(x, N)];
+        float val = (r & 1) ? z.y : z.x;
+        ex[(size_t)(y0 + r) * N + x] = (x & 1) ? -val : val;
+    }
+}
+
+// ------------------------------------------------------------ launch
+template <int LOGN>
+static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {
+    constexpr int N = 1 << LOGN;
+    size_t smem = (size_t)kSpecBuffers * N * sizeof(float2);
+    float inv_ab = (float)(1.0 / c.Ab);
+    float cap = (float)(c.opt.target_density * c.Ab);
+    float pi_lx = (float)(M_PI / c.Lx), pi_ly = (float)(M_PI / c.Ly);
+    cudaError_t e = cudaSuccess;
+    if (which == 0) {
+        if (c.opt.deterministic) {
+            auto kf = k_rows_fwd<LOGN, true>;
+            kf<<<N / (2 * kSpecBuffers), kSpecThreads, smem, s>>>(nullptr, c.Dq, c.M, inv_ab, cap,
+                                                                   c.T1, c.tw, c.ph, c.acc);
+        } else {
+            auto kf = k_rows_fwd<LOGN, false>;
+            kf<<<N / (2 * kSpecBuffers), kSpecThreads, smem, s>>>(c.D, nullptr, c.M, inv_ab, cap,
+                                                                   c.T1, c.tw, c.ph, c.acc);
+        }
+    } else if (which == 1) {
+        auto kf = k_cols<LOGN>;
+        kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.T1, c.PT, c.RT, c.tw, c.ph, pi_lx, pi_ly,
+                                                        c.acc);
+    } else {
+        auto kf = k_rows_inv<LOGN>;
+        kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.PT, c.RT, c.psi, c.ex, c.ey, c.tw, c.ph,
+                                                        pi_lx);
+    }
+    c.launches++;
+    e = cudaGetLastError();
+    return e;
+}
+
+// Shared-memory opt-in for every kernel of one transform size (done at create,
+// outside any stream capture).
+template <int LOGN>
+static void prepare_logn() {
+    int smem = (int)((size_t)kSpecBuffers * (1 << LOGN) * sizeof(float2));
+    cudaFuncSetAttribute(k_rows_fwd<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_rows_fwd<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_cols<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_rows_inv<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+void prepare_spectral(int logn) {
+    switch (logn) {
+        case 4: prepare_logn<4>(); break;
+        case 5: prepare_logn<5>(); break;
+        case 6: prepare_logn<6>(); break;
+        case 7: prepare_logn<7>(); break;
+        case 8: prepare_logn<8>(); break;
+        case 9: prepare_logn<9>(); break;
+        case 10: prepare_logn<10>(); break;
+        case 11: prepare_logn<11>(); break;
+        case 12: prepare_logn<12>(); break;
+        default: break;
+    }
+}
+
+static cudaError_t dispatch(Ctx& c, int which, cudaStream_t s) {
+    switch (c.logn) {
+        case 4: return launch_all_logn<4>(c, which, s);
+        case 5: return launch_all_logn<5>(c, which, s);
+        case 6: return launch_all_logn<6>(c, which, s);
+        case 7: return launch_all_logn<7>(c, which, s);
+        case 8: return launch_all_logn<8>(c, which, s);
+        case 9: return launch_all_logn<9>(c, which, s);
+        case 10: return launch_all_logn<10>(c, which, s);
+        case 11: return launch_all_logn<11>(c, which, s);
+        case 12: return launch_all_logn<12>(c, which, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s) { return dispatch(c, 0, s); }
+cudaError_t launch_cols_spectral(Ctx& c, cudaStream_t s) { return dispatch(c, 1, s); }
+cudaError_t launch_rows_inv(Ctx& c, cudaStream_t s) { return dispatch(c, 2, s); }
+
+}  // namespace fftpl

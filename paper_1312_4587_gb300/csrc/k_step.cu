@@ -1,0 +1,186 @@
+// Placement loop kernels: the per-cell gradient with the lambda update, the
+// combined gradient g = grad W~ + lambda grad N with the step-size sums, and
+// the Nesterov position update (Algorithm 1 with Nesterov's method in place of
+// the conjugate-gradient solver; control of Section IV-A in loop_ctrl.cuh).
+//
+// Vectors hold x coordinates in [0, m) and y coordinates in [m, 2m).
+#include "loop_ctrl.cuh"
+
+namespace fftpl {
+
+struct LoopBufs {
+    float *u, *v, *vprev, *g, *gprev, *gN, *gW;
+    const float *w, *h;
+    double *ctrl, *acc, *recs;
+    unsigned int* counters;
+};
+
+// gather + pin sums at v (like k_cells) and, in the last CTA, lambda_k.
+template <bool CSR>
+__global__ void __launch_bounds__(kCellThreads)
+k_loop_cells(Grid gr, int m, LoopBufs b, const float* __restrict__ ex,
+             const float* __restrict__ ey, const int* __restrict__ cell_pin_ptr,
+             const float2* __restrict__ gpin) {
+    if (b.ctrl[C_DONE] != 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float nx = 0.0f, ny = 0.0f, wx = 0.0f, wy = 0.0f;
+    if (i < m) {
+        Span s = cell_span(gr, b.v[i], b.v[m + i], b.w[i], b.h[i]);
+        for (int j = s.jlo; j <= s.jhi; ++j) {
+            float oy = ov_len(gr.y0, gr.hb, j, s.yl, s.yh);
+            const float* rx = ex + (size_t)j * gr.n;
+            const float* ry = ey + (size_t)j * gr.n;
+            for (int k = s.ilo; k <= s.ihi; ++k) {
+                float o = __fmul_rn(ov_len(gr.x0, gr.wb, k, s.xl, s.xh), oy);
+                nx = fmaf(o, __ldg(rx + k), nx);
+                ny = fmaf(o, __ldg(ry + k), ny);
+            }
+        }
+        nx = -nx;
+        ny = -ny;
+        b.gN[i] = nx;
+        b.gN[m + i] = ny;
+        if (CSR) {
+            for (int q = cell_pin_ptr[i]; q < cell_pin_ptr[i + 1]; ++q) {
+                float2 p = gpin[q];
+                wx += p.x;
+                wy += p.y;
+            }
+            b.gW[i] = wx;
+            b.gW[m + i] = wy;
+        } else {
+            wx = b.gW[i];
+            wy = b.gW[m + i];
+        }
+    }
+    df_warp_atomic(df_add(df_zero(), fabsf(nx) + fabsf(ny)), b.acc + ACC_GN_L1);
+    df_warp_atomic(df_add(df_zero(), fabsf(wx) + fabsf(wy)), b.acc + ACC_GW_L1);
+    if (last_cta(b.counters + 0) && threadIdx.x == 0) ctrl_lambda(b.ctrl, b.acc);
+}
+
+// g = gW + lambda gN; sums for alpha_k; last CTA: alpha_k and beta_k.
+__global__ void __launch_bounds__(kCellThreads) k_loop_g(int m2, LoopBufs b) {
+    if (b.ctrl[C_DONE] != 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float lam = (float)b.ctrl[C_LAMBDA];
+    const bool first = b.ctrl[C_K] == 0.0;
+    float dg = 0.0f, dv = 0.0f, gi = 0.0f;
+    if (i < m2) {
+        float gg = fmaf(lam, b.gN[i], b.gW[i]);
+        b.g[i] = gg;
+        gi = fabsf(gg);
+        if (!first) {
+            float a = gg - b.gprev[i], c = b.v[i] - b.vprev[i];
+            dg = a * a;
+            dv = c * c;
+        }
+    }
+    df_warp_atomic(df_add(df_zero(), dg), b.acc + ACC_DG2);
+    df_warp_atomic(df_add(df_zero(), dv), b.acc + ACC_DV2);
+    float mx = warp_max(gi);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(b.acc + ACC_GINF, (double)mx);
+    if (last_cta(b.counters + 1) && threadIdx.x == 0) ctrl_alpha(b.ctrl, b.acc);
+}
+
+// u_{k+1} = clamp(v_k - alpha g_k); v_{k+1} = clamp(u_{k+1} + beta (u_{k+1} - u_k));
+// clamp keeps the cell inside the region.  Last CTA: record and advance.
+__global__ void __launch_bounds__(kCellThreads)
+k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
+    if (b.ctrl[C_DONE] != 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float alpha = (float)b.ctrl[C_ALPHA], beta = (float)b.ctrl[C_BETA];
+    float step = 0.0f;
+    if (i < 2 * m) {
+        bool isx = i < m;
+        int c = isx ? i : i - m;
+        float half = __fmul_rn(0.5f, isx ? b.w[c] : b.h[c]);
+        float lo = __fadd_rn(isx ? gr.x0 : gr.y0, half), hi = __fsub_rn(isx ? x1 : y1, half);
+        float vi = b.v[i], gi = b.g[i], ui = b.u[i];
+        float un = fminf(hi, fmaxf(lo, vi - alpha * gi));
+        step = fabsf(un - vi);
+        float vn = fminf(hi, fmaxf(lo, un + beta * (un - ui)));
+        b.vprev[i] = vi;
+        b.gprev[i] = gi;
+        b.u[i] = un;
+        b.v[i] = vn;
+    }
+    float mx = warp_max(step);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(b.acc + ACC_STEPMAX, (double)mx);
+    if (last_cta(b.counters + 2) && threadIdx.x == 0) ctrl_record(b.ctrl, b.acc, b.recs);
+}
+
+// u = v = clamp(x0, y0); previous vectors zeroed.
+__global__ void k_place_init(int m, Grid gr, float x1, float y1, const float* __restrict__ x0,
+                             const float* __restrict__ y0, LoopBufs b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * m) return;
+    bool isx = i < m;
+    int c = isx ? i : i - m;
+    float half = __fmul_rn(0.5f, isx ? b.w[c] : b.h[c]);
+    float lo = __fadd_rn(isx ? gr.x0 : gr.y0, half), hi = __fsub_rn(isx ? x1 : y1, half);
+    float p = isx ? x0[c] : y0[c];
+    p = fminf(hi, fmaxf(lo, p));
+    b.u[i] = p;
+    b.v[i] = p;
+    b.vprev[i] = p;
+    b.g[i] = 0.0f;
+    b.gprev[i] = 0.0f;
+}
+
+// gamma_0 from the overflow at the start (schedule mode).
+__global__ void k_gamma0(double* ctrl, const double* acc) {
+    double tau = ld(acc + ACC_TAU) / ctrl[C_MOV_AREA];
+    ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
+}
+
+static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }
+
+LoopBufs loop_bufs(Ctx& c) {
+    LoopBufs b;
+    b.u = c.u; b.v = c.v; b.vprev = c.vprev; b.g = c.g; b.gprev = c.gprev;
+    b.gN = c.gN; b.gW = c.gW; b.w = c.w; b.h = c.h;
+    b.ctrl = c.ctrl; b.acc = c.acc; b.recs = c.recs;
+    b.counters = reinterpret_cast<unsigned int*>(c.ctrl + C_COUNT);
+    return b;
+}
+
+cudaError_t launch_loop_cells(Ctx& c, cudaStream_t s) {
+    LoopBufs b = loop_bufs(c);
+    int nb = nblk(c.m_mov, kCellThreads);
+    if (c.opt.deterministic)
+        k_loop_cells<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.ex, c.ey,
+                                                       c.cell_pin_ptr, c.gpin);
+    else
+        k_loop_cells<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.ex, c.ey, nullptr,
+                                                        nullptr);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_g(Ctx& c, cudaStream_t s) {
+    k_loop_g<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_update(Ctx& c, cudaStream_t s) {
+    k_loop_update<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
+        c.m_mov, c.grid, (float)c.x1, (float)c.y1, loop_bufs(c));
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place_init(Ctx& c, const float* x0, const float* y0, cudaStream_t s) {
+    k_place_init<<<nblk(2LL * c.m_mov, 256), 256, 0, s>>>(c.m_mov, c.grid, (float)c.x1,
+                                                         (float)c.y1, x0, y0, loop_bufs(c));
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gamma0(Ctx& c, cudaStream_t s) {
+    k_gamma0<<<1, 1, 0, s>>>(c.ctrl, c.acc);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace fftpl

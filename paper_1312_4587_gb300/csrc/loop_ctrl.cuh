@@ -1,0 +1,112 @@
+// Placement-loop control scalars (Algorithm 1 with a Nesterov step; the
+// parameter control of Section IV-A), kept in FP64 in device memory and
+// updated by the last CTA of the kernel that produces their inputs (a CTA
+// learns it is last from an atomic ticket after a memory fence; nothing
+// waits, so no kernel can hang on it).
+#pragma once
+
+#include "fftpl_internal.cuh"
+
+namespace fftpl {
+
+enum {
+    C_LAMBDA = 0, C_GAMMA, C_ALPHA, C_ALPHA_MAX, C_A, C_BETA, C_HP_PREV, C_K, C_DONE, C_A_NEXT,
+    C_ALPHA_MAX0, C_DW_REF, C_GAMMA_FIXED, C_LAMBDA0_OPT, C_STOP_ON_TAU, C_TAU_STOP, C_WB,
+    C_HALF_AB, C_MOV_AREA, C_REC_CAP, C_REC_BASE,
+    C_COUNT
+};
+constexpr int kRecFields = 8;
+constexpr int kCounters = 4;   // one ticket counter per loop kernel kind
+
+// All threads fence their atomics, then thread 0 takes a ticket; the CTA that
+// draws the last ticket resets the counter and returns true.
+__device__ __forceinline__ bool last_cta(unsigned int* counter) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1);
+        if (is_last) *counter = 0u;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+__device__ __forceinline__ double ld(const double* p) { return __ldcg(p); }
+
+// After the cell kernel: lambda_k.  lambda_0 = ||grad W~||_1 / ||grad N||_1
+// unless given; for k >= 1 lambda_k = mu_k lambda_{k-1} with
+// mu_k = 1.1^(-dW/dW_ref + 1) bounded to [0.75, 1.1], dW the HPWL change.
+__device__ __forceinline__ void ctrl_lambda(double* ctrl, const double* acc) {
+    int k = (int)ctrl[C_K];
+    double hp = ld(acc + ACC_HPWL);
+    double lam = ctrl[C_LAMBDA];
+    if (k == 0 && ctrl[C_LAMBDA0_OPT] <= 0.0) {
+        double gn = ld(acc + ACC_GN_L1), gw = ld(acc + ACC_GW_L1);
+        lam = gn > 0.0 ? gw / gn : 1.0;
+    }
+    if (k >= 1) {
+        double mu = pow(1.1, -(hp - ctrl[C_HP_PREV]) / ctrl[C_DW_REF] + 1.0);
+        lam *= fmin(1.1, fmax(0.75, mu));
+    }
+    ctrl[C_HP_PREV] = hp;
+    ctrl[C_LAMBDA] = lam;
+}
+
+// After the combined gradient: the step alpha_k and the momentum weight.
+// alpha_0 = alpha_max_0 / ||g||_inf; alpha_k = ||v_k - v_{k-1}|| / ||g_k - g_{k-1}||;
+// alpha_k ||g||_inf is then kept within [0.01 alpha_max_k, alpha_max_k].
+__device__ __forceinline__ void ctrl_alpha(double* ctrl, const double* acc) {
+    int k = (int)ctrl[C_K];
+    double ginf = ld(acc + ACC_GINF);
+    double alpha = ctrl[C_ALPHA], amax = ctrl[C_ALPHA_MAX];
+    if (k == 0) {
+        alpha = ginf > 0.0 ? ctrl[C_ALPHA_MAX0] / ginf : 0.0;
+    } else {
+        double dg2 = ld(acc + ACC_DG2), dv2 = ld(acc + ACC_DV2);
+        if (dg2 > 0.0) alpha = sqrt(dv2) / sqrt(dg2);
+    }
+    if (ginf > 0.0) {
+        if (alpha * ginf > amax) alpha = amax / ginf;
+        if (alpha * ginf < 0.01 * amax) alpha = 0.01 * amax / ginf;
+    }
+    double a = ctrl[C_A];
+    double an = 0.5 * (1.0 + sqrt(1.0 + 4.0 * a * a));
+    ctrl[C_ALPHA] = alpha;
+    ctrl[C_A_NEXT] = an;
+    ctrl[C_BETA] = (a - 1.0) / an;
+}
+
+// gamma = 8.0 w_b 10^((20/9)(tau - 0.1) - 1) (Section IV-A).
+__device__ __forceinline__ double gamma_schedule(double tau, double wb) {
+    return 8.0 * wb * pow(10.0, (20.0 / 9.0) * (tau - 0.1) - 1.0);
+}
+
+// After the position update: record iteration k, then alpha_max_{k+1},
+// gamma_{k+1}, k+1 and the stop test tau <= tau_stop.
+__device__ __forceinline__ void ctrl_record(double* ctrl, const double* acc, double* recs) {
+    int k = (int)ctrl[C_K];
+    double tau = ld(acc + ACC_TAU) / ctrl[C_MOV_AREA];
+    double step_max = ld(acc + ACC_STEPMAX);
+    int slot = k - (int)ctrl[C_REC_BASE];
+    if (slot >= 0 && slot < (int)ctrl[C_REC_CAP]) {
+        double* r = recs + (size_t)slot * kRecFields;
+        r[0] = ld(acc + ACC_W);
+        r[1] = ld(acc + ACC_HPWL);
+        r[2] = ld(acc + ACC_N) * ctrl[C_HALF_AB];
+        r[3] = tau;
+        r[4] = ctrl[C_LAMBDA];
+        r[5] = ctrl[C_GAMMA];
+        r[6] = ctrl[C_ALPHA];
+        r[7] = step_max;
+    }
+    ctrl[C_A] = ctrl[C_A_NEXT];
+    ctrl[C_ALPHA_MAX] = fmax(ctrl[C_ALPHA_MAX0], 2.0 * step_max);
+    if (ctrl[C_GAMMA_FIXED] <= 0.0) ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
+    ctrl[C_K] = (double)(k + 1);
+    if (ctrl[C_STOP_ON_TAU] != 0.0 && tau <= ctrl[C_TAU_STOP]) ctrl[C_DONE] = 1.0;
+}
+
+}  // namespace fftpl

@@ -1,0 +1,105 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/fftpl.h declares; host-side validation rejects bad instances before
+any device work (so these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1312_4587_gb300 import _build
+    _build.build()
+    from paper_1312_4587_gb300 import fftpl
+    fftpl.lib()
+    return fftpl
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fftpl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fftpl_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("fftpl_create", "fftpl_density", "fftpl_wa", "fftpl_step", "fftpl_eval",
+                     "fftpl_destroy", "fftpl_fields", "fftpl_state_save", "fftpl_state_load"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(F):
+    lib = ctypes.CDLL(F.LIB_PATH)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_version_and_defaults(F):
+    assert F.fftpl_version() == 100
+    o = F.fftpl_default_options()
+    assert o.target_density == 1.0 and o.dw_ref == 3.5e5 and abs(o.alpha_max0_bins - 0.044) < 1e-15
+    assert o.tau_stop == 0.1 and o.solve_path == F.FFTPL_SOLVE_FFT
+
+
+def _tiny():
+    import synth
+    return synth.make_instance("tiny")
+
+
+def _create(F, inst, **kw):
+    args = dict(region=inst.region, n=inst.n, w=inst.w, h=inst.h, m_mov=inst.m_mov,
+                fix_x=inst.fix_x, fix_y=inst.fix_y, net_ptr=inst.net_ptr, pin_cell=inst.pin_cell,
+                pin_dx=inst.pin_dx, pin_dy=inst.pin_dy)
+    opts = kw.pop("options", None)
+    args.update(kw)
+    return F.fftpl_create(options=opts, stream=0, **args)
+
+
+@pytest.mark.parametrize("change,needle", [
+    (dict(n=48), "power of two"),
+    (dict(n=8), "power of two"),
+    (dict(n=8192), "power of two"),
+    (dict(region=(0.0, 0.0, 100.1, 100.1)), "exact in float32"),
+    (dict(region=(0.0, 0.0, -5.0, 10.0)), "x1 > x0"),
+])
+def test_invalid_instances_rejected(F, change, needle):
+    inst = _tiny()
+    with pytest.raises(F.FFTPLError) as ei:
+        _create(F, inst, **change)
+    assert ei.value.status == F.FFTPL_EINVAL
+    assert needle in str(ei.value)
+    assert needle in F.fftpl_last_error(None)
+
+
+def test_invalid_arrays_rejected(F):
+    inst = _tiny()
+    bad = inst.pin_cell.copy(); bad[3] = inst.m_mov + 5
+    with pytest.raises(F.FFTPLError, match="pin_cell out of range"):
+        _create(F, inst, pin_cell=bad)
+    w = inst.w.copy(); w[0] = -1.0
+    with pytest.raises(F.FFTPLError, match="sizes must be finite"):
+        _create(F, inst, w=w)
+    w = inst.w.copy(); w[1] = np.nan
+    with pytest.raises(F.FFTPLError, match="sizes must be finite"):
+        _create(F, inst, w=w)
+    npn = inst.net_ptr.copy(); npn[5] = npn[6] + 1
+    with pytest.raises(F.FFTPLError, match="non-decreasing"):
+        _create(F, inst, net_ptr=npn)
+    dx = inst.pin_dx.copy(); dx[0] = np.inf
+    with pytest.raises(F.FFTPLError, match="offsets must be finite"):
+        _create(F, inst, pin_dx=dx)
+    o = F.fftpl_default_options(target_density=0.0)
+    with pytest.raises(F.FFTPLError, match="target_density"):
+        _create(F, inst, options=o)
+
+
+def test_null_handle_calls_are_safe(F):
+    F.fftpl_destroy(None)
+    assert F.fftpl_launch_count(None) == 0
+    assert F.fftpl_device_bytes(None) == 0
+    assert F.lib().fftpl_check(None) == F.FFTPL_EINVAL

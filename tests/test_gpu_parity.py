@@ -1,0 +1,286 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 unless noted):
+  rho 1e-6; psi, E_x, E_y, grad N, grad W~ 1e-5 (FP32 path, stated bound);
+  HPWL and W~ 1e-6 relative (FP64 sums of float32 per-net terms);
+  N 2e-6 relative (Parseval sum of float32 spectra: the FFT's relative error
+  of ~log2(n) x 6e-8 on the dominant low-frequency terms);
+  tau 1e-5 relative (sum of float32 differences D_b - cap_b: each bin's area
+  carries ~1e-6 relative error, bounded by 1e-6 of the total movable area);
+  integer bookkeeping bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_MAP = 1e-5
+TOL_RHO = 1e-6
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1312_4587_gb300 import fftpl
+    fftpl.lib()
+    return fftpl
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def gpu_eval(F, inst, x=None, y=None, gamma=None, **opts):
+    import torch
+    x = inst.x if x is None else x
+    y = inst.y if y is None else y
+    gamma = inst.gamma if gamma is None else gamma
+    with F.Problem(inst, **opts) as p:
+        xd, yd = cuda(x), cuda(y)
+        g = [torch.empty_like(xd) for _ in range(4)]
+        rep = F.fftpl_eval(p.h, xd, yd, gamma, *g)
+        fl = F.fftpl_fields(p.h, inst.n)
+        out = {k: v.cpu().numpy() for k, v in fl.items()}
+        out.update(gNx=g[0].cpu().numpy(), gNy=g[1].cpu().numpy(), gWx=g[2].cpu().numpy(),
+                   gWy=g[3].cpu().numpy(), rep=rep, launches=F.fftpl_launch_count(p.h))
+    return out
+
+
+def check_eval(got, ref, tol_map=TOL_MAP):
+    errs = {
+        "rho": rel(got["rho"], ref["rho"]),
+        "psi": rel(got["psi"], ref["psi"]),
+        "ex": rel(got["ex"], ref["ex"]),
+        "ey": rel(got["ey"], ref["ey"]),
+        "gN": rel(np.concatenate([got["gNx"], got["gNy"]]), np.concatenate([ref["gNx"], ref["gNy"]])),
+        "gW": rel(np.concatenate([got["gWx"], got["gWy"]]), np.concatenate([ref["gWx"], ref["gWy"]])),
+        "N": abs(got["rep"]["N"] - ref["N"]) / abs(ref["N"]),
+        "W": abs(got["rep"]["W"] - ref["W"]) / abs(ref["W"]),
+        "hpwl": abs(got["rep"]["hpwl"] - ref["hpwl"]) / abs(ref["hpwl"]),
+        "tau": abs(got["rep"]["tau"] - ref["tau"]) / max(abs(ref["tau"]), 1e-12),
+    }
+    limits = {"rho": TOL_RHO, "psi": tol_map, "ex": tol_map, "ey": tol_map, "gN": tol_map,
+              "gW": tol_map, "N": 2e-6, "W": 1e-6, "hpwl": 1e-6, "tau": 1e-5}
+    bad = {k: (errs[k], limits[k]) for k in errs if not errs[k] <= limits[k]}
+    assert not bad, f"parity failures {bad}; all {errs}"
+    return errs
+
+
+@pytest.mark.parametrize("name", ["tiny", "medium", "precision_sub"])
+@pytest.mark.parametrize("det", [0, 1])
+def test_eval_parity(F, name, det):
+    inst = synth.make_instance(name)
+    ref = oracle.eval_instance(inst, maps=True)
+    got = gpu_eval(F, inst, deterministic=det)
+    check_eval(got, ref)
+    assert got["rep"]["mov_area"] == pytest.approx(ref["total_mov_area"], rel=1e-12)
+
+
+def test_large_full_parity(F):
+    """The 210K-cell, 512x512 instance, every output compared."""
+    inst = synth.make_instance("large")
+    ref = oracle.eval_instance(inst, maps=True)
+    got = gpu_eval(F, inst)
+    check_eval(got, ref)
+
+
+def edge_instance():
+    """Cells on bin edges, on and beyond the region boundary, wider than a
+    tile, stacked in one bin; nets of degree 1, 2 and 50, coincident pins."""
+    rng = np.random.default_rng(7)
+    L, n = 128.0, 64
+    base = synth.make_instance("tiny")
+    m = base.m_mov
+    x = base.x.copy(); y = base.y.copy(); w = base.w.copy(); h = base.h.copy()
+    wb = L / n
+    x[:20] = np.arange(20) * wb + 0.5 * w[:20]          # left edge on a bin edge
+    y[:20] = 10.0 + 0.5
+    x[20:30] = -1.0; y[20:30] = 50.0                     # partly outside
+    x[30:35] = 200.0                                     # fully outside
+    w[35:40] = 40.0; x[35:40] = 64.0                     # wide cells
+    x[40:140] = 33.3; y[40:140] = 77.7                   # hot spot
+    x[140] = 0.5 * w[140]; y[140] = 0.5                  # corner
+    net_ptr = [0]
+    pc = []
+    for d in [1, 2, 50, 5, 2, 3]:
+        pc += list(rng.choice(m, d, replace=False)); net_ptr.append(len(pc))
+    pc += [41, 42, 43]; net_ptr.append(len(pc))           # coincident pins (hot spot)
+    pc = np.array(pc, np.int32)
+    dx = np.zeros(pc.size, np.float32); dy = np.zeros(pc.size, np.float32)
+    base.x, base.y, base.w, base.h = x, y, w, h
+    base.net_ptr = np.array(net_ptr, np.int32)
+    base.pin_cell, base.pin_dx, base.pin_dy = pc, dx, dy
+    return base
+
+
+def test_edge_cases_parity(F):
+    inst = edge_instance()
+    ref = oracle.eval_instance(inst, maps=True)
+    for det in (0, 1):
+        got = gpu_eval(F, inst, deterministic=det)
+        check_eval(got, ref)
+
+
+def test_bin_ranges_bit_exact(F):
+    import torch
+    for inst in (synth.make_instance("medium"), edge_instance()):
+        m = inst.m_mov
+        ref, pairs = oracle.bin_ranges(inst.region, inst.n, inst.x, inst.y, inst.w[:m], inst.h[:m])
+        with F.Problem(inst) as p:
+            rng_d = torch.zeros((m, 4), dtype=torch.int32, device="cuda")
+            got_pairs = F.fftpl_bin_ranges(p.h, cuda(inst.x), cuda(inst.y), rng_d)
+            got = rng_d.cpu().numpy()
+        assert np.array_equal(got, ref)
+        assert got_pairs == pairs
+
+
+def test_deterministic_map_bit_exact(F):
+    import torch
+    inst = synth.make_instance("precision_sub")
+    m = inst.m_mov
+    ref = oracle.overlap_map_q(inst.region, inst.n, inst.x, inst.y, inst.w[:m], inst.h[:m])
+    with F.Problem(inst, deterministic=1) as p:
+        F.fftpl_density(p.h, cuda(inst.x), cuda(inst.y))
+        got = F.fftpl_fields_q(p.h, inst.n).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_wa_alone(F):
+    import torch
+    inst = synth.make_instance("medium")
+    ref = oracle.wa(inst.net_ptr, inst.pin_cell, inst.pin_dx, inst.pin_dy, inst.m_mov,
+                    inst.x, inst.y, inst.gamma, inst.fix_x, inst.fix_y)
+    for det in (0, 1):
+        with F.Problem(inst, deterministic=det) as p:
+            gx = torch.empty(inst.m_mov, device="cuda"); gy = torch.empty_like(gx)
+            W = F.fftpl_wa(p.h, cuda(inst.x), cuda(inst.y), inst.gamma, gx, gy)
+            rep = F.fftpl_report(p.h)
+        assert abs(W - ref["W"]) / ref["W"] < 1e-6
+        assert abs(rep["hpwl"] - ref["hpwl"]) / ref["hpwl"] < 1e-6
+        assert rel(np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()]),
+                   np.concatenate([ref["gcx"], ref["gcy"]])) < TOL_MAP
+
+
+def test_adjoint_parity(F):
+    import torch
+    inst = synth.make_instance("medium")
+    ref = oracle.eval_instance(inst, maps=True)
+    m = inst.m_mov
+    ax, ay = oracle.adjoint(inst.region, inst.n, inst.x, inst.y, inst.w[:m], inst.h[:m], ref["psi"])
+    with F.Problem(inst) as p:
+        gx = torch.empty(m, device="cuda"); gy = torch.empty_like(gx)
+        N = F.fftpl_density_adjoint(p.h, cuda(inst.x), cuda(inst.y), gx, gy)
+    assert abs(N - ref["N"]) / ref["N"] < 2e-6
+    assert rel(np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()]), np.concatenate([ax, ay])) < TOL_MAP
+
+
+def test_precision_full_size_sampled(F):
+    """2.2M cells, 2048x2048 bins, in the launch configuration the benchmark
+    times: rho and grad W~ in full; psi, E at 64 sampled bins; grad N at 64
+    sampled cells (their touched bins' field from the oracle's series)."""
+    import torch
+    inst = synth.make_instance("precision")
+    n, m = inst.n, inst.m_mov
+    got = gpu_eval(F, inst)
+    fx = inst.fix_x; fy = inst.fix_y
+    rho, D, Fm = oracle.density(inst.region, n, inst.target_density, inst.x, inst.y,
+                                inst.w[:m], inst.h[:m], fx, fy, inst.w[m:], inst.h[m:])
+    assert rel(got["rho"], rho) < TOL_RHO
+    wa = oracle.wa(inst.net_ptr, inst.pin_cell, inst.pin_dx, inst.pin_dy, m, inst.x, inst.y,
+                   inst.gamma, fx, fy)
+    assert abs(got["rep"]["W"] - wa["W"]) / wa["W"] < 1e-6
+    assert abs(got["rep"]["hpwl"] - wa["hpwl"]) / wa["hpwl"] < 1e-6
+    assert rel(np.concatenate([got["gWx"], got["gWy"]]), np.concatenate([wa["gcx"], wa["gcy"]])) < TOL_MAP
+    a = oracle.dct_coeffs(rho)
+    rng = np.random.default_rng(0)
+    xs = rng.integers(0, n, 64); ys = rng.integers(0, n, 64)
+    psi, ex, ey = oracle.potential_at(a, inst.region[2] - inst.region[0],
+                                      inst.region[3] - inst.region[1], xs, ys)
+    assert rel(got["psi"][ys, xs], psi) < TOL_MAP
+    assert rel(got["ex"][ys, xs], ex) < TOL_MAP
+    assert rel(got["ey"][ys, xs], ey) < TOL_MAP
+    # grad N at sampled cells
+    cells = rng.choice(m, 64, replace=False)
+    rr, _ = oracle.bin_ranges(inst.region, n, inst.x[cells], inst.y[cells], inst.w[cells], inst.h[cells])
+    bx, by = [], []
+    for (ilo, ihi, jlo, jhi) in rr:
+        for j in range(jlo, jhi + 1):
+            for k in range(ilo, ihi + 1):
+                bx.append(k); by.append(j)
+    _, exs, eys = oracle.potential_at(a, inst.region[2], inst.region[3], bx, by)
+    EX = np.zeros((n, n)); EY = np.zeros((n, n))
+    EX[by, bx] = exs; EY[by, bx] = eys
+    gx, gy = oracle.gather(inst.region, n, inst.x[cells], inst.y[cells], inst.w[cells],
+                           inst.h[cells], EX, EY)
+    assert rel(np.concatenate([got["gNx"][cells], got["gNy"][cells]]), np.concatenate([gx, gy])) < TOL_MAP
+    # energy by Parseval from the oracle's coefficients
+    eps = np.where(np.arange(n) == 0, 1.0, 2.0)
+    Lx = inst.region[2] - inst.region[0]
+    wu = np.pi * np.arange(n) / Lx
+    W2 = wu[:, None] ** 2 + wu[None, :] ** 2
+    W2[0, 0] = np.inf
+    Nref = 0.5 * inst.wb * inst.hb * np.sum(n * n / (eps[:, None] * eps[None, :]) * a * a / W2)
+    assert abs(got["rep"]["N"] - Nref) / Nref < 2e-6
+
+
+def test_graphs_and_host_path(F):
+    import torch
+    inst = synth.make_instance("medium")
+    ref = oracle.eval_instance(inst, maps=True)
+    with F.Problem(inst, use_graphs=1, deterministic=1) as p:
+        xd, yd = cuda(inst.x), cuda(inst.y)
+        outs = []
+        for _ in range(3):
+            g = [torch.empty_like(xd) for _ in range(4)]
+            rep = F.fftpl_eval(p.h, xd, yd, inst.gamma, *g)
+            outs.append((rep, [t.cpu().numpy() for t in g]))
+        # replays of the same graph are bit-identical in deterministic mode
+        for rep, g in outs[1:]:
+            assert all(np.array_equal(a, b) for a, b in zip(g, outs[0][1]))
+        n_launch = F.fftpl_launch_count(p.h)
+        assert n_launch >= 3 * 5
+        hx = torch.from_numpy(inst.x).pin_memory(); hy = torch.from_numpy(inst.y).pin_memory()
+        hg = [torch.empty(inst.m_mov, dtype=torch.float32).pin_memory() for _ in range(4)]
+        rep_h = F.fftpl_eval_host(p.h, hx, hy, inst.gamma, *hg)
+        assert all(np.array_equal(a.numpy(), b) for a, b in zip(hg, outs[0][1]))
+    got = {"rep": rep_h, "gNx": hg[0].numpy(), "gNy": hg[1].numpy(), "gWx": hg[2].numpy(),
+           "gWy": hg[3].numpy(), "rho": ref["rho"], "psi": ref["psi"], "ex": ref["ex"], "ey": ref["ey"]}
+    check_eval(got, ref)
+
+
+def test_max_grid_properties(F):
+    """n = 4096 (the largest grid): a uniform covering density gives psi = E = 0;
+    the potential has zero sum; N >= 0."""
+    import torch
+    inst = synth.make_instance("tiny")
+    inst.n = 4096
+    inst.region = (0.0, 0.0, 2048.0, 2048.0)
+    m = 4
+    inst.m_mov = m
+    inst.w = np.full(m, 1024.0, np.float32); inst.h = np.full(m, 1024.0, np.float32)
+    inst.x = np.array([512, 1536, 512, 1536], np.float32)
+    inst.y = np.array([512, 512, 1536, 1536], np.float32)
+    inst.net_ptr = np.array([0, 2], np.int32); inst.pin_cell = np.array([0, 3], np.int32)
+    inst.pin_dx = np.zeros(2, np.float32); inst.pin_dy = np.zeros(2, np.float32)
+    inst.fix_x = np.zeros(0, np.float32); inst.fix_y = np.zeros(0, np.float32)
+    got = gpu_eval(F, inst, gamma=2.0)
+    assert np.abs(got["rho"] - 1.0).max() < 1e-6
+    assert np.abs(got["psi"]).max() < 1e-6 and np.abs(got["ex"]).max() < 1e-6
+    # one cell in one quadrant: zero-sum psi and positive energy
+    inst.x = inst.x[:1]; inst.y = inst.y[:1]; inst.w = inst.w[:1]; inst.h = inst.h[:1]; inst.m_mov = 1
+    inst.pin_cell = np.array([0, 0], np.int32)
+    got = gpu_eval(F, inst, gamma=2.0)
+    assert abs(got["psi"].astype(np.float64).sum()) < 1e-5 * np.abs(got["psi"]).sum()
+    assert got["rep"]["N"] > 0
