@@ -210,8 +210,9 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
 
 // ------------------------------------------------- pass 2: columns
 // CTA: 4 rows u of T1.  Forward DCT-II along y, spectral divide, energy,
-// then per row one complex IFFT carrying P (cosine sum) in the real part and
-// R (sine sum, via reversed coefficients) in the imaginary part.
+// then the inverse sums along y: P (cosine sum of Psi) and R (sine sum of
+// w_v Psi, via reversed coefficients).  Each complex IFFT carries the same
+// quantity for two rows (P with P, R with R), so both parts share a scale.
 template <int LOGN>
 __global__ void __launch_bounds__(kSpecThreads)
 k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__ RT,
@@ -233,7 +234,7 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
     constexpr int HALF = N / 2 + 1;
     constexpr int ITEMS = (NB / 2) * HALF;
     constexpr int PI = (ITEMS + T - 1) / T;
-    float2 zo[PI][4];   // [row a at v, row a at N-v, row b at v, row b at N-v]
+    float2 zo[PI][4];   // [P at v, P at N-v, R at v, R at N-v], rows packed re/im
     int where[PI];
     const float invn2 = 1.0f / ((float)N * (float)N);
     dfloat energy = df_zero();
@@ -249,48 +250,47 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
             float2 v1 = make_float2(0.5f * (zu.x + zn.x), 0.5f * (zu.y - zn.y));
             float2 v2 = make_float2(0.5f * (zu.y + zn.y), 0.5f * (zn.x - zu.x));
             float2 p = ph[v], q = ph[N - v];
-            // B[row][v] (unnormalised DCT-II along y)
+            // B[row][v], B[row][N-v] (unnormalised DCT-II along y)
             float B[2][2];
             B[0][0] = v1.x * p.x - v1.y * p.y;
             B[1][0] = v2.x * p.x - v2.y * p.y;
             B[0][1] = v1.x * q.x + v1.y * q.y;
             B[1][1] = v2.x * q.x + v2.y * q.y;
             float wv = pi_ly * (float)v, wvn = pi_ly * (float)(N - v);
+            float ev = (v == 0) ? 1.0f : 2.0f;
+            bool has_n = (v > 0 && v < N / 2);
+            // halved inverse coefficients per row: c1 (P) and c2 (R) at v and N-v
+            float c1v[2], c1n[2], c2v[2], c2n[2];
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
                 int u = u0 + 2 * f + rr;
                 float wu = pi_lx * (float)u;
                 float eu = (u == 0) ? 1.0f : 2.0f;
-                // Psi at v and at N - v (v = 0 has no partner: coefficient index N is absent)
-                float ev = (v == 0) ? 1.0f : 2.0f;
-                float d0 = wu * wu + wv * wv;
                 float a0 = eu * ev * invn2 * B[rr][0];
-                float psi0 = (u == 0 && v == 0) ? 0.0f : a0 / d0;
+                float psi0 = (u == 0 && v == 0) ? 0.0f : a0 / (wu * wu + wv * wv);
                 float psin = 0.0f;
-                bool has_n = (v > 0 && v < N / 2);
                 if (has_n) {
-                    float dn = wu * wu + wvn * wvn;
                     float an = eu * 2.0f * invn2 * B[rr][1];
-                    psin = an / dn;
+                    psin = an / (wu * wu + wvn * wvn);
                     energy = df_add(energy, B[rr][1] * psin);
                 }
                 energy = df_add(energy, B[rr][0] * psi0);
-                // inverse inputs: c1 = Psi (cosine sum), c2[v'] = s[N - v'] with
-                // s[v] = w_v Psi[v] (sine sum), c2[0] = 0
-                // halved coefficients ct[k] = c[k] / 2 for k >= 1
-                float c1v = (v == 0) ? psi0 : 0.5f * psi0;
-                float c1n = 0.5f * psin;                              // index N - v (0 if v == 0)
-                float c2v = (v == 0) ? 0.0f : 0.5f * wvn * psin;      // c2[v] = s[N-v]
-                float c2n = (v == 0) ? 0.0f : 0.5f * wv * psi0;       // c2[N-v] = s[v]
+                // P: cosine sum of Psi.  R: cosine sum of c2[v'] = s[N-v'],
+                // s[v] = w_v Psi[v], c2[0] = 0; then R = (-1)^y * that.
+                c1v[rr] = (v == 0) ? psi0 : 0.5f * psi0;
+                c1n[rr] = 0.5f * psin;
+                c2v[rr] = (v == 0) ? 0.0f : 0.5f * wvn * psin;
+                c2n[rr] = (v == 0) ? 0.0f : 0.5f * wv * psi0;
                 if (v == N / 2) {
-                    // partner of N/2 is itself: c1[N/2] = Psi(N/2), c2[N/2] = s[N/2]
-                    c1n = c1v;
-                    c2v = 0.5f * wv * psi0;
-                    c2n = c2v;
+                    c1n[rr] = c1v[rr];
+                    c2v[rr] = 0.5f * wv * psi0;
+                    c2n[rr] = c2v[rr];
                 }
-                zo[i][2 * rr + 0] = pack_inv(c1v, c1n, c2v, c2n, p);
-                zo[i][2 * rr + 1] = pack_inv(c1n, c1v, c2n, c2v, q);
             }
+            zo[i][0] = pack_inv(c1v[0], c1n[0], c1v[1], c1n[1], p);
+            zo[i][1] = pack_inv(c1n[0], c1v[0], c1n[1], c1v[1], q);
+            zo[i][2] = pack_inv(c2v[0], c2n[0], c2v[1], c2n[1], p);
+            zo[i][3] = pack_inv(c2n[0], c2v[0], c2n[1], c2v[1], q);
             where[i] = f * HALF + v;
         }
     }
@@ -300,30 +300,32 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
     for (int i = 0; i < PI; ++i) {
         if (where[i] < 0) continue;
         int f = where[i] / HALF, v = where[i] % HALF;
-        for (int rr = 0; rr < 2; ++rr) {
-            float2* row = sm + (2 * f + rr) * N;
-            row[v & (N - 1)] = zo[i][2 * rr + 0];
-            if (v > 0 && v < N / 2) row[N - v] = zo[i][2 * rr + 1];
+        float2* rowP = sm + (2 * f) * N;
+        float2* rowR = sm + (2 * f + 1) * N;
+        rowP[v & (N - 1)] = zo[i][0];
+        rowR[v & (N - 1)] = zo[i][2];
+        if (v > 0 && v < N / 2) {
+            rowP[N - v] = zo[i][1];
+            rowR[N - v] = zo[i][3];
         }
     }
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, true);
-    // unshuffle: y even <- k = y/2, y odd <- k = N-1-(y-1)/2;  P = Re, R = (-1)^y Im
+    // unshuffle: y even <- k = y/2, y odd <- k = N-1-(y-1)/2
     for (int y = threadIdx.x; y < N; y += T) {
         int k = mk_src(y, N);
         float sgn = (y & 1) ? -1.0f : 1.0f;
-        float4 pv, rv;
-        float2 z0 = sm[0 * N + k], z1 = sm[1 * N + k], z2 = sm[2 * N + k], z3 = sm[3 * N + k];
-        pv = make_float4(z0.x, z1.x, z2.x, z3.x);
-        rv = make_float4(sgn * z0.y, sgn * z1.y, sgn * z2.y, sgn * z3.y);
-        *reinterpret_cast<float4*>(PT + (size_t)y * N + u0) = pv;
-        *reinterpret_cast<float4*>(RT + (size_t)y * N + u0) = rv;
+        float2 p0 = sm[0 * N + k], r0 = sm[1 * N + k], p1 = sm[2 * N + k], r1 = sm[3 * N + k];
+        *reinterpret_cast<float4*>(PT + (size_t)y * N + u0) = make_float4(p0.x, p0.y, p1.x, p1.y);
+        *reinterpret_cast<float4*>(RT + (size_t)y * N + u0) =
+            make_float4(sgn * r0.x, sgn * r0.y, sgn * r1.x, sgn * r1.y);
     }
 }
 
 // ------------------------------------------------- pass 3: inverse rows
-// CTA: 4 rows y.  Round A: psi (cosine sum of P) + i E_y (cosine sum of R),
-// one IFFT per row.  Round B: E_x (sine sum of w_u P) for rows pairwise.
+// CTA: 4 rows y.  Round A: psi (cosine sum of P) for two rows per IFFT and
+// E_y (cosine sum of R) for two rows per IFFT.  Round B: E_x (sine sum of
+// w_u P) for two rows per IFFT.
 template <int LOGN>
 __global__ void __launch_bounds__(kSpecThreads)
 k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __restrict__ psi,
@@ -336,28 +338,35 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __
     constexpr int HALF = N / 2 + 1;
     extern __shared__ float2 sm[];
     const int y0 = blockIdx.x * ROWS;
-    // round A
-    for (int idx = threadIdx.x; idx < ROWS * HALF; idx += T) {
-        int r = idx / HALF, u = idx % HALF;
-        const float* P = PT + (size_t)(y0 + r) * N;
-        const float* R = RT + (size_t)(y0 + r) * N;
-        float pu = P[u & (N - 1)], ru = R[u & (N - 1)];
-        float pn = (u > 0) ? P[N - u] : 0.0f, rn = (u > 0) ? R[N - u] : 0.0f;
-        float c1u = (u == 0) ? pu : 0.5f * pu, c2u = (u == 0) ? ru : 0.5f * ru;
-        float c1n = 0.5f * pn, c2n = 0.5f * rn;
-        if (u == N / 2) { c1n = c1u; c2n = c2u; }
-        float2* row = sm + r * N;
-        row[u & (N - 1)] = pack_inv(c1u, c1n, c2u, c2n, ph[u]);
-        if (u > 0 && u < N / 2) row[N - u] = pack_inv(c1n, c1u, c2n, c2u, ph[N - u]);
+    // round A: buffer 2f holds psi of rows (2f, 2f+1), buffer 2f+1 holds E_y
+    for (int idx = threadIdx.x; idx < (ROWS / 2) * HALF; idx += T) {
+        int f = idx / HALF, u = idx % HALF;
+        int un = (N - u) & (N - 1);
+        const float* src[2] = {PT, RT};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float* A = src[q] + (size_t)(y0 + 2 * f) * N;
+            const float* Bq = A + N;
+            float au = A[u & (N - 1)], bu = Bq[u & (N - 1)];
+            float an = (u > 0) ? A[un] : 0.0f, bn = (u > 0) ? Bq[un] : 0.0f;
+            float cau = (u == 0) ? au : 0.5f * au, cbu = (u == 0) ? bu : 0.5f * bu;
+            float can = 0.5f * an, cbn = 0.5f * bn;
+            if (u == N / 2) { can = cau; cbn = cbu; }
+            float2* row = sm + (2 * f + q) * N;
+            row[u & (N - 1)] = pack_inv(cau, can, cbu, cbn, ph[u]);
+            if (u > 0 && u < N / 2) row[N - u] = pack_inv(can, cau, cbn, cbu, ph[N - u]);
+        }
     }
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, true);
     for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
         int r = idx >> LOGN, x = idx & (N - 1);
-        float2 z = sm[r * N + mk_src(x, N)];
+        int f = r >> 1;
+        int k = mk_src(x, N);
+        float2 zp = sm[(2 * f) * N + k], ze = sm[(2 * f + 1) * N + k];
         size_t b = (size_t)(y0 + r) * N + x;
-        psi[b] = z.x;
-        ey[b] = z.y;
+        psi[b] = (r & 1) ? zp.y : zp.x;
+        ey[b] = (r & 1) ? ze.y : ze.x;
     }
     __syncthreads();
     // round B: E_x rows (2 per buffer).  c[u'] = s[N-u'] (u' >= 1), c[0] = 0,

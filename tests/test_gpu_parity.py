@@ -277,7 +277,12 @@ def test_max_grid_properties(F):
     inst.fix_x = np.zeros(0, np.float32); inst.fix_y = np.zeros(0, np.float32)
     got = gpu_eval(F, inst, gamma=2.0)
     assert np.abs(got["rho"] - 1.0).max() < 1e-6
-    assert np.abs(got["psi"]).max() < 1e-6 and np.abs(got["ex"]).max() < 1e-6
+    # natural scales of the solution for rho ~ 1: psi ~ (L/pi)^2, E ~ L/pi;
+    # float32 rounding leaves only noise far below them
+    L = 2048.0
+    assert np.abs(got["psi"]).max() < 1e-6 * (L / np.pi) ** 2
+    assert np.abs(got["ex"]).max() < 1e-6 * (L / np.pi)
+    assert np.abs(got["ey"]).max() < 1e-6 * (L / np.pi)
     # one cell in one quadrant: zero-sum psi and positive energy
     inst.x = inst.x[:1]; inst.y = inst.y[:1]; inst.w = inst.w[:1]; inst.h = inst.h[:1]; inst.m_mov = 1
     inst.pin_cell = np.array([0, 0], np.int32)
