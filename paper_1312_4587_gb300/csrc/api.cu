@@ -191,17 +191,15 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
                           float* gNx, float* gNy, float* gWx, float* gWy) {
     cudaStream_t s = c.stream;
     size_t nn = (size_t)c.n * c.n;
-    CK(cudaMemsetAsync(c.acc, 0, ACC_COUNT * sizeof(double), s));
+    CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
     bool dens = (what & EV_DENSITY) != 0, wa = (what & EV_WA) != 0;
     if (wa) {
         CK(cudaEventRecord(c.ev_fork, s));
         CK(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
         Stage st(c, 4, c.side);
-        if (!c.opt.deterministic) {
-            CK(cudaMemsetAsync(gWx, 0, (size_t)c.m_mov * sizeof(float), c.side));
-            CK(cudaMemsetAsync(gWy, 0, (size_t)c.m_mov * sizeof(float), c.side));
-        }
-        CK(launch_wa(c, x, y, gamma, gWx, gWy, c.side));
+        if (!c.opt.deterministic)
+            CK(cudaMemsetAsync(c.gW2, 0, (size_t)c.m_mov * sizeof(float2), c.side));
+        CK(launch_wa(c, x, y, gamma, c.side));
     }
     if (wa) CK(cudaEventRecord(c.ev_join, c.side));
     if (dens) {
@@ -226,23 +224,31 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
         }
     }
     c.rho_valid = false;
+    c.split_valid = false;
     c.fields_valid = dens;
     return FFTPL_OK;
 }
 
+// total of one striped accumulator
+double acc_total(const double* acc, int q) {
+    double s = 0.0;
+    for (int k = 0; k < kAccStripes; ++k) s += acc[k * kAccStride + q];
+    return s;
+}
+
 void fill_report(const Ctx& c, const double* acc, fftpl_eval_report* rep) {
-    rep->N = 0.5 * c.Ab * acc[ACC_N];
-    rep->W = acc[ACC_W];
-    rep->hpwl = acc[ACC_HPWL];
-    rep->tau = c.mov_area > 0 ? acc[ACC_TAU] / c.mov_area : 0.0;
-    rep->gN_l1 = acc[ACC_GN_L1];
-    rep->gW_l1 = acc[ACC_GW_L1];
-    rep->charge = acc[ACC_CHARGE];
+    rep->N = 0.5 * c.Ab * acc_total(acc, ACC_N);
+    rep->W = acc_total(acc, ACC_W);
+    rep->hpwl = acc_total(acc, ACC_HPWL);
+    rep->tau = c.mov_area > 0 ? acc_total(acc, ACC_TAU) / c.mov_area : 0.0;
+    rep->gN_l1 = acc_total(acc, ACC_GN_L1);
+    rep->gW_l1 = acc_total(acc, ACC_GW_L1);
+    rep->charge = acc_total(acc, ACC_CHARGE);
     rep->mov_area = c.mov_area;
 }
 
 fftpl_status read_report(Ctx& c, fftpl_eval_report* rep) {
-    CK(cudaMemcpyAsync(c.acc_host, c.acc, ACC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(c.acc_host, c.acc, kAccDoubles * sizeof(double), cudaMemcpyDeviceToHost,
                        c.stream));
     CK(cudaStreamSynchronize(c.stream));
     if (rep) fill_report(c, c.acc_host, rep);
@@ -279,6 +285,95 @@ void fftpl_debug_fail_alloc_after(int32_t k) { g_fail_after.store(k > 0 ? k : 0)
 const char* fftpl_last_error(fftpl_t h) {
     if (!h) return g_create_error.c_str();
     return h->last_error.c_str();
+}
+
+// Re-lays the netlist for the WA kernel: nets of degree >= 2 grouped by
+// degree (original order kept within a degree) into slabs of up to 32 nets;
+// pin k of slab net j at slot base + 32 k + j.  Degree-1 nets have no
+// wirelength and are left out.  In deterministic mode also builds the
+// cell-ordered pin slots (pins of each movable cell contiguous, in net order).
+static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins* pins) {
+    const int32_t* np = nets->net_ptr;
+    int maxd = 0;
+    for (int e = 0; e < c.E; ++e) maxd = std::max(maxd, np[e + 1] - np[e]);
+    std::vector<std::vector<int32_t>> by_deg((size_t)maxd + 1);
+    for (int e = 0; e < c.E; ++e) {
+        int d = np[e + 1] - np[e];
+        if (d >= 2) by_deg[d].push_back(e);
+    }
+    std::vector<int4> slabs;
+    int64_t slots = 0;
+    for (int d = 2; d <= maxd; ++d) {
+        const auto& v = by_deg[d];
+        for (size_t s0 = 0; s0 < v.size(); s0 += 32) {
+            int cnt = (int)std::min<size_t>(32, v.size() - s0);
+            slabs.push_back(make_int4((int)slots, d, cnt, 0));
+            slots += 32LL * d;
+        }
+    }
+    if (slots > 0x7fffffffLL) return set_err(c, FFTPL_EINVAL, "too many pins");
+    c.nslabs = (int)slabs.size();
+    c.slab_slots = slots;
+    // cell-ordered slots for the deterministic reduction
+    std::vector<int32_t> cslot;
+    if (c.opt.deterministic) {
+        std::vector<int32_t> cnt((size_t)c.m_mov + 1, 0);
+        for (int e = 0; e < c.E; ++e) {
+            if (np[e + 1] - np[e] < 2) continue;
+            for (int p = np[e]; p < np[e + 1]; ++p)
+                if (pins->pin_cell[p] < c.m_mov) cnt[pins->pin_cell[p] + 1]++;
+        }
+        for (int i = 0; i < c.m_mov; ++i) cnt[i + 1] += cnt[i];
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        cslot.assign((size_t)c.P, -1);
+        for (int e = 0; e < c.E; ++e) {
+            if (np[e + 1] - np[e] < 2) continue;
+            for (int p = np[e]; p < np[e + 1]; ++p) {
+                int cc = pins->pin_cell[p];
+                if (cc < c.m_mov) cslot[p] = fill[cc]++;
+            }
+        }
+        CK(cudaMemcpy(c.cell_pin_ptr, cnt.data(), cnt.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice));
+    }
+    std::vector<int32_t> spc((size_t)std::max<int64_t>(slots, 1), 0), sslot;
+    std::vector<float> sdx((size_t)std::max<int64_t>(slots, 1), 0.0f), sdy(sdx.size(), 0.0f);
+    if (c.opt.deterministic) sslot.assign(spc.size(), -1);
+    {
+        size_t si = 0;
+        for (int d = 2; d <= maxd; ++d) {
+            const auto& v = by_deg[d];
+            for (size_t s0 = 0; s0 < v.size(); s0 += 32, ++si) {
+                const int4& sl = slabs[si];
+                for (int j = 0; j < sl.z; ++j) {
+                    int e = v[s0 + j];
+                    for (int k = 0; k < d; ++k) {
+                        int p = np[e] + k;
+                        size_t slot = (size_t)sl.x + 32 * (size_t)k + j;
+                        spc[slot] = pins->pin_cell[p];
+                        sdx[slot] = pins->dx[p];
+                        sdy[slot] = pins->dy[p];
+                        if (c.opt.deterministic) sslot[slot] = cslot[p];
+                    }
+                }
+            }
+        }
+    }
+    TRY(dalloc(c, &c.slabs, std::max<size_t>(slabs.size(), 1)));
+    TRY(dalloc(c, &c.pin_cell, spc.size()));
+    TRY(dalloc(c, &c.pin_dx, sdx.size()));
+    TRY(dalloc(c, &c.pin_dy, sdy.size()));
+    if (!slabs.empty())
+        CK(cudaMemcpy(c.slabs, slabs.data(), slabs.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.pin_cell, spc.data(), spc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.pin_dx, sdx.data(), sdx.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.pin_dy, sdy.data(), sdy.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (c.opt.deterministic) {
+        TRY(dalloc(c, &c.pin_slot, sslot.size()));
+        CK(cudaMemcpy(c.pin_slot, sslot.data(), sslot.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice));
+    }
+    return FFTPL_OK;
 }
 
 static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const fftpl_cells* cells,
@@ -324,7 +419,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     CK(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
-    CK(cudaMallocHost((void**)&c.acc_host, ACC_COUNT * sizeof(double)));
+    CK(cudaMallocHost((void**)&c.acc_host, kAccDoubles * sizeof(double)));
 
     size_t nn = (size_t)n * n;
     int mt = c.m_mov + c.m_fix;
@@ -339,20 +434,15 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     TRY(dalloc(c, &c.PT, nn));
     TRY(dalloc(c, &c.RT, nn));
     TRY(dalloc(c, &c.psi, nn));
-    TRY(dalloc(c, &c.ex, nn));
-    TRY(dalloc(c, &c.ey, nn));
+    TRY(dalloc(c, &c.E2, nn));
     TRY(dalloc(c, &c.tw, n));
     TRY(dalloc(c, &c.ph, n + 1));
-    TRY(dalloc(c, &c.net_ptr, (size_t)c.E + 1));
-    TRY(dalloc(c, &c.pin_cell, c.P));
-    TRY(dalloc(c, &c.pin_dx, c.P));
-    TRY(dalloc(c, &c.pin_dy, c.P));
-    TRY(dalloc(c, &c.acc, ACC_COUNT));
+    TRY(dalloc(c, &c.acc, kAccDoubles));
     TRY(dalloc(c, &c.err, 1));
     TRY(dalloc(c, &c.gN, 2 * (size_t)c.m_mov));
     TRY(dalloc(c, &c.gW, 2 * (size_t)c.m_mov));
+    TRY(dalloc(c, &c.gW2, (size_t)c.m_mov));
     if (c.opt.deterministic) {
-        TRY(dalloc(c, &c.pin_slot, c.P));
         TRY(dalloc(c, &c.cell_pin_ptr, (size_t)c.m_mov + 1));
         TRY(dalloc(c, &c.gpin, c.P));
     }
@@ -362,13 +452,6 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     if (c.m_fix) {
         CK(cudaMemcpyAsync(c.fix_x, cells->fix_x, c.m_fix * sizeof(float), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(c.fix_y, cells->fix_y, c.m_fix * sizeof(float), cudaMemcpyHostToDevice, s));
-    }
-    CK(cudaMemcpyAsync(c.net_ptr, nets->net_ptr, ((size_t)c.E + 1) * sizeof(int32_t),
-                       cudaMemcpyHostToDevice, s));
-    if (c.P) {
-        CK(cudaMemcpyAsync(c.pin_cell, pins->pin_cell, c.P * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(c.pin_dx, pins->dx, c.P * sizeof(float), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(c.pin_dy, pins->dy, c.P * sizeof(float), cudaMemcpyHostToDevice, s));
     }
     // transform tables (FP64 on the host, rounded once): FFT twiddles
     // exp(-2 pi i k / n) and cosine-transform twiddles exp(-i pi u / 2n)
@@ -383,25 +466,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     }
     CK(cudaMemcpyAsync(c.tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.ph, ph.data(), (n + 1) * sizeof(float2), cudaMemcpyHostToDevice, s));
-    // deterministic pin-to-cell layout: pins of each movable cell made
-    // contiguous (in net order); pin_slot maps a pin to its slot
-    if (c.opt.deterministic) {
-        std::vector<int32_t> cnt((size_t)c.m_mov + 1, 0), slot(c.P);
-        for (long long p = 0; p < c.P; ++p)
-            if (pins->pin_cell[p] < c.m_mov) cnt[pins->pin_cell[p] + 1]++;
-        for (int i = 0; i < c.m_mov; ++i) cnt[i + 1] += cnt[i];
-        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
-        for (long long p = 0; p < c.P; ++p) {
-            int cc = pins->pin_cell[p];
-            slot[p] = cc < c.m_mov ? fill[cc]++ : -1;
-        }
-        CK(cudaMemcpyAsync(c.cell_pin_ptr, cnt.data(), cnt.size() * sizeof(int32_t),
-                           cudaMemcpyHostToDevice, s));
-        if (c.P)
-            CK(cudaMemcpyAsync(c.pin_slot, slot.data(), c.P * sizeof(int32_t),
-                               cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));  // host vectors go out of scope
-    }
+    TRY(build_slabs(c, nets, pins));
     // fixed-cell map M = rho_t F (Section III-B), order-free int64 sums
     {
         long long* q = nullptr;
@@ -544,6 +609,7 @@ fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma, 
         c.launches += c.graph_nkernels;
         c.fields_valid = true;
         c.rho_valid = false;
+        c.split_valid = false;
     } else {
         TRY(enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy));
     }
@@ -593,8 +659,18 @@ fftpl_status fftpl_fields(fftpl_t h, const float** rho, const float** psi, const
         *rho = c.rho;
     }
     if (psi) *psi = c.psi;
-    if (ex) *ex = c.ex;
-    if (ey) *ey = c.ey;
+    if (ex || ey) {
+        if (!c.ex) {
+            TRY(dalloc(c, &c.ex, (size_t)c.n * c.n));
+            TRY(dalloc(c, &c.ey, (size_t)c.n * c.n));
+        }
+        if (!c.split_valid) {
+            CK(launch_split_field(c, c.stream));
+            c.split_valid = true;
+        }
+        if (ex) *ex = c.ex;
+        if (ey) *ey = c.ey;
+    }
     CK(cudaStreamSynchronize(c.stream));
     return FFTPL_OK;
 }
@@ -614,12 +690,12 @@ fftpl_status fftpl_bin_ranges(fftpl_t h, const float* x, const float* y, int32_t
     if (!h) return FFTPL_EINVAL;
     Ctx& c = *h;
     if (c.m_mov > 0 && (!x || !y || !ranges)) return set_err(c, FFTPL_EINVAL, "null argument");
-    CK(cudaMemsetAsync(c.acc, 0, ACC_COUNT * sizeof(double), c.stream));
-    CK(launch_bin_ranges(c, x, y, ranges, c.acc + ACC_CHARGE, c.stream));
-    CK(cudaMemcpyAsync(c.acc_host, c.acc, ACC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+    CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), c.stream));
+    CK(launch_bin_ranges(c, x, y, ranges, c.stream));
+    CK(cudaMemcpyAsync(c.acc_host, c.acc, kAccDoubles * sizeof(double), cudaMemcpyDeviceToHost,
                        c.stream));
     CK(cudaStreamSynchronize(c.stream));
-    if (pairs) *pairs = (int64_t)llround(c.acc_host[ACC_CHARGE]);
+    if (pairs) *pairs = (int64_t)llround(acc_total(c.acc_host, ACC_CHARGE));
     return FFTPL_OK;
 }
 
@@ -657,7 +733,7 @@ fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
     if (c.opt.gamma_fixed <= 0.0) {
         // gamma_0 from the overflow at the start
         size_t nn = (size_t)c.n * c.n;
-        CK(cudaMemsetAsync(c.acc, 0, ACC_COUNT * sizeof(double), s));
+        CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
         if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
         else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
         CK(launch_scatter(c, c.v, c.v + c.m_mov, c.w, c.h, c.m_mov, c.D, c.Dq, s));
@@ -674,16 +750,14 @@ static fftpl_status enqueue_iteration(Ctx& c) {
     size_t nn = (size_t)c.n * c.n;
     const float* vx = c.v;
     const float* vy = c.v + c.m_mov;
-    float* gWx = c.gW;
-    float* gWy = c.gW + c.m_mov;
-    CK(cudaMemsetAsync(c.acc, 0, ACC_COUNT * sizeof(double), s));
+    CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
     CK(cudaEventRecord(c.ev_fork, s));
     CK(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
     {
         Stage st(c, 4, c.side);
         if (!c.opt.deterministic)
-            CK(cudaMemsetAsync(c.gW, 0, 2 * (size_t)c.m_mov * sizeof(float), c.side));
-        CK(launch_wa_impl(c, vx, vy, 1.0f, c.ctrl + C_GAMMA, gWx, gWy, c.ctrl + C_DONE, c.side));
+            CK(cudaMemsetAsync(c.gW2, 0, (size_t)c.m_mov * sizeof(float2), c.side));
+        CK(launch_wa_impl(c, vx, vy, 1.0f, c.ctrl + C_GAMMA, c.ctrl + C_DONE, c.side));
     }
     CK(cudaEventRecord(c.ev_join, c.side));
     {
@@ -743,6 +817,7 @@ fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32
     }
     c.fields_valid = true;
     c.rho_valid = false;
+    c.split_valid = false;
     return FFTPL_OK;
 }
 

@@ -8,9 +8,11 @@
 //   spectral        T1 [u][y]  (rows transformed along x, stored transposed)
 //                   PT [y][u], RT [y][u]  (columns transformed and inverted)
 //                   psi, ex, ey [y][x], rho [y][x] (formed on demand)
-//   nets/pins       net_ptr (E+1), pin_cell, pin_dx, pin_dy (P, net order)
-//                   pin_slot (P), cell_pin_ptr (m_mov+1), gpin (P float2) for
-//                   the deterministic pin-to-cell reduction
+//   nets/pins       slabs of nets of equal degree; pin_cell, pin_dx, pin_dy,
+//                   pin_slot in slab order (slot base + 32 k + lane);
+//                   cell_pin_ptr (m_mov+1), gpin (float2 per pin) for the
+//                   deterministic pin-to-cell reduction; gW2 (float2, m_mov)
+//                   the atomic one
 //   accumulators    acc[ACC_*] doubles, err word
 #pragma once
 
@@ -46,6 +48,14 @@ enum {
     ACC_STEPMAX,    // max |u_{k+1} - v_k|
     ACC_COUNT
 };
+
+// The FP64 sums are striped: a block adds its total to stripe
+// (blockIdx & 31), one 128-byte line of kAccStride doubles per stripe, so no
+// single address takes every block's atomic; readers add the stripes.
+constexpr int kAccStripes = 32;
+constexpr int kAccStride = 16;
+constexpr int kAccDoubles = kAccStripes * kAccStride;
+static_assert(ACC_COUNT <= kAccStride, "accumulator stripe too small");
 
 // device error word bits
 enum { ERR_TIMEOUT = 1, ERR_BOUNDS = 2 };
@@ -113,6 +123,53 @@ __device__ __forceinline__ float ov_len(float lo, float step, int k, float a, fl
     return fmaxf(v, 0.0f);
 }
 
+// Field gather of one cell: sum_b ov(i,b) E2[b] over its bin span, E2 the
+// interleaved (E_x, E_y) map.  Spans of at most 2 rows x 4 columns (nearly
+// every cell) issue all their loads at once, predicated, before any use.
+__device__ __forceinline__ float2 gather_span(const Grid& g, const Span& s,
+                                              const float2* __restrict__ E2) {
+    const int nr = s.jhi - s.jlo + 1, nc = s.ihi - s.ilo + 1;
+    float sx = 0.0f, sy = 0.0f;
+    if (nr <= 0 || nc <= 0) return make_float2(0.0f, 0.0f);
+    if (nr <= 2 && nc <= 4) {
+        float2 e[2][4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int j = min(s.jlo + a, s.jhi);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int k = min(s.ilo + b, s.ihi);
+                e[a][b] = (a < nr && b < nc) ? __ldg(E2 + (size_t)j * g.n + k)
+                                             : make_float2(0.0f, 0.0f);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a >= nr) break;
+            float oy = ov_len(g.y0, g.hb, s.jlo + a, s.yl, s.yh);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (b >= nc) break;
+                float o = __fmul_rn(ov_len(g.x0, g.wb, s.ilo + b, s.xl, s.xh), oy);
+                sx = fmaf(o, e[a][b].x, sx);
+                sy = fmaf(o, e[a][b].y, sy);
+            }
+        }
+    } else {
+        for (int j = s.jlo; j <= s.jhi; ++j) {
+            float oy = ov_len(g.y0, g.hb, j, s.yl, s.yh);
+            const float2* r = E2 + (size_t)j * g.n;
+            for (int k = s.ilo; k <= s.ihi; ++k) {
+                float o = __fmul_rn(ov_len(g.x0, g.wb, k, s.xl, s.xh), oy);
+                float2 e = __ldg(r + k);
+                sx = fmaf(o, e.x, sx);
+                sy = fmaf(o, e.y, sy);
+            }
+        }
+    }
+    return make_float2(sx, sy);
+}
+
 // --------------------------------------------------- double-float sums
 // An unevaluated sum hi + lo of two floats (error-free transformations:
 // Knuth's TwoSum and Dekker's Fast2Sum).  Used to keep the grid-wide FP64
@@ -137,8 +194,7 @@ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
     return df_add(r, b.lo);
 }
 
-// Warp-reduces a dfloat and adds it to *dst with one FP64 atomic per warp.
-__device__ __forceinline__ void df_warp_atomic(dfloat v, double* dst) {
+__device__ __forceinline__ dfloat warp_df_sum(dfloat v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         dfloat w;
@@ -146,8 +202,11 @@ __device__ __forceinline__ void df_warp_atomic(dfloat v, double* dst) {
         w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
         v = df_add(v, w);
     }
-    if ((threadIdx.x & 31) == 0 && (v.hi != 0.0f || v.lo != 0.0f))
-        atomicAdd(dst, (double)v.hi + (double)v.lo);
+    return v;
+}
+
+__device__ __forceinline__ double* acc_stripe(double* acc, int q) {
+    return acc + (blockIdx.x & (kAccStripes - 1)) * kAccStride + q;
 }
 
 // Max of non-negative doubles through their ordered bit patterns.
@@ -156,10 +215,53 @@ __device__ __forceinline__ void atomic_max_nonneg(double* dst, double v) {
               (unsigned long long)__double_as_longlong(v));
 }
 
+// Block-wide sums of a and b (every thread of the block must call this);
+// thread 0 adds each nonzero total to its stripe of quantity qa / qb
+// (qb < 0: none).  One FP64 atomic per quantity per block.
+__device__ __forceinline__ void block_acc2(dfloat a, dfloat b, double* acc, int qa, int qb) {
+    __shared__ dfloat s_a[32], s_b[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    a = warp_df_sum(a);
+    b = warp_df_sum(b);
+    __syncthreads();   // s_a/s_b may still be read by an earlier call
+    if (l == 0) { s_a[w] = a; s_b[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = l < nw ? s_a[l] : dfloat{0.0f, 0.0f};
+        b = l < nw ? s_b[l] : dfloat{0.0f, 0.0f};
+        a = warp_df_sum(a);
+        b = warp_df_sum(b);
+        if (l == 0) {
+            if (qa >= 0 && (a.hi != 0.0f || a.lo != 0.0f))
+                atomicAdd(acc_stripe(acc, qa), (double)a.hi + (double)a.lo);
+            if (qb >= 0 && (b.hi != 0.0f || b.lo != 0.0f))
+                atomicAdd(acc_stripe(acc, qb), (double)b.hi + (double)b.lo);
+        }
+    }
+}
+
+__device__ __forceinline__ void block_acc1(dfloat a, double* acc, int qa) {
+    block_acc2(a, dfloat{0.0f, 0.0f}, acc, qa, -1);
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Block-wide max of non-negative v into the stripe of quantity q.
+__device__ __forceinline__ void block_max(float v, double* acc, int q) {
+    __shared__ float s_m[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (l == 0) s_m[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = warp_max(l < nw ? s_m[l] : 0.0f);
+        if (l == 0) atomic_max_nonneg(acc_stripe(acc, q), (double)v);
+    }
 }
 
 // ------------------------------------------------------------ complex
@@ -197,10 +299,16 @@ struct Ctx {
     long long* Dq = nullptr;
     float *T1 = nullptr, *PT = nullptr, *RT = nullptr;
     float *psi = nullptr, *ex = nullptr, *ey = nullptr, *rho = nullptr;
+    float2* E2 = nullptr;       // interleaved field (E_x, E_y) [n][n]
     float2 *tw = nullptr, *ph = nullptr;
-    int32_t *net_ptr = nullptr, *pin_cell = nullptr, *pin_slot = nullptr, *cell_pin_ptr = nullptr;
+    // pins re-laid into degree slabs (see k_wire.cu): slot base + 32 k + lane
+    int4* slabs = nullptr;      // {base slot, degree, net count, 0}
+    int nslabs = 0;
+    int64_t slab_slots = 0;
+    int32_t *pin_cell = nullptr, *pin_slot = nullptr, *cell_pin_ptr = nullptr;
     float *pin_dx = nullptr, *pin_dy = nullptr;
     float2* gpin = nullptr;
+    float2* gW2 = nullptr;      // interleaved wirelength gradient accumulator (m_mov)
     double* acc = nullptr;
     int* err = nullptr;
     double* acc_host = nullptr;   // pinned mirror
@@ -226,7 +334,7 @@ struct Ctx {
     std::vector<int> prof_stage;
     int prof_used = 0;
 
-    bool rho_valid = false, fields_valid = false;
+    bool rho_valid = false, fields_valid = false, split_valid = false;
     std::string last_error;
     std::vector<void*> dev_allocs;
     size_t dev_bytes = 0;
@@ -238,19 +346,18 @@ void prepare_spectral(int logn);
 cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* w,
                            const float* h, int m, float* D, long long* Dq, cudaStream_t s);
 cudaError_t launch_bin_ranges(Ctx& c, const float* x, const float* y, int32_t* ranges,
-                              double* pairs, cudaStream_t s);
+                              cudaStream_t s);
 cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s);
 cudaError_t launch_cols_spectral(Ctx& c, cudaStream_t s);
 cudaError_t launch_rows_inv(Ctx& c, cudaStream_t s);
 cudaError_t launch_rho(Ctx& c, cudaStream_t s);
+cudaError_t launch_split_field(Ctx& c, cudaStream_t s);
 cudaError_t launch_q_to_f(const long long* q, float scale, float* out, int count, cudaStream_t s);
 cudaError_t launch_gather(Ctx& c, const float* x, const float* y, float* gx, float* gy,
                           bool adjoint, cudaStream_t s);
-cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, float* gx,
-                      float* gy, cudaStream_t s);
+cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, cudaStream_t s);
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
-                           const double* gamma_dev, float* gx, float* gy, const double* done,
-                           cudaStream_t s);
+                           const double* gamma_dev, const double* done, cudaStream_t s);
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s);
 cudaError_t launch_cells(Ctx& c, const float* x, const float* y, float* gNx, float* gNy,
                          float* gWx, float* gWy, cudaStream_t s);

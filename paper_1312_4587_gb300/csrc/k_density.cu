@@ -11,7 +11,10 @@
 
 namespace fftpl {
 
-// One thread per cell.  FP32 mode: red.global.add.f32 of ov into D.
+// One thread per cell.  FP32 mode: ov added into D with 16-byte vector
+// atomics over the aligned groups of 4 bins a row span touches (zeros for
+// the bins of a group outside the span), which cuts the atomic count about
+// in half for cells spanning 2-4 bins.
 // Deterministic mode: ov is formed in float32 (x and y lengths, then their
 // product), scaled by 2^32 (exact) and rounded to the nearest integer (ties to
 // even); int64 atomics make the bin sums independent of order.
@@ -25,15 +28,23 @@ k_scatter(Grid g, int m, const float* __restrict__ x, const float* __restrict__ 
     Span s = cell_span(g, x[i], y[i], w[i], h[i]);
     for (int j = s.jlo; j <= s.jhi; ++j) {
         float oy = ov_len(g.y0, g.hb, j, s.yl, s.yh);
-        for (int k = s.ilo; k <= s.ihi; ++k) {
-            float ox = ov_len(g.x0, g.wb, k, s.xl, s.xh);
-            float a = __fmul_rn(ox, oy);
-            size_t b = (size_t)j * g.n + k;
-            if (QUANT) {
+        if (QUANT) {
+            for (int k = s.ilo; k <= s.ihi; ++k) {
+                float a = __fmul_rn(ov_len(g.x0, g.wb, k, s.xl, s.xh), oy);
                 long long q = __float2ll_rn(__fmul_rn(a, 4294967296.0f));
-                atomicAdd(Dq + b, (unsigned long long)q);
-            } else {
-                atomicAdd(D + b, a);
+                atomicAdd(Dq + (size_t)j * g.n + k, (unsigned long long)q);
+            }
+        } else {
+            float* row = D + (size_t)j * g.n;
+            for (int q = s.ilo >> 2; q <= (s.ihi >> 2); ++q) {
+                float v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    int k = 4 * q + t;
+                    v[t] = (k >= s.ilo && k <= s.ihi)
+                               ? __fmul_rn(ov_len(g.x0, g.wb, k, s.xl, s.xh), oy) : 0.0f;
+                }
+                atomicAdd(reinterpret_cast<float4*>(row + 4 * q), make_float4(v[0], v[1], v[2], v[3]));
             }
         }
     }
@@ -42,7 +53,7 @@ k_scatter(Grid g, int m, const float* __restrict__ x, const float* __restrict__ 
 __global__ void __launch_bounds__(kCellThreads)
 k_bin_ranges(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
              const float* __restrict__ w, const float* __restrict__ h, int4* __restrict__ out,
-             double* __restrict__ pairs) {
+             double* __restrict__ acc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float cnt = 0.0f;
     if (i < m) {
@@ -55,8 +66,7 @@ k_bin_ranges(Grid g, int m, const float* __restrict__ x, const float* __restrict
             cnt = (float)((s.ihi - s.ilo + 1) * (s.jhi - s.jlo + 1));
         }
     }
-    dfloat d = {cnt, 0.0f};
-    df_warp_atomic(d, pairs);
+    block_acc1(dfloat{cnt, 0.0f}, acc, ACC_CHARGE);
 }
 
 // Field gather (ADJ = false) or exact edge-difference adjoint (ADJ = true,
@@ -65,25 +75,16 @@ template <bool ADJ>
 __global__ void __launch_bounds__(kCellThreads)
 k_gather(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
          const float* __restrict__ w, const float* __restrict__ h, const float* __restrict__ fx,
-         const float* __restrict__ fy, float* __restrict__ gx, float* __restrict__ gy,
-         double* __restrict__ l1) {
+         const float2* __restrict__ E2, float* __restrict__ gx, float* __restrict__ gy,
+         double* __restrict__ acc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float sx = 0.0f, sy = 0.0f;
     if (i < m) {
         Span s = cell_span(g, x[i], y[i], w[i], h[i]);
         if (!ADJ) {
-            for (int j = s.jlo; j <= s.jhi; ++j) {
-                float oy = ov_len(g.y0, g.hb, j, s.yl, s.yh);
-                const float* rx = fx + (size_t)j * g.n;
-                const float* ry = fy + (size_t)j * g.n;
-                for (int k = s.ilo; k <= s.ihi; ++k) {
-                    float o = __fmul_rn(ov_len(g.x0, g.wb, k, s.xl, s.xh), oy);
-                    sx = fmaf(o, __ldg(rx + k), sx);
-                    sy = fmaf(o, __ldg(ry + k), sy);
-                }
-            }
-            sx = -sx;
-            sy = -sy;
+            float2 e = gather_span(g, s, E2);
+            sx = -e.x;
+            sy = -e.y;
         } else if (s.ilo <= s.ihi && s.jlo <= s.jhi) {
             int n = g.n;
             int kl = last_edge<false>(g.x0, g.wb, g.inv_wb, n, s.xl);
@@ -109,11 +110,7 @@ k_gather(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y
         gx[i] = sx;
         gy[i] = sy;
     }
-    if (l1) {
-        dfloat d = {fabsf(sx) + fabsf(sy), 0.0f};
-        d = df_add(df_zero(), d);
-        df_warp_atomic(d, l1);
-    }
+    block_acc1(dfloat{fabsf(sx) + fabsf(sy), 0.0f}, acc, ACC_GN_L1);
 }
 
 // rho = (D + M) / A_b (formed on demand for fftpl_fields).
@@ -124,6 +121,16 @@ __global__ void k_rho(int count, const float* __restrict__ D, const long long* _
     if (i >= count) return;
     float d = QUANT ? (float)Dq[i] * 2.3283064365386963e-10f : D[i];
     rho[i] = (d + M[i]) * inv_ab;
+}
+
+__global__ void k_split_field(int count, const float2* __restrict__ E2, float* __restrict__ ex,
+                              float* __restrict__ ey) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        float2 e = E2[i];
+        ex[i] = e.x;
+        ey[i] = e.y;
+    }
 }
 
 __global__ void k_q_to_f(const long long* __restrict__ q, float scale, float* __restrict__ out,
@@ -148,10 +155,10 @@ cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* 
 }
 
 cudaError_t launch_bin_ranges(Ctx& c, const float* x, const float* y, int32_t* ranges,
-                              double* pairs, cudaStream_t s) {
+                              cudaStream_t s) {
     if (c.m_mov <= 0) return cudaSuccess;
     k_bin_ranges<<<blocks_for(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
-        c.grid, c.m_mov, x, y, c.w, c.h, reinterpret_cast<int4*>(ranges), pairs);
+        c.grid, c.m_mov, x, y, c.w, c.h, reinterpret_cast<int4*>(ranges), c.acc);
     c.launches++;
     return cudaGetLastError();
 }
@@ -161,11 +168,11 @@ cudaError_t launch_gather(Ctx& c, const float* x, const float* y, float* gx, flo
     if (c.m_mov <= 0) return cudaSuccess;
     int nb = blocks_for(c.m_mov, kCellThreads);
     if (adjoint)
-        k_gather<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.psi, c.psi,
-                                                  gx, gy, c.acc + ACC_GN_L1);
+        k_gather<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.psi, nullptr,
+                                                  gx, gy, c.acc);
     else
-        k_gather<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.ex, c.ey,
-                                                   gx, gy, c.acc + ACC_GN_L1);
+        k_gather<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, nullptr, c.E2,
+                                                   gx, gy, c.acc);
     c.launches++;
     return cudaGetLastError();
 }
@@ -177,6 +184,13 @@ cudaError_t launch_rho(Ctx& c, cudaStream_t s) {
         k_rho<true><<<blocks_for(count, 256), 256, 0, s>>>(count, nullptr, c.Dq, c.M, inv_ab, c.rho);
     else
         k_rho<false><<<blocks_for(count, 256), 256, 0, s>>>(count, c.D, nullptr, c.M, inv_ab, c.rho);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_field(Ctx& c, cudaStream_t s) {
+    int count = c.n * c.n;
+    k_split_field<<<blocks_for(count, 256), 256, 0, s>>>(count, c.E2, c.ex, c.ey);
     c.launches++;
     return cudaGetLastError();
 }

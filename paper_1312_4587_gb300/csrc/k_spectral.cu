@@ -27,87 +27,159 @@
 namespace fftpl {
 
 // ------------------------------------------------------------ FFT core
-// NB complex FFTs of length N = 2^LOGN, in place in buf[NB][N] (the stage
-// reads everything into registers, synchronises, then writes).  Forward:
-// X[k] = sum x[j] exp(-2 pi i jk / N); inverse: + sign, no 1/N.
+// Buffers are padded by one element every 16 (index i lives at i + i/16) so
+// that the strided Stockham writes spread over the shared-memory banks.
+__host__ __device__ constexpr int padded(int n) { return n + n / 16; }
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+// Twiddle exp(-+2 pi i k / 16) for the small exponents a radix-16 butterfly
+// uses (cos and sin of multiples of pi/8).
+__device__ __forceinline__ float2 w16(int e, bool inv) {
+    const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+    float2 w;
+    switch (e & 15) {
+        case 0: w = make_float2(1.0f, 0.0f); break;
+        case 1: w = make_float2(c1, -s1); break;
+        case 2: w = make_float2(h, -h); break;
+        case 3: w = make_float2(s1, -c1); break;
+        case 4: w = make_float2(0.0f, -1.0f); break;
+        case 6: w = make_float2(-h, -h); break;
+        case 9: w = make_float2(-c1, s1); break;
+        default: w = make_float2(1.0f, 0.0f); break;  // not used
+    }
+    if (inv) w.y = -w.y;
+    return w;
+}
+
+// multiply by -i (forward) or +i (inverse)
+__device__ __forceinline__ float2 rot(float2 a, bool inv) {
+    return inv ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+// in-place 4-point DFT of (a0, a1, a2, a3)
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3, bool inv) {
+    float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+    float2 s13 = cadd(a1, a3), d13 = rot(csub(a1, a3), inv);
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = cadd(d02, d13);
+    a3 = csub(d02, d13);
+}
+
+// R-point DFT in registers, natural order in and out.
+template <int R>
+__device__ __forceinline__ void dft(float2 (&v)[R], bool inv);
+
+template <>
+__device__ __forceinline__ void dft<2>(float2 (&v)[2], bool) { dft2(v[0], v[1]); }
+
+template <>
+__device__ __forceinline__ void dft<4>(float2 (&v)[4], bool inv) { dft4(v[0], v[1], v[2], v[3], inv); }
+
+template <>
+__device__ __forceinline__ void dft<8>(float2 (&v)[8], bool inv) {
+    // 8 = 2 x 4: DFT4 of even and odd samples, twiddle W8^k, combine
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4(e0, e1, e2, e3, inv);
+    dft4(o0, o1, o2, o3, inv);
+    o1 = cmul(o1, w16(2, inv));
+    o2 = cmul(o2, w16(4, inv));
+    o3 = cmul(o3, w16(6, inv));
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+template <>
+__device__ __forceinline__ void dft<16>(float2 (&v)[16], bool inv) {
+    // 16 = 4 x 4: X[k1 + 4 k2] = sum_n2 W4^(n2 k2) W16^(n2 k1) sum_n1 x[4 n1 + n2] W4^(n1 k1)
+    float2 y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        y[n2][0] = v[n2]; y[n2][1] = v[n2 + 4]; y[n2][2] = v[n2 + 8]; y[n2][3] = v[n2 + 12];
+        dft4(y[n2][0], y[n2][1], y[n2][2], y[n2][3], inv);
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1)
+            if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w16(n2 * k1, inv));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 a0 = y[0][k1], a1 = y[1][k1], a2 = y[2][k1], a3 = y[3][k1];
+        dft4(a0, a1, a2, a3, inv);
+        v[k1] = a0; v[k1 + 4] = a1; v[k1 + 8] = a2; v[k1 + 12] = a3;
+    }
+}
+
+// One Stockham stage of radix R over NB padded buffers of length N, with Ns
+// the product of the radices already applied.  Reads everything it needs
+// into registers, synchronises, then writes.
+template <int LOGN, int NB, int R>
+__device__ __forceinline__ void stockham_stage(float2* __restrict__ buf, const float2* __restrict__ tw,
+                                               int Ns, bool inv) {
+    constexpr int N = 1 << LOGN;
+    constexpr int NP = padded(N);
+    constexpr int T = kSpecThreads;
+    constexpr int NR = N / R;
+    constexpr int ITEMS = NB * NR;
+    constexpr int PER = (ITEMS + T - 1) / T;
+    float2 v[PER][R];
+    int dst[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        int gi = threadIdx.x + i * T;
+        dst[i] = -1;
+        if (ITEMS % T == 0 || gi < ITEMS) {
+            int f = gi / NR, j = gi % NR;
+            int k = j & (Ns - 1);
+            const float2* src = buf + f * NP;
+            int st = (N / (R * Ns)) * k;   // twiddle index step: W_N^(r st)
+            v[i][0] = src[pidx(j)];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[r * st];
+                if (inv) w.y = -w.y;
+                v[i][r] = cmul(src[pidx(j + r * NR)], w);
+            }
+            dst[i] = (f << 24) | ((j - k) * R + k);   // buffer and element index
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        if (dst[i] < 0) continue;
+        dft<R>(v[i], inv);
+        float2* out = buf + (dst[i] >> 24) * NP;
+        int o = dst[i] & 0xffffff;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[pidx(o + r * Ns)] = v[i][r];
+    }
+    __syncthreads();
+}
+
+// NB complex FFTs of length N = 2^LOGN in the padded buffers.  Forward:
+// X[k] = sum x[j] exp(-2 pi i jk / N); inverse: + sign, no 1/N.  Radix-16
+// stages first, then one radix-2/4/8 stage for the remaining factor.
 template <int LOGN, int NB>
 __device__ __forceinline__ void fft_block(float2* __restrict__ buf, const float2* __restrict__ tw,
                                           bool inv) {
-    constexpr int N = 1 << LOGN;
-    constexpr int T = kSpecThreads;
-    constexpr int NQ = N / 4;
-    constexpr int I4 = NB * NQ;
-    constexpr int P4 = (I4 + T - 1) / T;
     int Ns = 1;
-#pragma unroll 1
-    for (int s = 0; s + 2 <= LOGN; s += 2) {
-        float2 v[P4][4];
-        int dsti[P4];
 #pragma unroll
-        for (int i = 0; i < P4; ++i) {
-            int gi = threadIdx.x + i * T;
-            dsti[i] = -1;
-            if (I4 % T == 0 || gi < I4) {
-                int f = gi / NQ, j = gi % NQ;
-                int k = j & (Ns - 1);
-                const float2* src = buf + f * N + j;
-                int st = (NQ / Ns) * k;
-                float2 w1 = tw[st], w2 = tw[2 * st], w3 = tw[3 * st];
-                if (inv) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
-                v[i][0] = src[0];
-                v[i][1] = cmul(src[NQ], w1);
-                v[i][2] = cmul(src[2 * NQ], w2);
-                v[i][3] = cmul(src[3 * NQ], w3);
-                dsti[i] = f * N + (j - k) * 4 + k;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < P4; ++i) {
-            if (dsti[i] < 0) continue;
-            float2 a0 = v[i][0], a1 = v[i][1], a2 = v[i][2], a3 = v[i][3];
-            float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
-            float2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
-            // forward: multiply d13 by -i ; inverse: by +i
-            float2 rd13 = inv ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-            float2* dst = buf + dsti[i];
-            dst[0] = cadd(s02, s13);
-            dst[Ns] = cadd(d02, rd13);
-            dst[2 * Ns] = csub(s02, s13);
-            dst[3 * Ns] = csub(d02, rd13);
-        }
-        __syncthreads();
-        Ns <<= 2;
+    for (int s = 0; s + 4 <= LOGN; s += 4) {
+        stockham_stage<LOGN, NB, 16>(buf, tw, Ns, inv);
+        Ns <<= 4;
     }
-    if (LOGN & 1) {
-        constexpr int NH = N / 2;
-        constexpr int I2 = NB * NH;
-        constexpr int P2 = (I2 + T - 1) / T;
-        float2 v0[P2], v1[P2];
-        int dsti[P2];
-#pragma unroll
-        for (int i = 0; i < P2; ++i) {
-            int gi = threadIdx.x + i * T;
-            dsti[i] = -1;
-            if (I2 % T == 0 || gi < I2) {
-                int f = gi / NH, j = gi % NH;
-                int k = j & (Ns - 1);
-                float2 w1 = tw[(NH / Ns) * k];
-                if (inv) w1.y = -w1.y;
-                v0[i] = buf[f * N + j];
-                v1[i] = cmul(buf[f * N + j + NH], w1);
-                dsti[i] = f * N + (j - k) * 2 + k;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < P2; ++i) {
-            if (dsti[i] < 0) continue;
-            buf[dsti[i]] = cadd(v0[i], v1[i]);
-            buf[dsti[i] + Ns] = csub(v0[i], v1[i]);
-        }
-        __syncthreads();
-    }
+    constexpr int REM = LOGN & 3;
+    if (REM == 1) stockham_stage<LOGN, NB, 2>(buf, tw, Ns, inv);
+    if (REM == 2) stockham_stage<LOGN, NB, 4>(buf, tw, Ns, inv);
+    if (REM == 3) stockham_stage<LOGN, NB, 8>(buf, tw, Ns, inv);
 }
 
 // Position of sample x in Makhoul's reordering.
@@ -129,7 +201,7 @@ __device__ __forceinline__ float2 pack_inv(float c1u, float c1nu, float c2u, flo
 // -------------------------------------------------------- pass 1: rows
 // CTA: 8 rows of rho (2 per complex buffer).  Writes T1[u][y0..y0+7].
 template <int LOGN, bool QUANT>
-__global__ void __launch_bounds__(kSpecThreads)
+__global__ void __launch_bounds__(kSpecThreads, 2)
 k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
            const float* __restrict__ M, float inv_ab, float cap, float* __restrict__ T1,
            const float2* __restrict__ tw, const float2* __restrict__ ph, double* __restrict__ acc) {
@@ -137,6 +209,7 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = 2 * NB;
     constexpr int T = kSpecThreads;
+    constexpr int NP = padded(N);
     extern __shared__ float2 sm[];
     const int y0 = blockIdx.x * ROWS;
     dfloat tau = df_zero(), charge = df_zero();
@@ -148,10 +221,9 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
         tau = df_add(tau, fmaxf(0.0f, d - (cap - mm)));
         charge = df_add(charge, d + mm);
         float rho = (d + mm) * inv_ab;
-        reinterpret_cast<float*>(sm + (r >> 1) * N + mk_pos(x, N))[r & 1] = rho;
+        reinterpret_cast<float*>(sm + (r >> 1) * NP + pidx(mk_pos(x, N)))[r & 1] = rho;
     }
-    df_warp_atomic(tau, acc + ACC_TAU);
-    df_warp_atomic(charge, acc + ACC_CHARGE);
+    block_acc2(tau, charge, acc, ACC_TAU, ACC_CHARGE);
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, false);
     // split the packed spectra and apply the post-twiddle:
@@ -168,8 +240,8 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
         where[i] = -1;
         if (gi < ITEMS) {
             int f = gi / HALF, u = gi % HALF;
-            float2 zu = sm[f * N + u];
-            float2 zn = sm[f * N + ((N - u) & (N - 1))];
+            float2 zu = sm[f * NP + pidx(u)];
+            float2 zn = sm[f * NP + pidx((N - u) & (N - 1))];
             float2 v1 = make_float2(0.5f * (zu.x + zn.x), 0.5f * (zu.y - zn.y));
             float2 v2 = make_float2(0.5f * (zu.y + zn.y), 0.5f * (zn.x - zu.x));
             float2 p = ph[u];
@@ -214,7 +286,7 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
 // w_v Psi, via reversed coefficients).  Each complex IFFT carries the same
 // quantity for two rows (P with P, R with R), so both parts share a scale.
 template <int LOGN>
-__global__ void __launch_bounds__(kSpecThreads)
+__global__ void __launch_bounds__(kSpecThreads, 2)
 k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__ RT,
        const float2* __restrict__ tw, const float2* __restrict__ ph, float pi_lx, float pi_ly,
        double* __restrict__ acc) {
@@ -222,12 +294,13 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = NB;
     constexpr int T = kSpecThreads;
+    constexpr int NP = padded(N);
     extern __shared__ float2 sm[];
     const int u0 = blockIdx.x * ROWS;
     for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
         int r = idx >> LOGN, y = idx & (N - 1);
         float val = T1[(size_t)(u0 + r) * N + y];
-        reinterpret_cast<float*>(sm + (r >> 1) * N + mk_pos(y, N))[r & 1] = val;
+        reinterpret_cast<float*>(sm + (r >> 1) * NP + pidx(mk_pos(y, N)))[r & 1] = val;
     }
     __syncthreads();
     fft_block<LOGN, NB / 2>(sm, tw, false);
@@ -245,8 +318,8 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
         if (gi < ITEMS) {
             int f = gi / HALF, v = gi % HALF;
             int vn = (N - v) & (N - 1);
-            float2 zu = sm[f * N + v];
-            float2 zn = sm[f * N + vn];
+            float2 zu = sm[f * NP + pidx(v)];
+            float2 zn = sm[f * NP + pidx(vn)];
             float2 v1 = make_float2(0.5f * (zu.x + zn.x), 0.5f * (zu.y - zn.y));
             float2 v2 = make_float2(0.5f * (zu.y + zn.y), 0.5f * (zn.x - zu.x));
             float2 p = ph[v], q = ph[N - v];
@@ -294,28 +367,28 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
             where[i] = f * HALF + v;
         }
     }
-    df_warp_atomic(energy, acc + ACC_N);
+    block_acc1(energy, acc, ACC_N);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < PI; ++i) {
         if (where[i] < 0) continue;
         int f = where[i] / HALF, v = where[i] % HALF;
-        float2* rowP = sm + (2 * f) * N;
-        float2* rowR = sm + (2 * f + 1) * N;
-        rowP[v & (N - 1)] = zo[i][0];
-        rowR[v & (N - 1)] = zo[i][2];
+        float2* rowP = sm + (2 * f) * NP;
+        float2* rowR = sm + (2 * f + 1) * NP;
+        rowP[pidx(v & (N - 1))] = zo[i][0];
+        rowR[pidx(v & (N - 1))] = zo[i][2];
         if (v > 0 && v < N / 2) {
-            rowP[N - v] = zo[i][1];
-            rowR[N - v] = zo[i][3];
+            rowP[pidx(N - v)] = zo[i][1];
+            rowR[pidx(N - v)] = zo[i][3];
         }
     }
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, true);
     // unshuffle: y even <- k = y/2, y odd <- k = N-1-(y-1)/2
     for (int y = threadIdx.x; y < N; y += T) {
-        int k = mk_src(y, N);
+        int k = pidx(mk_src(y, N));
         float sgn = (y & 1) ? -1.0f : 1.0f;
-        float2 p0 = sm[0 * N + k], r0 = sm[1 * N + k], p1 = sm[2 * N + k], r1 = sm[3 * N + k];
+        float2 p0 = sm[0 * NP + k], r0 = sm[1 * NP + k], p1 = sm[2 * NP + k], r1 = sm[3 * NP + k];
         *reinterpret_cast<float4*>(PT + (size_t)y * N + u0) = make_float4(p0.x, p0.y, p1.x, p1.y);
         *reinterpret_cast<float4*>(RT + (size_t)y * N + u0) =
             make_float4(sgn * r0.x, sgn * r0.y, sgn * r1.x, sgn * r1.y);
@@ -324,19 +397,22 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
 
 // ------------------------------------------------- pass 3: inverse rows
 // CTA: 4 rows y.  Round A: psi (cosine sum of P) for two rows per IFFT and
-// E_y (cosine sum of R) for two rows per IFFT.  Round B: E_x (sine sum of
-// w_u P) for two rows per IFFT.
+// E_y (cosine sum of R) for two rows per IFFT; E_y is parked in shared
+// memory.  Round B: E_x (sine sum of w_u P) for two rows per IFFT, written
+// with E_y as the interleaved field map E2[y][x] = (E_x, E_y).
 template <int LOGN>
-__global__ void __launch_bounds__(kSpecThreads)
+__global__ void __launch_bounds__(kSpecThreads, 2)
 k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __restrict__ psi,
-           float* __restrict__ ex, float* __restrict__ ey, const float2* __restrict__ tw,
-           const float2* __restrict__ ph, float pi_lx) {
+           float2* __restrict__ E2, const float2* __restrict__ tw, const float2* __restrict__ ph,
+           float pi_lx) {
     constexpr int N = 1 << LOGN;
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = NB;
     constexpr int T = kSpecThreads;
     constexpr int HALF = N / 2 + 1;
+    constexpr int NP = padded(N);
     extern __shared__ float2 sm[];
+    float* eys = reinterpret_cast<float*>(sm + NB * NP);  // E_y parked [ROWS][N]
     const int y0 = blockIdx.x * ROWS;
     // round A: buffer 2f holds psi of rows (2f, 2f+1), buffer 2f+1 holds E_y
     for (int idx = threadIdx.x; idx < (ROWS / 2) * HALF; idx += T) {
@@ -352,9 +428,9 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __
             float cau = (u == 0) ? au : 0.5f * au, cbu = (u == 0) ? bu : 0.5f * bu;
             float can = 0.5f * an, cbn = 0.5f * bn;
             if (u == N / 2) { can = cau; cbn = cbu; }
-            float2* row = sm + (2 * f + q) * N;
-            row[u & (N - 1)] = pack_inv(cau, can, cbu, cbn, ph[u]);
-            if (u > 0 && u < N / 2) row[N - u] = pack_inv(can, cau, cbn, cbu, ph[N - u]);
+            float2* row = sm + (2 * f + q) * NP;
+            row[pidx(u & (N - 1))] = pack_inv(cau, can, cbu, cbn, ph[u]);
+            if (u > 0 && u < N / 2) row[pidx(N - u)] = pack_inv(can, cau, cbn, cbu, ph[N - u]);
         }
     }
     __syncthreads();
@@ -362,11 +438,10 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __
     for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
         int r = idx >> LOGN, x = idx & (N - 1);
         int f = r >> 1;
-        int k = mk_src(x, N);
-        float2 zp = sm[(2 * f) * N + k], ze = sm[(2 * f + 1) * N + k];
-        size_t b = (size_t)(y0 + r) * N + x;
-        psi[b] = (r & 1) ? zp.y : zp.x;
-        ey[b] = (r & 1) ? ze.y : ze.x;
+        int k = pidx(mk_src(x, N));
+        float2 zp = sm[(2 * f) * NP + k], ze = sm[(2 * f + 1) * NP + k];
+        psi[(size_t)(y0 + r) * N + x] = (r & 1) ? zp.y : zp.x;
+        eys[r * N + x] = (r & 1) ? ze.y : ze.x;
     }
     __syncthreads();
     // round B: E_x rows (2 per buffer).  c[u'] = s[N-u'] (u' >= 1), c[0] = 0,
@@ -382,17 +457,17 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __
         float ca_n = (u == 0) ? 0.0f : 0.5f * wu * Pa[u];
         float cb_n = (u == 0) ? 0.0f : 0.5f * wu * Pb[u];
         if (u == N / 2) { ca_n = ca_u; cb_n = cb_u; }
-        float2* row = sm + f * N;
-        row[u & (N - 1)] = pack_inv(ca_u, ca_n, cb_u, cb_n, ph[u]);
-        if (u > 0 && u < N / 2) row[N - u] = pack_inv(ca_n, ca_u, cb_n, cb_u, ph[N - u]);
+        float2* row = sm + f * NP;
+        row[pidx(u & (N - 1))] = pack_inv(ca_u, ca_n, cb_u, cb_n, ph[u]);
+        if (u > 0 && u < N / 2) row[pidx(N - u)] = pack_inv(ca_n, ca_u, cb_n, cb_u, ph[N - u]);
     }
     __syncthreads();
     fft_block<LOGN, NB / 2>(sm, tw, true);
     for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
         int r = idx >> LOGN, x = idx & (N - 1);
-        float2 z = sm[(r >> 1) * N + mk_src(x, N)];
+        float2 z = sm[(r >> 1) * NP + pidx(mk_src(x, N))];
         float val = (r & 1) ? z.y : z.x;
-        ex[(size_t)(y0 + r) * N + x] = (x & 1) ? -val : val;
+        E2[(size_t)(y0 + r) * N + x] = make_float2((x & 1) ? -val : val, eys[r * N + x]);
     }
 }
 
@@ -400,7 +475,7 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __
 template <int LOGN>
 static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {
     constexpr int N = 1 << LOGN;
-    size_t smem = (size_t)kSpecBuffers * N * sizeof(float2);
+    size_t smem = (size_t)kSpecBuffers * padded(N) * sizeof(float2);
     float inv_ab = (float)(1.0 / c.Ab);
     float cap = (float)(c.opt.target_density * c.Ab);
     float pi_lx = (float)(M_PI / c.Lx), pi_ly = (float)(M_PI / c.Ly);
@@ -421,8 +496,9 @@ static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {
                                                         c.acc);
     } else {
         auto kf = k_rows_inv<LOGN>;
-        kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.PT, c.RT, c.psi, c.ex, c.ey, c.tw, c.ph,
-                                                        pi_lx);
+        size_t smem_inv = smem + (size_t)kSpecBuffers * N * sizeof(float);
+        kf<<<N / kSpecBuffers, kSpecThreads, smem_inv, s>>>(c.PT, c.RT, c.psi, c.E2, c.tw, c.ph,
+                                                            pi_lx);
     }
     c.launches++;
     e = cudaGetLastError();
@@ -433,11 +509,12 @@ static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {
 // outside any stream capture).
 template <int LOGN>
 static void prepare_logn() {
-    int smem = (int)((size_t)kSpecBuffers * (1 << LOGN) * sizeof(float2));
+    int smem = (int)((size_t)kSpecBuffers * padded(1 << LOGN) * sizeof(float2));
     cudaFuncSetAttribute(k_rows_fwd<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_rows_fwd<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_cols<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_rows_inv<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_rows_inv<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem + (int)(kSpecBuffers * (1 << LOGN) * sizeof(float)));
 }
 
 void prepare_spectral(int logn) {

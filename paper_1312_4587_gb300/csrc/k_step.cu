@@ -18,26 +18,17 @@ struct LoopBufs {
 // gather + pin sums at v (like k_cells) and, in the last CTA, lambda_k.
 template <bool CSR>
 __global__ void __launch_bounds__(kCellThreads)
-k_loop_cells(Grid gr, int m, LoopBufs b, const float* __restrict__ ex,
-             const float* __restrict__ ey, const int* __restrict__ cell_pin_ptr,
-             const float2* __restrict__ gpin) {
+k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
+             const int* __restrict__ cell_pin_ptr,
+             const float2* __restrict__ gpin, const float2* __restrict__ gW2) {
     if (b.ctrl[C_DONE] != 0.0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float nx = 0.0f, ny = 0.0f, wx = 0.0f, wy = 0.0f;
     if (i < m) {
         Span s = cell_span(gr, b.v[i], b.v[m + i], b.w[i], b.h[i]);
-        for (int j = s.jlo; j <= s.jhi; ++j) {
-            float oy = ov_len(gr.y0, gr.hb, j, s.yl, s.yh);
-            const float* rx = ex + (size_t)j * gr.n;
-            const float* ry = ey + (size_t)j * gr.n;
-            for (int k = s.ilo; k <= s.ihi; ++k) {
-                float o = __fmul_rn(ov_len(gr.x0, gr.wb, k, s.xl, s.xh), oy);
-                nx = fmaf(o, __ldg(rx + k), nx);
-                ny = fmaf(o, __ldg(ry + k), ny);
-            }
-        }
-        nx = -nx;
-        ny = -ny;
+        float2 e = gather_span(gr, s, E2);
+        nx = -e.x;
+        ny = -e.y;
         b.gN[i] = nx;
         b.gN[m + i] = ny;
         if (CSR) {
@@ -46,15 +37,16 @@ k_loop_cells(Grid gr, int m, LoopBufs b, const float* __restrict__ ex,
                 wx += p.x;
                 wy += p.y;
             }
-            b.gW[i] = wx;
-            b.gW[m + i] = wy;
         } else {
-            wx = b.gW[i];
-            wy = b.gW[m + i];
+            float2 v = gW2[i];
+            wx = v.x;
+            wy = v.y;
         }
+        b.gW[i] = wx;
+        b.gW[m + i] = wy;
     }
-    df_warp_atomic(df_add(df_zero(), fabsf(nx) + fabsf(ny)), b.acc + ACC_GN_L1);
-    df_warp_atomic(df_add(df_zero(), fabsf(wx) + fabsf(wy)), b.acc + ACC_GW_L1);
+    block_acc2(dfloat{fabsf(nx) + fabsf(ny), 0.0f}, dfloat{fabsf(wx) + fabsf(wy), 0.0f}, b.acc,
+               ACC_GN_L1, ACC_GW_L1);
     if (last_cta(b.counters + 0) && threadIdx.x == 0) ctrl_lambda(b.ctrl, b.acc);
 }
 
@@ -75,10 +67,8 @@ __global__ void __launch_bounds__(kCellThreads) k_loop_g(int m2, LoopBufs b) {
             dv = c * c;
         }
     }
-    df_warp_atomic(df_add(df_zero(), dg), b.acc + ACC_DG2);
-    df_warp_atomic(df_add(df_zero(), dv), b.acc + ACC_DV2);
-    float mx = warp_max(gi);
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(b.acc + ACC_GINF, (double)mx);
+    block_acc2(dfloat{dg, 0.0f}, dfloat{dv, 0.0f}, b.acc, ACC_DG2, ACC_DV2);
+    block_max(gi, b.acc, ACC_GINF);
     if (last_cta(b.counters + 1) && threadIdx.x == 0) ctrl_alpha(b.ctrl, b.acc);
 }
 
@@ -104,8 +94,7 @@ k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
         b.u[i] = un;
         b.v[i] = vn;
     }
-    float mx = warp_max(step);
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(b.acc + ACC_STEPMAX, (double)mx);
+    block_max(step, b.acc, ACC_STEPMAX);
     if (last_cta(b.counters + 2) && threadIdx.x == 0) ctrl_record(b.ctrl, b.acc, b.recs);
 }
 
@@ -129,7 +118,7 @@ __global__ void k_place_init(int m, Grid gr, float x1, float y1, const float* __
 
 // gamma_0 from the overflow at the start (schedule mode).
 __global__ void k_gamma0(double* ctrl, const double* acc) {
-    double tau = ld(acc + ACC_TAU) / ctrl[C_MOV_AREA];
+    double tau = acc_sum(acc, ACC_TAU) / ctrl[C_MOV_AREA];
     ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
 }
 
@@ -148,11 +137,11 @@ cudaError_t launch_loop_cells(Ctx& c, cudaStream_t s) {
     LoopBufs b = loop_bufs(c);
     int nb = nblk(c.m_mov, kCellThreads);
     if (c.opt.deterministic)
-        k_loop_cells<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.ex, c.ey,
-                                                       c.cell_pin_ptr, c.gpin);
+        k_loop_cells<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.E2,
+                                                       c.cell_pin_ptr, c.gpin, nullptr);
     else
-        k_loop_cells<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.ex, c.ey, nullptr,
-                                                        nullptr);
+        k_loop_cells<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.E2, nullptr,
+                                                        nullptr, c.gW2);
     c.launches++;
     return cudaGetLastError();
 }

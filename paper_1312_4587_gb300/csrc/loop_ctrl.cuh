@@ -34,17 +34,27 @@ __device__ __forceinline__ bool last_cta(unsigned int* counter) {
     return is_last;
 }
 
-__device__ __forceinline__ double ld(const double* p) { return __ldcg(p); }
+// totals of the striped accumulators (read past L1)
+__device__ __forceinline__ double acc_sum(const double* acc, int q) {
+    double s = 0.0;
+    for (int k = 0; k < kAccStripes; ++k) s += __ldcg(acc + k * kAccStride + q);
+    return s;
+}
+__device__ __forceinline__ double acc_max(const double* acc, int q) {
+    double s = 0.0;
+    for (int k = 0; k < kAccStripes; ++k) s = fmax(s, __ldcg(acc + k * kAccStride + q));
+    return s;
+}
 
 // After the cell kernel: lambda_k.  lambda_0 = ||grad W~||_1 / ||grad N||_1
 // unless given; for k >= 1 lambda_k = mu_k lambda_{k-1} with
 // mu_k = 1.1^(-dW/dW_ref + 1) bounded to [0.75, 1.1], dW the HPWL change.
 __device__ __forceinline__ void ctrl_lambda(double* ctrl, const double* acc) {
     int k = (int)ctrl[C_K];
-    double hp = ld(acc + ACC_HPWL);
+    double hp = acc_sum(acc, ACC_HPWL);
     double lam = ctrl[C_LAMBDA];
     if (k == 0 && ctrl[C_LAMBDA0_OPT] <= 0.0) {
-        double gn = ld(acc + ACC_GN_L1), gw = ld(acc + ACC_GW_L1);
+        double gn = acc_sum(acc, ACC_GN_L1), gw = acc_sum(acc, ACC_GW_L1);
         lam = gn > 0.0 ? gw / gn : 1.0;
     }
     if (k >= 1) {
@@ -60,12 +70,12 @@ __device__ __forceinline__ void ctrl_lambda(double* ctrl, const double* acc) {
 // alpha_k ||g||_inf is then kept within [0.01 alpha_max_k, alpha_max_k].
 __device__ __forceinline__ void ctrl_alpha(double* ctrl, const double* acc) {
     int k = (int)ctrl[C_K];
-    double ginf = ld(acc + ACC_GINF);
+    double ginf = acc_max(acc, ACC_GINF);
     double alpha = ctrl[C_ALPHA], amax = ctrl[C_ALPHA_MAX];
     if (k == 0) {
         alpha = ginf > 0.0 ? ctrl[C_ALPHA_MAX0] / ginf : 0.0;
     } else {
-        double dg2 = ld(acc + ACC_DG2), dv2 = ld(acc + ACC_DV2);
+        double dg2 = acc_sum(acc, ACC_DG2), dv2 = acc_sum(acc, ACC_DV2);
         if (dg2 > 0.0) alpha = sqrt(dv2) / sqrt(dg2);
     }
     if (ginf > 0.0) {
@@ -88,14 +98,14 @@ __device__ __forceinline__ double gamma_schedule(double tau, double wb) {
 // gamma_{k+1}, k+1 and the stop test tau <= tau_stop.
 __device__ __forceinline__ void ctrl_record(double* ctrl, const double* acc, double* recs) {
     int k = (int)ctrl[C_K];
-    double tau = ld(acc + ACC_TAU) / ctrl[C_MOV_AREA];
-    double step_max = ld(acc + ACC_STEPMAX);
+    double tau = acc_sum(acc, ACC_TAU) / ctrl[C_MOV_AREA];
+    double step_max = acc_max(acc, ACC_STEPMAX);
     int slot = k - (int)ctrl[C_REC_BASE];
     if (slot >= 0 && slot < (int)ctrl[C_REC_CAP]) {
         double* r = recs + (size_t)slot * kRecFields;
-        r[0] = ld(acc + ACC_W);
-        r[1] = ld(acc + ACC_HPWL);
-        r[2] = ld(acc + ACC_N) * ctrl[C_HALF_AB];
+        r[0] = acc_sum(acc, ACC_W);
+        r[1] = acc_sum(acc, ACC_HPWL);
+        r[2] = acc_sum(acc, ACC_N) * ctrl[C_HALF_AB];
         r[3] = tau;
         r[4] = ctrl[C_LAMBDA];
         r[5] = ctrl[C_GAMMA];
