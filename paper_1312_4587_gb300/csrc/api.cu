@@ -288,11 +288,13 @@ const char* fftpl_last_error(fftpl_t h) {
 }
 
 // Re-lays the netlist for the WA kernel: nets of degree >= 2 grouped by
-// degree (original order kept within a degree) into slabs of up to 32 nets;
+// degree, largest first (original order kept within a degree), into slabs of
+// up to 32 nets;
 // pin k of slab net j at slot base + 32 k + j.  Degree-1 nets have no
 // wirelength and are left out.  In deterministic mode also builds the
 // cell-ordered pin slots (pins of each movable cell contiguous, in net order).
-static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins* pins) {
+static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins* pins,
+                                const float* fix_x, const float* fix_y) {
     const int32_t* np = nets->net_ptr;
     int maxd = 0;
     for (int e = 0; e < c.E; ++e) maxd = std::max(maxd, np[e + 1] - np[e]);
@@ -301,9 +303,11 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
         int d = np[e + 1] - np[e];
         if (d >= 2) by_deg[d].push_back(e);
     }
+    // heaviest slabs first: the long nets start early and overlap with the
+    // many short ones instead of forming a tail
     std::vector<int4> slabs;
     int64_t slots = 0;
-    for (int d = 2; d <= maxd; ++d) {
+    for (int d = maxd; d >= 2; --d) {
         const auto& v = by_deg[d];
         for (size_t s0 = 0; s0 < v.size(); s0 += 32) {
             int cnt = (int)std::min<size_t>(32, v.size() - s0);
@@ -336,12 +340,12 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
         CK(cudaMemcpy(c.cell_pin_ptr, cnt.data(), cnt.size() * sizeof(int32_t),
                       cudaMemcpyHostToDevice));
     }
-    std::vector<int32_t> spc((size_t)std::max<int64_t>(slots, 1), 0), sslot;
+    std::vector<int32_t> spc((size_t)std::max<int64_t>(slots, 1), -1), sslot;
     std::vector<float> sdx((size_t)std::max<int64_t>(slots, 1), 0.0f), sdy(sdx.size(), 0.0f);
     if (c.opt.deterministic) sslot.assign(spc.size(), -1);
     {
         size_t si = 0;
-        for (int d = 2; d <= maxd; ++d) {
+        for (int d = maxd; d >= 2; --d) {
             const auto& v = by_deg[d];
             for (size_t s0 = 0; s0 < v.size(); s0 += 32, ++si) {
                 const int4& sl = slabs[si];
@@ -350,9 +354,20 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
                     for (int k = 0; k < d; ++k) {
                         int p = np[e] + k;
                         size_t slot = (size_t)sl.x + 32 * (size_t)k + j;
-                        spc[slot] = pins->pin_cell[p];
-                        sdx[slot] = pins->dx[p];
-                        sdy[slot] = pins->dy[p];
+                        int cc = pins->pin_cell[p];
+                        if (cc < c.m_mov) {
+                            spc[slot] = cc;
+                            sdx[slot] = pins->dx[p];
+                            sdy[slot] = pins->dy[p];
+                        } else {
+                            // pin on a fixed cell: its coordinate never
+                            // changes; store fl32(centre + offset) itself
+                            volatile float ax = fix_x[cc - c.m_mov] + pins->dx[p];
+                            volatile float ay = fix_y[cc - c.m_mov] + pins->dy[p];
+                            spc[slot] = -1;
+                            sdx[slot] = ax;
+                            sdy[slot] = ay;
+                        }
                         if (c.opt.deterministic) sslot[slot] = cslot[p];
                     }
                 }
@@ -363,6 +378,7 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     TRY(dalloc(c, &c.pin_cell, spc.size()));
     TRY(dalloc(c, &c.pin_dx, sdx.size()));
     TRY(dalloc(c, &c.pin_dy, sdy.size()));
+    TRY(dalloc(c, &c.pxy, sdy.size()));
     if (!slabs.empty())
         CK(cudaMemcpy(c.slabs, slabs.data(), slabs.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c.pin_cell, spc.data(), spc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -442,6 +458,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     TRY(dalloc(c, &c.gN, 2 * (size_t)c.m_mov));
     TRY(dalloc(c, &c.gW, 2 * (size_t)c.m_mov));
     TRY(dalloc(c, &c.gW2, (size_t)c.m_mov));
+    TRY(dalloc(c, &c.pos2, (size_t)c.m_mov));
     if (c.opt.deterministic) {
         TRY(dalloc(c, &c.cell_pin_ptr, (size_t)c.m_mov + 1));
         TRY(dalloc(c, &c.gpin, c.P));
@@ -466,7 +483,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     }
     CK(cudaMemcpyAsync(c.tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.ph, ph.data(), (n + 1) * sizeof(float2), cudaMemcpyHostToDevice, s));
-    TRY(build_slabs(c, nets, pins));
+    TRY(build_slabs(c, nets, pins, cells->fix_x, cells->fix_y));
     // fixed-cell map M = rho_t F (Section III-B), order-free int64 sums
     {
         long long* q = nullptr;

@@ -72,7 +72,9 @@ __device__ __forceinline__ float edge_at(float lo, float step, int k) {
 }
 
 // Largest k in [-1, n] with e_k <= t (strict: e_k < t).  The float estimate
-// is corrected against the exact edges, so rounding never decides an index.
+// floor((t - x0) / w_b) is within one of the answer (its relative error is a
+// few 2^-24 and the quotient is at most n + 1 after clamping), so one
+// comparison against the exact edges in each direction settles the index.
 template <bool STRICT>
 __device__ __forceinline__ int last_edge(float lo, float step, float inv, int n, float t) {
     float kf = floorf(__fmul_rn(__fsub_rn(t, lo), inv));
@@ -80,19 +82,13 @@ __device__ __forceinline__ int last_edge(float lo, float step, float inv, int n,
     if (!(kf >= -1.0f)) k = -1;          // also catches NaN
     else if (kf > (float)n) k = n;
     else k = (int)kf;
-#pragma unroll 1
-    for (int it = 0; it < 3 && k >= 0; ++it) {
-        float e = edge_at(lo, step, k);
-        bool ok = STRICT ? (e < t) : (e <= t);
-        if (ok) break;
-        --k;
-    }
-#pragma unroll 1
-    for (int it = 0; it < 3 && k < n; ++it) {
+    if (k < n) {
         float e = edge_at(lo, step, k + 1);
-        bool ok = STRICT ? (e < t) : (e <= t);
-        if (!ok) break;
-        ++k;
+        if (STRICT ? (e < t) : (e <= t)) return k + 1;
+    }
+    if (k >= 0) {
+        float e = edge_at(lo, step, k);
+        if (!(STRICT ? (e < t) : (e <= t))) return k - 1;
     }
     return k;
 }
@@ -123,6 +119,29 @@ __device__ __forceinline__ float ov_len(float lo, float step, int k, float a, fl
     return fmaxf(v, 0.0f);
 }
 
+// Overlap lengths of a span [lo, hi] along one axis: the end bins take the
+// generic formula; every bin strictly inside is covered whole, and
+// e_{k+1} - e_k is exactly the bin size in float32, so "step" is the same
+// value the generic formula gives there.
+struct AxisOv {
+    int lo, hi;
+    float first, last, step;
+};
+
+__device__ __forceinline__ AxisOv axis_ov(float e0, float step, int lo, int hi, float a, float b) {
+    AxisOv r;
+    r.lo = lo;
+    r.hi = hi;
+    r.step = step;
+    r.first = ov_len(e0, step, lo, a, b);
+    r.last = ov_len(e0, step, hi, a, b);
+    return r;
+}
+
+__device__ __forceinline__ float ov_at(const AxisOv& r, int k) {
+    return k == r.lo ? r.first : (k == r.hi ? r.last : r.step);
+}
+
 // Field gather of one cell: sum_b ov(i,b) E2[b] over its bin span, E2 the
 // interleaved (E_x, E_y) map.  Spans of at most 2 rows x 4 columns (nearly
 // every cell) issue all their loads at once, predicated, before any use.
@@ -131,6 +150,8 @@ __device__ __forceinline__ float2 gather_span(const Grid& g, const Span& s,
     const int nr = s.jhi - s.jlo + 1, nc = s.ihi - s.ilo + 1;
     float sx = 0.0f, sy = 0.0f;
     if (nr <= 0 || nc <= 0) return make_float2(0.0f, 0.0f);
+    const AxisOv ax = axis_ov(g.x0, g.wb, s.ilo, s.ihi, s.xl, s.xh);
+    const AxisOv ay = axis_ov(g.y0, g.hb, s.jlo, s.jhi, s.yl, s.yh);
     if (nr <= 2 && nc <= 4) {
         float2 e[2][4];
 #pragma unroll
@@ -146,21 +167,21 @@ __device__ __forceinline__ float2 gather_span(const Grid& g, const Span& s,
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             if (a >= nr) break;
-            float oy = ov_len(g.y0, g.hb, s.jlo + a, s.yl, s.yh);
+            float oy = ov_at(ay, s.jlo + a);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 if (b >= nc) break;
-                float o = __fmul_rn(ov_len(g.x0, g.wb, s.ilo + b, s.xl, s.xh), oy);
+                float o = __fmul_rn(ov_at(ax, s.ilo + b), oy);
                 sx = fmaf(o, e[a][b].x, sx);
                 sy = fmaf(o, e[a][b].y, sy);
             }
         }
     } else {
         for (int j = s.jlo; j <= s.jhi; ++j) {
-            float oy = ov_len(g.y0, g.hb, j, s.yl, s.yh);
+            float oy = ov_at(ay, j);
             const float2* r = E2 + (size_t)j * g.n;
             for (int k = s.ilo; k <= s.ihi; ++k) {
-                float o = __fmul_rn(ov_len(g.x0, g.wb, k, s.xl, s.xh), oy);
+                float o = __fmul_rn(ov_at(ax, k), oy);
                 float2 e = __ldg(r + k);
                 sx = fmaf(o, e.x, sx);
                 sy = fmaf(o, e.y, sy);
@@ -215,34 +236,34 @@ __device__ __forceinline__ void atomic_max_nonneg(double* dst, double v) {
               (unsigned long long)__double_as_longlong(v));
 }
 
-// Block-wide sums of a and b (every thread of the block must call this);
-// thread 0 adds each nonzero total to its stripe of quantity qa / qb
-// (qb < 0: none).  One FP64 atomic per quantity per block.
-__device__ __forceinline__ void block_acc2(dfloat a, dfloat b, double* acc, int qa, int qb) {
-    __shared__ dfloat s_a[32], s_b[32];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-    a = warp_df_sum(a);
-    b = warp_df_sum(b);
-    __syncthreads();   // s_a/s_b may still be read by an earlier call
-    if (l == 0) { s_a[w] = a; s_b[w] = b; }
-    __syncthreads();
-    if (w == 0) {
-        a = l < nw ? s_a[l] : dfloat{0.0f, 0.0f};
-        b = l < nw ? s_b[l] : dfloat{0.0f, 0.0f};
-        a = warp_df_sum(a);
-        b = warp_df_sum(b);
-        if (l == 0) {
-            if (qa >= 0 && (a.hi != 0.0f || a.lo != 0.0f))
-                atomicAdd(acc_stripe(acc, qa), (double)a.hi + (double)a.lo);
-            if (qb >= 0 && (b.hi != 0.0f || b.lo != 0.0f))
-                atomicAdd(acc_stripe(acc, qb), (double)b.hi + (double)b.lo);
-        }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums of non-negative per-thread values a and b over each warp (a float32
+// tree: relative error at most 5 units in the last place for non-negative
+// terms); lane 0 adds each nonzero warp total in FP64 to the stripe of
+// quantity qa / qb (qb < 0: none) chosen by the warp's global index.  No
+// block-wide barrier, and the atomics spread over 32 lines.
+__device__ __forceinline__ void block_acc2(float a, float b, double* acc, int qa, int qb) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+        unsigned gw = (blockIdx.x * ((blockDim.x + 31) >> 5)) + (threadIdx.x >> 5);
+        double* st = acc + (gw & (kAccStripes - 1)) * kAccStride;
+        if (qa >= 0 && a != 0.0f) atomicAdd(st + qa, (double)a);
+        if (qb >= 0 && b != 0.0f) atomicAdd(st + qb, (double)b);
     }
 }
 
-__device__ __forceinline__ void block_acc1(dfloat a, double* acc, int qa) {
-    block_acc2(a, dfloat{0.0f, 0.0f}, acc, qa, -1);
+__device__ __forceinline__ void block_acc1(float a, double* acc, int qa) {
+    block_acc2(a, 0.0f, acc, qa, -1);
 }
+
+// a dfloat collapsed to the nearest float
+__device__ __forceinline__ float df_val(dfloat d) { return d.hi + d.lo; }
 
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
@@ -250,17 +271,12 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Block-wide max of non-negative v into the stripe of quantity q.
+// Max of non-negative v over each warp into the stripe of quantity q.
 __device__ __forceinline__ void block_max(float v, double* acc, int q) {
-    __shared__ float s_m[32];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
     v = warp_max(v);
-    __syncthreads();
-    if (l == 0) s_m[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = warp_max(l < nw ? s_m[l] : 0.0f);
-        if (l == 0) atomic_max_nonneg(acc_stripe(acc, q), (double)v);
+    if ((threadIdx.x & 31) == 0) {
+        unsigned gw = (blockIdx.x * ((blockDim.x + 31) >> 5)) + (threadIdx.x >> 5);
+        atomic_max_nonneg(acc + (gw & (kAccStripes - 1)) * kAccStride + q, (double)v);
     }
 }
 
@@ -309,6 +325,8 @@ struct Ctx {
     float *pin_dx = nullptr, *pin_dy = nullptr;
     float2* gpin = nullptr;
     float2* gW2 = nullptr;      // interleaved wirelength gradient accumulator (m_mov)
+    float2* pxy = nullptr;      // pin coordinates in slab order (slab_slots)
+    float2* pos2 = nullptr;     // interleaved cell centres (m_mov)
     double* acc = nullptr;
     int* err = nullptr;
     double* acc_host = nullptr;   // pinned mirror

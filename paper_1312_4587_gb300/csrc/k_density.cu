@@ -26,11 +26,14 @@ k_scatter(Grid g, int m, const float* __restrict__ x, const float* __restrict__ 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     Span s = cell_span(g, x[i], y[i], w[i], h[i]);
+    if (s.ilo > s.ihi || s.jlo > s.jhi) return;
+    const AxisOv ax = axis_ov(g.x0, g.wb, s.ilo, s.ihi, s.xl, s.xh);
+    const AxisOv ay = axis_ov(g.y0, g.hb, s.jlo, s.jhi, s.yl, s.yh);
     for (int j = s.jlo; j <= s.jhi; ++j) {
-        float oy = ov_len(g.y0, g.hb, j, s.yl, s.yh);
+        float oy = ov_at(ay, j);
         if (QUANT) {
             for (int k = s.ilo; k <= s.ihi; ++k) {
-                float a = __fmul_rn(ov_len(g.x0, g.wb, k, s.xl, s.xh), oy);
+                float a = __fmul_rn(ov_at(ax, k), oy);
                 long long q = __float2ll_rn(__fmul_rn(a, 4294967296.0f));
                 atomicAdd(Dq + (size_t)j * g.n + k, (unsigned long long)q);
             }
@@ -41,8 +44,7 @@ k_scatter(Grid g, int m, const float* __restrict__ x, const float* __restrict__ 
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     int k = 4 * q + t;
-                    v[t] = (k >= s.ilo && k <= s.ihi)
-                               ? __fmul_rn(ov_len(g.x0, g.wb, k, s.xl, s.xh), oy) : 0.0f;
+                    v[t] = (k >= s.ilo && k <= s.ihi) ? __fmul_rn(ov_at(ax, k), oy) : 0.0f;
                 }
                 atomicAdd(reinterpret_cast<float4*>(row + 4 * q), make_float4(v[0], v[1], v[2], v[3]));
             }
@@ -66,7 +68,7 @@ k_bin_ranges(Grid g, int m, const float* __restrict__ x, const float* __restrict
             cnt = (float)((s.ihi - s.ilo + 1) * (s.jhi - s.jlo + 1));
         }
     }
-    block_acc1(dfloat{cnt, 0.0f}, acc, ACC_CHARGE);
+    block_acc1(cnt, acc, ACC_CHARGE);
 }
 
 // Field gather (ADJ = false) or exact edge-difference adjoint (ADJ = true,
@@ -110,7 +112,7 @@ k_gather(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y
         gx[i] = sx;
         gy[i] = sy;
     }
-    block_acc1(dfloat{fabsf(sx) + fabsf(sy), 0.0f}, acc, ACC_GN_L1);
+    block_acc1(fabsf(sx) + fabsf(sy), acc, ACC_GN_L1);
 }
 
 // rho = (D + M) / A_b (formed on demand for fftpl_fields).

@@ -213,17 +213,39 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
     extern __shared__ float2 sm[];
     const int y0 = blockIdx.x * ROWS;
     dfloat tau = df_zero(), charge = df_zero();
-    for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
+    // ROWS*N values, 4 per thread and iteration (float4 loads), unrolled so
+    // that many loads are in flight
+    constexpr int V4 = ROWS * N / 4;
+#pragma unroll 4
+    for (int it = 0; it < (V4 + T - 1) / T; ++it) {
+        int q = threadIdx.x + it * T;
+        if (V4 % T != 0 && q >= V4) break;
+        int idx = 4 * q;
         int r = idx >> LOGN, x = idx & (N - 1);
         size_t b = (size_t)(y0 + r) * N + x;
-        float d = QUANT ? (float)Dq[b] * 2.3283064365386963e-10f : D[b];
-        float mm = M[b];
-        tau = df_add(tau, fmaxf(0.0f, d - (cap - mm)));
-        charge = df_add(charge, d + mm);
-        float rho = (d + mm) * inv_ab;
-        reinterpret_cast<float*>(sm + (r >> 1) * NP + pidx(mk_pos(x, N)))[r & 1] = rho;
+        float d4[4], m4[4];
+        float4 mv = *reinterpret_cast<const float4*>(M + b);
+        m4[0] = mv.x; m4[1] = mv.y; m4[2] = mv.z; m4[3] = mv.w;
+        if (QUANT) {
+            longlong2 q0 = *reinterpret_cast<const longlong2*>(Dq + b);
+            longlong2 q1 = *reinterpret_cast<const longlong2*>(Dq + b + 2);
+            d4[0] = (float)q0.x * 2.3283064365386963e-10f;
+            d4[1] = (float)q0.y * 2.3283064365386963e-10f;
+            d4[2] = (float)q1.x * 2.3283064365386963e-10f;
+            d4[3] = (float)q1.y * 2.3283064365386963e-10f;
+        } else {
+            float4 dv = *reinterpret_cast<const float4*>(D + b);
+            d4[0] = dv.x; d4[1] = dv.y; d4[2] = dv.z; d4[3] = dv.w;
+        }
+        float* row = reinterpret_cast<float*>(sm + (r >> 1) * NP);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            tau = df_add(tau, fmaxf(0.0f, d4[t] - (cap - m4[t])));
+            charge = df_add(charge, d4[t] + m4[t]);
+            row[2 * pidx(mk_pos(x + t, N)) + (r & 1)] = (d4[t] + m4[t]) * inv_ab;
+        }
     }
-    block_acc2(tau, charge, acc, ACC_TAU, ACC_CHARGE);
+    block_acc2(df_val(tau), df_val(charge), acc, ACC_TAU, ACC_CHARGE);
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, false);
     // split the packed spectra and apply the post-twiddle:
@@ -297,10 +319,19 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
     constexpr int NP = padded(N);
     extern __shared__ float2 sm[];
     const int u0 = blockIdx.x * ROWS;
-    for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
+    constexpr int V4 = ROWS * N / 4;
+#pragma unroll 4
+    for (int it = 0; it < (V4 + T - 1) / T; ++it) {
+        int q = threadIdx.x + it * T;
+        if (V4 % T != 0 && q >= V4) break;
+        int idx = 4 * q;
         int r = idx >> LOGN, y = idx & (N - 1);
-        float val = T1[(size_t)(u0 + r) * N + y];
-        reinterpret_cast<float*>(sm + (r >> 1) * NP + pidx(mk_pos(y, N)))[r & 1] = val;
+        float4 v = *reinterpret_cast<const float4*>(T1 + (size_t)(u0 + r) * N + y);
+        float* row = reinterpret_cast<float*>(sm + (r >> 1) * NP);
+        row[2 * pidx(mk_pos(y + 0, N)) + (r & 1)] = v.x;
+        row[2 * pidx(mk_pos(y + 1, N)) + (r & 1)] = v.y;
+        row[2 * pidx(mk_pos(y + 2, N)) + (r & 1)] = v.z;
+        row[2 * pidx(mk_pos(y + 3, N)) + (r & 1)] = v.w;
     }
     __syncthreads();
     fft_block<LOGN, NB / 2>(sm, tw, false);
@@ -367,7 +398,7 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
             where[i] = f * HALF + v;
         }
     }
-    block_acc1(energy, acc, ACC_N);
+    block_acc1(df_val(energy), acc, ACC_N);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < PI; ++i) {
@@ -415,6 +446,7 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __
     float* eys = reinterpret_cast<float*>(sm + NB * NP);  // E_y parked [ROWS][N]
     const int y0 = blockIdx.x * ROWS;
     // round A: buffer 2f holds psi of rows (2f, 2f+1), buffer 2f+1 holds E_y
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < (ROWS / 2) * HALF; idx += T) {
         int f = idx / HALF, u = idx % HALF;
         int un = (N - u) & (N - 1);
@@ -446,6 +478,7 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __
     __syncthreads();
     // round B: E_x rows (2 per buffer).  c[u'] = s[N-u'] (u' >= 1), c[0] = 0,
     // s[u] = w_u P[u]; E_x[x] = (-1)^x cosine-sum(c)[x].
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < (ROWS / 2) * HALF; idx += T) {
         int f = idx / HALF, u = idx % HALF;
         const float* Pa = PT + (size_t)(y0 + 2 * f) * N;

@@ -45,8 +45,7 @@ k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
         b.gW[i] = wx;
         b.gW[m + i] = wy;
     }
-    block_acc2(dfloat{fabsf(nx) + fabsf(ny), 0.0f}, dfloat{fabsf(wx) + fabsf(wy), 0.0f}, b.acc,
-               ACC_GN_L1, ACC_GW_L1);
+    block_acc2(fabsf(nx) + fabsf(ny), fabsf(wx) + fabsf(wy), b.acc, ACC_GN_L1, ACC_GW_L1);
     if (last_cta(b.counters + 0) && threadIdx.x == 0) ctrl_lambda(b.ctrl, b.acc);
 }
 
@@ -67,7 +66,7 @@ __global__ void __launch_bounds__(kCellThreads) k_loop_g(int m2, LoopBufs b) {
             dv = c * c;
         }
     }
-    block_acc2(dfloat{dg, 0.0f}, dfloat{dv, 0.0f}, b.acc, ACC_DG2, ACC_DV2);
+    block_acc2(dg, dv, b.acc, ACC_DG2, ACC_DV2);
     block_max(gi, b.acc, ACC_GINF);
     if (last_cta(b.counters + 1) && threadIdx.x == 0) ctrl_alpha(b.ctrl, b.acc);
 }

@@ -18,18 +18,143 @@ namespace fftpl {
 
 // Nets are re-laid at create time into slabs of up to 32 nets of one degree
 // d (slab = {first pin slot, d, net count}); pin k of the slab's net j sits
-// at slot base + 32 k + j.  One warp takes one slab, one lane one net: every
-// lane walks the same d pins (no divergence) and each pin load of the warp is
-// one contiguous 128-byte access.  The first kWaRegPins pins stay in registers
-// across the three passes; further pins are reloaded (L1 hits).
-constexpr int kWaRegPins = 8;
+// at slot base + 32 k + j.  Two kernels:
+//   k_pins  one thread per slot: pin coordinate = fl32(cell centre + offset)
+//           into pxy[slot] (independent loads, so the random position
+//           gathers overlap fully);
+//   k_wa    one warp per slab, one lane per net: every lane walks the same d
+//           pins (no divergence) and each pin read of the warp is one
+//           contiguous 256-byte access.
+// Slabs of degree 2..6 (the bulk of the nets) run a body specialised for
+// their degree with the pins and exponentials held in registers.
+
+// A pin on a fixed cell carries cell -1 and its absolute coordinate
+// fl32(fixed centre + offset) in place of the offset; padding slots carry -1
+// and offset 0.  Four consecutive slots per thread (16-byte loads), all
+// record loads issued before the position gathers.
+__global__ void __launch_bounds__(256)
+k_pins(int64_t slots4, const int4* __restrict__ pin_cell, const float4* __restrict__ pdx,
+       const float4* __restrict__ pdy, const float2* __restrict__ pos, float4* __restrict__ pxy,
+       const double* __restrict__ done) {
+    if (done && *done != 0.0) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= slots4) return;
+    int4 c = pin_cell[i];
+    float4 dx = pdx[i], dy = pdy[i];
+    const float2 z = make_float2(0.0f, 0.0f);
+    float2 p0 = c.x >= 0 ? pos[c.x] : z, p1 = c.y >= 0 ? pos[c.y] : z;
+    float2 p2 = c.z >= 0 ? pos[c.z] : z, p3 = c.w >= 0 ? pos[c.w] : z;
+    pxy[2 * i] = make_float4(__fadd_rn(p0.x, dx.x), __fadd_rn(p0.y, dy.x),
+                             __fadd_rn(p1.x, dx.y), __fadd_rn(p1.y, dy.y));
+    pxy[2 * i + 1] = make_float4(__fadd_rn(p2.x, dx.z), __fadd_rn(p2.y, dy.z),
+                                 __fadd_rn(p3.x, dx.w), __fadd_rn(p3.y, dy.w));
+}
+
+// (x, y) -> interleaved positions, so that one random 8-byte load (one
+// sector) fetches a pin's cell centre.
+__global__ void __launch_bounds__(256)
+k_interleave(int m, const float* __restrict__ x, const float* __restrict__ y,
+             float2* __restrict__ pos, const double* __restrict__ done) {
+    if (done && *done != 0.0) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) pos[i] = make_float2(x[i], y[i]);
+}
+
+// Per-net WA of one lane's net, D known at compile time (D > 0) or not
+// (D == 0: runtime degree d, pins re-read in each pass).  Adds W~ and the
+// HPWL term to wsum/hsum and sends each pin's gradient out.
+struct WaOut {
+    float2* gW;
+    const int* pin_cell;
+    const int* pin_slot;
+    float2* gpin;
+};
+
+template <int D, bool CSR>
+__device__ __forceinline__ void wa_net(const float2* __restrict__ pxy, int base, int d, float l2g,
+                                       float inv_g, const WaOut& o, dfloat& wsum, dfloat& hsum) {
+    constexpr int R = D > 0 ? D : 1;
+    float rx[R], ry[R], ex_p[R], ex_m[R], ey_p[R], ey_m[R];
+    const int dd = D > 0 ? D : d;
+    float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
+    if (D > 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            float2 p = pxy[base + 32 * k];
+            rx[k] = p.x;
+            ry[k] = p.y;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            Mx = fmaxf(Mx, rx[k]); mx = fminf(mx, rx[k]);
+            My = fmaxf(My, ry[k]); my = fminf(my, ry[k]);
+        }
+    } else {
+#pragma unroll 4
+        for (int k = 0; k < dd; ++k) {
+            float2 p = pxy[base + 32 * k];
+            Mx = fmaxf(Mx, p.x); mx = fminf(mx, p.x);
+            My = fmaxf(My, p.y); my = fminf(my, p.y);
+        }
+    }
+    float Spx = 0, Tpx = 0, Smx = 0, Tmx = 0, Spy = 0, Tpy = 0, Smy = 0, Tmy = 0;
+    auto sums = [&](float px, float py, float& apx, float& amx, float& apy, float& amy) {
+        float tpx = px - Mx, tmx = px - mx, tpy = py - My, tmy = py - my;
+        apx = exp2f(tpx * l2g); amx = exp2f(-tmx * l2g);
+        apy = exp2f(tpy * l2g); amy = exp2f(-tmy * l2g);
+        Spx += apx; Tpx = fmaf(tpx, apx, Tpx); Smx += amx; Tmx = fmaf(tmx, amx, Tmx);
+        Spy += apy; Tpy = fmaf(tpy, apy, Tpy); Smy += amy; Tmy = fmaf(tmy, amy, Tmy);
+    };
+    if (D > 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) sums(rx[k], ry[k], ex_p[k], ex_m[k], ey_p[k], ey_m[k]);
+    } else {
+#pragma unroll 4
+        for (int k = 0; k < dd; ++k) {
+            float2 p = pxy[base + 32 * k];
+            float a, b, c2, e;
+            sums(p.x, p.y, a, b, c2, e);
+        }
+    }
+    const float Wpx = Tpx / Spx, Wmx = Tmx / Smx, Wpy = Tpy / Spy, Wmy = Tmy / Smy;
+    const float isx = 1.0f / Spx, imx = 1.0f / Smx, isy = 1.0f / Spy, imy = 1.0f / Smy;
+    dfloat spanx = df_add({Mx, 0.0f}, -mx);
+    dfloat spany = df_add({My, 0.0f}, -my);
+    dfloat span = df_add(spanx, spany);
+    hsum = df_add(hsum, span);
+    wsum = df_add(df_add(wsum, span), (Wpx - Wmx) + (Wpy - Wmy));
+    auto emit = [&](int k, float px, float py, float apx, float amx, float apy, float amy) {
+        float tpx = px - Mx, tmx = px - mx, tpy = py - My, tmy = py - my;
+        float gxj = apx * isx * (1.0f + (tpx - Wpx) * inv_g) -
+                    amx * imx * (1.0f - (tmx - Wmx) * inv_g);
+        float gyj = apy * isy * (1.0f + (tpy - Wpy) * inv_g) -
+                    amy * imy * (1.0f - (tmy - Wmy) * inv_g);
+        if (CSR) {
+            int sl = o.pin_slot[base + 32 * k];
+            if (sl >= 0) o.gpin[sl] = make_float2(gxj, gyj);
+        } else {
+            int c = o.pin_cell[base + 32 * k];
+            if (c >= 0) atomicAdd(o.gW + c, make_float2(gxj, gyj));
+        }
+    };
+    if (D > 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) emit(k, rx[k], ry[k], ex_p[k], ex_m[k], ey_p[k], ey_m[k]);
+    } else {
+#pragma unroll 4
+        for (int k = 0; k < dd; ++k) {
+            float2 p = pxy[base + 32 * k];
+            float tpx = p.x - Mx, tmx = p.x - mx, tpy = p.y - My, tmy = p.y - my;
+            emit(k, p.x, p.y, exp2f(tpx * l2g), exp2f(-tmx * l2g), exp2f(tpy * l2g),
+                 exp2f(-tmy * l2g));
+        }
+    }
+}
 
 template <bool CSR>
-__global__ void __launch_bounds__(kWaThreads)
+__global__ void __launch_bounds__(kWaThreads, 4)
 k_wa(int nslabs, const int4* __restrict__ slabs, const int* __restrict__ pin_cell,
-     const float* __restrict__ pdx, const float* __restrict__ pdy, int m_mov,
-     const float* __restrict__ x, const float* __restrict__ y, const float* __restrict__ fx,
-     const float* __restrict__ fy, float gamma, const double* __restrict__ gamma_dev,
+     const float2* __restrict__ pxy, float gamma, const double* __restrict__ gamma_dev,
      float2* __restrict__ gW, const int* __restrict__ pin_slot, float2* __restrict__ gpin,
      double* __restrict__ acc, const double* __restrict__ done) {
     if (done && *done != 0.0) return;
@@ -37,84 +162,24 @@ k_wa(int nslabs, const int4* __restrict__ slabs, const int* __restrict__ pin_cel
     const int lane = threadIdx.x & 31;
     if (gamma_dev) gamma = (float)*gamma_dev;
     const float inv_g = 1.0f / gamma;
+    // exp(t / g) = exp2(t * log2(e) / g)
+    const float l2g = (float)(1.4426950408889634 / (double)gamma);
     const int4 sl = warp < nslabs ? slabs[warp] : make_int4(0, 0, 0, 0);
     const int base = sl.x + lane, d = sl.y;
-    const bool act = lane < sl.z;
-    auto load = [&](int k, float& px, float& py, int& c) {
-        int i = base + 32 * k;
-        c = pin_cell[i];
-        float cx, cy;
-        if (c < m_mov) { cx = x[c]; cy = y[c]; }
-        else { cx = fx[c - m_mov]; cy = fy[c - m_mov]; }
-        px = __fadd_rn(cx, pdx[i]);
-        py = __fadd_rn(cy, pdy[i]);
-    };
-    float rx[kWaRegPins], ry[kWaRegPins];
-    int rc[kWaRegPins];
-    float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
+    const WaOut o{gW, pin_cell, pin_slot, gpin};
     dfloat wsum = df_zero(), hsum = df_zero();
-    if (act) {
-#pragma unroll
-        for (int k = 0; k < kWaRegPins; ++k) {
-            if (k < d) {
-                load(k, rx[k], ry[k], rc[k]);
-                Mx = fmaxf(Mx, rx[k]); mx = fminf(mx, rx[k]);
-                My = fmaxf(My, ry[k]); my = fminf(my, ry[k]);
-            }
-        }
-        for (int k = kWaRegPins; k < d; ++k) {
-            float px, py; int c;
-            load(k, px, py, c);
-            Mx = fmaxf(Mx, px); mx = fminf(mx, px);
-            My = fmaxf(My, py); my = fminf(my, py);
-        }
-        float Spx = 0, Tpx = 0, Smx = 0, Tmx = 0, Spy = 0, Tpy = 0, Smy = 0, Tmy = 0;
-        auto accum = [&](float px, float py) {
-            float tpx = px - Mx, tmx = px - mx, tpy = py - My, tmy = py - my;
-            float apx = expf(tpx * inv_g), amx = expf(-tmx * inv_g);
-            float apy = expf(tpy * inv_g), amy = expf(-tmy * inv_g);
-            Spx += apx; Tpx = fmaf(tpx, apx, Tpx); Smx += amx; Tmx = fmaf(tmx, amx, Tmx);
-            Spy += apy; Tpy = fmaf(tpy, apy, Tpy); Smy += amy; Tmy = fmaf(tmy, amy, Tmy);
-        };
-#pragma unroll
-        for (int k = 0; k < kWaRegPins; ++k)
-            if (k < d) accum(rx[k], ry[k]);
-        for (int k = kWaRegPins; k < d; ++k) {
-            float px, py; int c;
-            load(k, px, py, c);
-            accum(px, py);
-        }
-        const float Wpx = Tpx / Spx, Wmx = Tmx / Smx, Wpy = Tpy / Spy, Wmy = Tmy / Smy;
-        const float isx = 1.0f / Spx, imx = 1.0f / Smx, isy = 1.0f / Spy, imy = 1.0f / Smy;
-        dfloat spanx = df_add({Mx, 0.0f}, -mx);
-        dfloat spany = df_add({My, 0.0f}, -my);
-        hsum = df_add(spanx, spany);
-        wsum = df_add(hsum, (Wpx - Wmx) + (Wpy - Wmy));
-        auto emit = [&](int k, float px, float py, int c) {
-            float tpx = px - Mx, tmx = px - mx, tpy = py - My, tmy = py - my;
-            float apx = expf(tpx * inv_g), amx = expf(-tmx * inv_g);
-            float apy = expf(tpy * inv_g), amy = expf(-tmy * inv_g);
-            float gxj = apx * isx * (1.0f + (tpx - Wpx) * inv_g) -
-                        amx * imx * (1.0f - (tmx - Wmx) * inv_g);
-            float gyj = apy * isy * (1.0f + (tpy - Wpy) * inv_g) -
-                        amy * imy * (1.0f - (tmy - Wmy) * inv_g);
-            if (CSR) {
-                int sl2 = pin_slot[base + 32 * k];
-                if (sl2 >= 0) gpin[sl2] = make_float2(gxj, gyj);
-            } else if (c < m_mov) {
-                atomicAdd(gW + c, make_float2(gxj, gyj));
-            }
-        };
-#pragma unroll
-        for (int k = 0; k < kWaRegPins; ++k)
-            if (k < d) emit(k, rx[k], ry[k], rc[k]);
-        for (int k = kWaRegPins; k < d; ++k) {
-            float px, py; int c;
-            load(k, px, py, c);
-            emit(k, px, py, c);
+    if (lane < sl.z) {
+        // d is the same for the whole warp, so this switch does not diverge
+        switch (d) {
+            case 2: wa_net<2, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
+            case 3: wa_net<3, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
+            case 4: wa_net<4, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
+            case 5: wa_net<5, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
+            case 6: wa_net<6, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
+            default: wa_net<0, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
         }
     }
-    block_acc2(wsum, hsum, acc, ACC_W, ACC_HPWL);
+    block_acc2(df_val(wsum), df_val(hsum), acc, ACC_W, ACC_HPWL);
 }
 
 // Per-cell kernel: density gradient by the field gather (q.E of Eq. 7),
@@ -153,8 +218,7 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
         gWx[i] = wx;
         gWy[i] = wy;
     }
-    block_acc2(dfloat{fabsf(nx) + fabsf(ny), 0.0f}, dfloat{fabsf(wx) + fabsf(wy), 0.0f}, acc,
-               ACC_GN_L1, ACC_GW_L1);
+    block_acc2(fabsf(nx) + fabsf(ny), fabsf(wx) + fabsf(wy), acc, ACC_GN_L1, ACC_GW_L1);
 }
 
 // Deterministic pin-to-cell sum on its own (fftpl_wa in CSR mode).
@@ -172,7 +236,7 @@ k_pin_sum(int m, const int* __restrict__ cell_pin_ptr, const float2* __restrict_
         gx[i] = wx;
         gy[i] = wy;
     }
-    block_acc1(dfloat{fabsf(wx) + fabsf(wy), 0.0f}, acc, ACC_GW_L1);
+    block_acc1(fabsf(wx) + fabsf(wy), acc, ACC_GW_L1);
 }
 
 // Splits the interleaved atomic accumulator into gx, gy and adds ||g||_1.
@@ -187,7 +251,7 @@ k_split(int m, const float2* __restrict__ gW2, float* __restrict__ gx, float* __
         gy[i] = g.y;
         v = fabsf(g.x) + fabsf(g.y);
     }
-    block_acc1(dfloat{v, 0.0f}, acc, ACC_GW_L1);
+    block_acc1(v, acc, ACC_GW_L1);
 }
 
 static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }
@@ -195,16 +259,23 @@ static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                            const double* gamma_dev, const double* done, cudaStream_t s) {
     if (c.nslabs <= 0) return cudaSuccess;
+    if (c.m_mov > 0) {
+        k_interleave<<<nblk(c.m_mov, 256), 256, 0, s>>>(c.m_mov, x, y, c.pos2, done);
+        c.launches++;
+    }
+    int64_t slots4 = c.slab_slots / 4;   // slab sizes are multiples of 64 slots
+    k_pins<<<(int)((slots4 + 255) / 256), 256, 0, s>>>(
+        slots4, reinterpret_cast<const int4*>(c.pin_cell), reinterpret_cast<const float4*>(c.pin_dx),
+        reinterpret_cast<const float4*>(c.pin_dy), c.pos2, reinterpret_cast<float4*>(c.pxy), done);
+    c.launches++;
     const int wpb = kWaThreads / 32;
     int nb = nblk(c.nslabs, wpb);
     if (c.opt.deterministic)
-        k_wa<true><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, c.pin_cell, c.pin_dx, c.pin_dy,
-                                             c.m_mov, x, y, c.fix_x, c.fix_y, gamma, gamma_dev,
-                                             nullptr, c.pin_slot, c.gpin, c.acc, done);
+        k_wa<true><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, c.pin_cell, c.pxy, gamma,
+                                             gamma_dev, nullptr, c.pin_slot, c.gpin, c.acc, done);
     else
-        k_wa<false><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, c.pin_cell, c.pin_dx, c.pin_dy,
-                                              c.m_mov, x, y, c.fix_x, c.fix_y, gamma, gamma_dev,
-                                              c.gW2, nullptr, nullptr, c.acc, done);
+        k_wa<false><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, c.pin_cell, c.pxy, gamma,
+                                              gamma_dev, c.gW2, nullptr, nullptr, c.acc, done);
     c.launches++;
     return cudaGetLastError();
 }
