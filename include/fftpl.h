@@ -268,6 +268,38 @@ fftpl_status fftpl_stage_times(fftpl_t h, double* ms, int64_t* launches, int32_t
 /* Number of kernels this handle has launched (all stages). */
 int64_t fftpl_launch_count(fftpl_t h);
 
+/* --------------------------------------------- allocation-free solve */
+
+/* Largest grid fftpl_solve_noalloc accepts. */
+#define FFTPL_NOALLOC_MAX_N 1024
+
+/* Poisson solve of a caller-supplied density map, for callers that cannot
+ * allocate device memory themselves: code running where cudaMalloc is not
+ * allowed or not wanted (inside a host callback, a real-time or
+ * preallocated-memory service, an allocator-less plugin host), or where an
+ * allocation could fail or stall mid-run.  The paper has no counterpart: it
+ * is the same spectral solve as the density path, offered without a handle.
+ *
+ * rho: device, n*n float32 bin densities, row-major [y][x].  psi, ex, ey:
+ * device outputs of the same layout (potential and field of Eqs. 11-12 for
+ * a region of size Lx x Ly; the (0,0) mode of rho is dropped).  N: host,
+ * may be NULL; if given, the call synchronises the stream and stores
+ * 1/2 (Lx Ly / n^2) sum rho psi there.  n: power of two in [16,
+ * FFTPL_NOALLOC_MAX_N]; larger n returns FFTPL_EINVAL.  stream: a
+ * cudaStream_t (NULL: legacy default stream).
+ *
+ * Memory: the intermediate transforms live in one fixed array in the
+ * library's device image (about 20 MiB), which every GPU that loads the
+ * library keeps until the process exits; the call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  The first call on a
+ * device looks up that array's device address and sets up the kernels for
+ * it, so make the first call on each device before any stream capture.
+ * Every call shares the array: calls that may overlap on the GPU (different
+ * streams, different host threads) race; serialise them, e.g. on one
+ * stream. */
+fftpl_status fftpl_solve_noalloc(const float* rho, int32_t n, double Lx, double Ly, float* psi,
+                                 float* ex, float* ey, double* N, void* stream);
+
 /* ------------------------------------------------------- test hooks */
 
 /* Host-side fault injection: the k-th device allocation from now fails with

@@ -260,6 +260,8 @@ float* scratch(Ctx& c, int which) { return (which < 2 ? c.gN : c.gW) + (which & 
 
 }  // namespace
 
+void fftpl::set_global_error(const std::string& msg) { g_create_error = msg; }
+
 // =========================================================================
 extern "C" {
 

@@ -358,6 +358,9 @@ struct Ctx {
     size_t dev_bytes = 0;
 };
 
+// Sets the text fftpl_last_error(NULL) returns on this thread.
+void set_global_error(const std::string& msg);
+
 // ------------------------------------------------------------ launchers
 // (each returns the CUDA error of the launch)
 void prepare_spectral(int logn);

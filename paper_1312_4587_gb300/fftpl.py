@@ -120,6 +120,7 @@ def lib():
             "fftpl_stage_times": (S, [_H, _P, _P, C.c_int32]),
             "fftpl_launch_count": (C.c_int64, [_H]),
             "fftpl_debug_fail_alloc_after": (None, [C.c_int32]),
+            "fftpl_solve_noalloc": (S, [_P, C.c_int32, C.c_double, C.c_double, _P, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -337,6 +338,20 @@ def fftpl_stage_times(h, reset=False):
 
 def fftpl_launch_count(h):
     return int(lib().fftpl_launch_count(h))
+
+
+def fftpl_solve_noalloc(rho, n, Lx, Ly, psi, ex, ey, want_N=False, stream=None):
+    """Allocation-free solve of a device density map rho ([n, n] float32 CUDA
+    tensor) into caller-owned psi, ex, ey; returns N if want_N."""
+    N = C.c_double(0.0)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().fftpl_solve_noalloc(_dptr(rho), C.c_int32(int(n)), C.c_double(Lx),
+                                     C.c_double(Ly), _dptr(psi), _dptr(ex), _dptr(ey),
+                                     C.byref(N) if want_N else None, C.c_void_p(int(stream or 0))),
+           None)
+    return float(N.value) if want_N else None
 
 
 def fftpl_debug_fail_alloc_after(k):
