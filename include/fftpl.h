@@ -198,6 +198,19 @@ fftpl_status fftpl_density(fftpl_t h, const float* x, const float* y, double* N,
 fftpl_status fftpl_density_adjoint(fftpl_t h, const float* x, const float* y, double* N,
                                    float* gx, float* gy);
 
+/* The two halves of fftpl_density, for callers that differentiate N
+ * themselves (an autograd backward).  fftpl_energy: scatter and spectral
+ * solve only (Section III: density, Eqs. 9-12), energy N to *N (host; the
+ * call synchronises when N is non-NULL).  fftpl_gather: the density
+ * gradient at (x, y) from the maps of the last density evaluation on this
+ * handle (FFTPL_ESTATE if there is none): mode 0 the field gather
+ * -sum_b ov(i,b) E_b (q.E of Eq. 7), mode 1 the exact derivative of the
+ * binned N (as fftpl_density_adjoint).  x, y must be the positions that
+ * evaluation used. */
+fftpl_status fftpl_energy(fftpl_t h, const float* x, const float* y, double* N);
+fftpl_status fftpl_gather(fftpl_t h, const float* x, const float* y, int32_t mode, float* gx,
+                          float* gy);
+
 /* Weighted-average wirelength (Eq. 3) and its gradient; HPWL (Eq. 1) as a
  * by-product.  gx, gy device outputs (m_mov), may be NULL.  W host output:
  * non-NULL synchronises. */

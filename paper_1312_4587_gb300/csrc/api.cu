@@ -184,7 +184,7 @@ struct Stage {
 };
 
 // ---------------------------------------------------------------- evaluation
-enum { EV_DENSITY = 1, EV_WA = 2, EV_ADJOINT = 4 };
+enum { EV_DENSITY = 1, EV_WA = 2, EV_ADJOINT = 4, EV_NO_GATHER = 8 };
 
 // Enqueues one evaluation; gradients must be non-null device arrays.
 fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, int what,
@@ -214,7 +214,7 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
         { Stage st(c, 3, s); CK(launch_rows_inv(c, s)); }
     }
     if (wa) CK(cudaStreamWaitEvent(s, c.ev_join, 0));
-    {
+    if (!(what & EV_NO_GATHER)) {
         Stage st(c, 5, s);
         if (dens && wa && !(what & EV_ADJOINT)) {
             CK(launch_cells(c, x, y, gNx, gNy, gWx, gWy, s));
@@ -571,6 +571,29 @@ fftpl_status fftpl_density_adjoint(fftpl_t h, const float* x, const float* y, do
         TRY(read_report(c, &r));
         *N = r.N;
     }
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_energy(fftpl_t h, const float* x, const float* y, double* N) {
+    if (!h || (h->m_mov > 0 && (!x || !y))) return h ? set_err(*h, FFTPL_EINVAL, "null positions") : FFTPL_EINVAL;
+    Ctx& c = *h;
+    TRY(enqueue_eval(c, x, y, 0.0f, EV_DENSITY | EV_NO_GATHER, nullptr, nullptr, nullptr, nullptr));
+    if (N) {
+        fftpl_eval_report r;
+        TRY(read_report(c, &r));
+        *N = r.N;
+    }
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl_gather(fftpl_t h, const float* x, const float* y, int32_t mode, float* gx,
+                          float* gy) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (c.m_mov > 0 && (!x || !y || !gx || !gy)) return set_err(c, FFTPL_EINVAL, "null argument");
+    if (mode != 0 && mode != 1) return set_err(c, FFTPL_EINVAL, "mode must be 0 or 1");
+    if (!c.fields_valid) return set_err(c, FFTPL_ESTATE, "no density evaluation yet");
+    CK(launch_gather(c, x, y, gx, gy, mode == 1, c.stream));
     return FFTPL_OK;
 }
 

@@ -105,6 +105,8 @@ def lib():
             "fftpl_density": (S, [_H, _P, _P, _P, _P, _P]),
             "fftpl_density_adjoint": (S, [_H, _P, _P, _P, _P, _P]),
             "fftpl_wa": (S, [_H, _P, _P, C.c_float, _P, _P, _P]),
+            "fftpl_energy": (S, [_H, _P, _P, _P]),
+            "fftpl_gather": (S, [_H, _P, _P, C.c_int32, _P, _P]),
             "fftpl_eval": (S, [_H, _P, _P, C.c_float, _P, _P, _P, _P, _P]),
             "fftpl_eval_host": (S, [_H, _P, _P, C.c_float, _P, _P, _P, _P, _P]),
             "fftpl_report": (S, [_H, _P]),
@@ -241,6 +243,17 @@ def fftpl_density_adjoint(h, x, y, gx=None, gy=None, sync=True):
     _check(lib().fftpl_density_adjoint(h, _dptr(x), _dptr(y), C.byref(N) if sync else None,
                                        _dptr(gx), _dptr(gy)), h)
     return float(N.value) if sync else None
+
+
+def fftpl_energy(h, x, y, sync=True):
+    N = C.c_double(0.0)
+    _check(lib().fftpl_energy(h, _dptr(x), _dptr(y), C.byref(N) if sync else None), h)
+    return float(N.value) if sync else None
+
+
+def fftpl_gather(h, x, y, gx, gy, mode=0):
+    _check(lib().fftpl_gather(h, _dptr(x), _dptr(y), C.c_int32(int(mode)), _dptr(gx), _dptr(gy)),
+           h)
 
 
 def fftpl_wa(h, x, y, gamma, gx=None, gy=None, sync=True):

@@ -1,0 +1,124 @@
+"""The placement loop (Algorithm 1 with the Nesterov step and the parameter
+control of Section IV-A) on the GPU against the oracle's loop.
+
+FP32 and FP64 trajectories of a nonlinear iteration drift apart, so exact
+parity is asserted on the first 10 iterations (positions within 1e-4
+relative L2; sums W~, HPWL, N and lambda within 1e-4 relative; the overflow
+within 1e-4 absolute, as it sums the positive parts of D_b - cap_b, which
+jump when a cell crosses into a full bin; the maxima alpha and step_max, which follow whichever
+cell is extreme, within 1e-3) and the 200-iteration run is compared with an
+ensemble of oracle runs from starts perturbed by 1e-6 relative (float32
+noise): the oracle itself spreads by about 3 % in final HPWL there, so the
+GPU result must lie within twice that spread of the ensemble mean.
+
+The reference HPWL change of the lambda update is scaled to the design
+(3.5e5 times this design's starting HPWL over the 210K-cell instance's),
+as the constant of Section IV-A is quoted for ISPD-sized circuits.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1312_4587_gb300 import fftpl
+    fftpl.lib()
+    return fftpl
+
+
+def run_gpu(F, inst, iters, **opts):
+    import torch
+    with F.Problem(inst, **opts) as p:
+        x0 = torch.from_numpy(inst.x).cuda()
+        y0 = torch.from_numpy(inst.y).cuda()
+        F.fftpl_place_init(p.h, x0, y0)
+        rows, ran = F.fftpl_step(p.h, iters)
+        x = torch.empty_like(x0); y = torch.empty_like(y0)
+        F.fftpl_place_positions(p.h, x, y)
+        return x.cpu().numpy(), y.cpu().numpy(), rows, ran
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("schedule", [False, True])
+def test_first_iterations_match_oracle(F, schedule):
+    inst = synth.make_instance("tiny")
+    gf = 0.0 if schedule else inst.gamma
+    ox, oy, orows, oran = oracle.nesterov(inst, 10, gamma_fixed=gf)
+    gx, gy, grows, gran = run_gpu(F, inst, 10, gamma_fixed=gf)
+    assert gran == oran == 10
+    assert rel(np.concatenate([gx, gy]), np.concatenate([ox, oy])) < 1e-4
+    for k in range(10):
+        for key, rtol, atol in (("hpwl", 1e-4, 0), ("W", 1e-4, 0), ("N", 1e-4, 0),
+                                ("lam", 1e-4, 0), ("gamma", 1e-4, 0), ("tau", 0, 1e-4),
+                                ("alpha", 1e-3, 0), ("step_max", 1e-3, 0)):
+            a, b = grows[k][key], orows[k][key]
+            assert abs(a - b) <= rtol * abs(b) + atol, (k, key, a, b)
+
+
+def start_hpwl(inst):
+    return oracle.wa(inst.net_ptr, inst.pin_cell, inst.pin_dx, inst.pin_dy, inst.m_mov,
+                     inst.x, inst.y, inst.gamma, inst.fix_x, inst.fix_y)["hpwl"]
+
+
+def scaled_dw_ref(inst):
+    return 3.5e5 * start_hpwl(inst) / start_hpwl(synth.make_instance("large"))
+
+
+def test_two_hundred_iterations_statistics(F):
+    inst = synth.make_instance("tiny")
+    dw = scaled_dw_ref(inst)
+    ens = []
+    for s in range(4):
+        rng = np.random.default_rng(s)
+        xp = (inst.x * (1 + 1e-6 * rng.standard_normal(inst.x.size))).astype(np.float32)
+        _, _, rows, _ = oracle.nesterov(inst, 200, dw_ref=dw, x=xp)
+        ens.append((rows[49]["hpwl"], rows[-1]["hpwl"], rows[-1]["tau"]))
+    ens = np.array(ens)
+    gx, gy, grows, ran = run_gpu(F, inst, 200, dw_ref=dw)
+    assert ran == 200
+    for col, k in ((0, 49), (1, 199)):
+        mean = ens[:, col].mean()
+        spread = max((ens[:, col].max() - ens[:, col].min()) / mean, 0.01)
+        assert abs(grows[k]["hpwl"] - mean) <= 2 * spread * mean, (k, grows[k]["hpwl"], ens[:, col])
+    assert abs(grows[-1]["tau"] - ens[:, 2].mean()) <= 0.01
+    # HPWL falls well below the start while the overflow goes to ~0
+    assert grows[49]["hpwl"] < 0.75 * grows[0]["hpwl"] and grows[49]["tau"] < 0.01
+    m = inst.m_mov
+    assert np.all(gx - inst.w[:m] / 2 >= -1e-4) and np.all(gx + inst.w[:m] / 2 <= 128 + 1e-4)
+
+
+def test_stop_on_overflow(F):
+    inst = synth.make_instance("tiny")
+    _, _, rows, ran = run_gpu(F, inst, 200, stop_on_tau=1, tau_stop=0.2)
+    assert ran < 200 and rows[-1]["tau"] <= 0.2
+    assert all(r["tau"] > 0.2 for r in rows[:-1])
+
+
+def test_state_save_and_resume(F):
+    """Checkpoint/resume: in deterministic mode a resumed run is bit-identical."""
+    import torch
+    inst = synth.make_instance("tiny")
+    with F.Problem(inst, deterministic=1) as p:
+        x0 = torch.from_numpy(inst.x).cuda(); y0 = torch.from_numpy(inst.y).cuda()
+        F.fftpl_place_init(p.h, x0, y0)
+        F.fftpl_step(p.h, 7)
+        state = F.fftpl_state_save(p.h)
+        rows_a, _ = F.fftpl_step(p.h, 9)
+        xa = torch.empty_like(x0); ya = torch.empty_like(y0)
+        F.fftpl_place_positions(p.h, xa, ya)
+        F.fftpl_state_load(p.h, state)
+        rows_b, _ = F.fftpl_step(p.h, 9)
+        xb = torch.empty_like(x0); yb = torch.empty_like(y0)
+        F.fftpl_place_positions(p.h, xb, yb)
+    assert torch.equal(xa, xb) and torch.equal(ya, yb)
+    assert [r["hpwl"] for r in rows_a] == [r["hpwl"] for r in rows_b]
