@@ -168,6 +168,40 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def run_serving(args):
+    """Serving stream: Poisson arrivals (50 jobs/s) of placement jobs with
+    5K-500K cells (bins the next power of two >= sqrt(cells), 12 % macros),
+    300 iterations each, under a 150 GB budget, with continuous batching;
+    then the same jobs one at a time for comparison."""
+    import numpy as np
+
+    import synth
+    from paper_1312_4587_gb300 import serve
+
+    rng = np.random.default_rng(1316)
+    pool = []
+    for k in range(args.serving_pool):
+        cfg = synth.serving_job_config(rng)
+        pool.append(synth.make_instance(cfg.name, seed=2000 + k, cfg=cfg))
+    jobs = [pool[k % len(pool)] for k in range(args.serving_jobs)]
+    arrivals = serve.poisson_arrivals(rng, len(jobs), args.serving_rate)
+    out = {"jobs": len(jobs), "distinct_instances": len(pool), "arrival_rate_per_s": args.serving_rate,
+           "iters_per_job": args.serving_iters, "budget_GB": 150,
+           "cells": [int(min(j.m_mov for j in pool)), int(max(j.m_mov for j in pool))]}
+    with serve.Server(budget_bytes=150 << 30, max_active=64, iters_per_tick=5) as s:
+        st, _ = serve.run_stream(jobs, arrivals, args.serving_iters, s)
+    out.update({"jobs_per_s": st["jobs_per_s"], "iter_p50_ms": st["iter_p50_ms"],
+                "iter_p99_ms": st["iter_p99_ms"], "job_p50_ms": st["job_p50_ms"],
+                "job_p99_ms": st["job_p99_ms"], "peak_active": st["peak_active"],
+                "peak_device_GB": st["peak_device_bytes"] / 2**30, "failed": st["failed"]})
+    # the same jobs one at a time, back to back (all submitted at once)
+    with serve.Server(budget_bytes=150 << 30, max_active=1, iters_per_tick=5) as s:
+        st1, _ = serve.run_stream(jobs, np.zeros(len(jobs)), args.serving_iters, s)
+    out["alone"] = {"jobs_per_s": st1["jobs_per_s"], "iter_p50_ms": st1["iter_p50_ms"],
+                    "iter_p99_ms": st1["iter_p99_ms"]}
+    return out
+
+
 def cpu_baseline_sample(inst):
     """The oracle as it stands, one evaluation of the same instance."""
     import oracle
@@ -286,6 +320,8 @@ def run_ours(args, ws, rank, local):
                             "peak_kind": peak_kind}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(inst)
+    if rank == 0 and ws == 1 and args.serving_jobs > 0:
+        line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     prob.close()
@@ -301,6 +337,11 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=200,
+                    help="jobs in the serving stream (0: skip; the full stream is 2000)")
+    ap.add_argument("--serving-pool", type=int, default=16)
+    ap.add_argument("--serving-rate", type=float, default=50.0)
+    ap.add_argument("--serving-iters", type=int, default=300)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if ws > 1:

@@ -281,6 +281,79 @@ fftpl_status fftpl_stage_times(fftpl_t h, double* ms, int64_t* launches, int32_t
 /* Number of kernels this handle has launched (all stages). */
 int64_t fftpl_launch_count(fftpl_t h);
 
+/* ------------------------------------------------------------ serving */
+
+/* A stream of placement jobs served with continuous batching (build system
+ * pattern; the paper places one design at a time).  Each job is one
+ * instance plus start positions and an iteration count; it runs Algorithm 1
+ * with the Nesterov step (as fftpl_step).  fftpl_server_tick admits queued
+ * jobs while their device memory fits the budget and a slot is free, then
+ * launches iters_per_tick iterations of every active job, each job on its
+ * own stream so that jobs of different sizes run concurrently on the device,
+ * waits for them, and retires finished jobs (final positions copied to the
+ * host, device memory released).  Jobs that arrive while others run join at
+ * the next tick.  With dry_run the server executes nothing on a GPU: each
+ * launch only advances the job's count (admission, budget and latency
+ * bookkeeping can be exercised on any host, with fftpl_server_set_clock). */
+
+typedef struct fftpl_server* fftpl_server_t;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device memory all active jobs may hold */
+    int32_t max_active;       /* at most this many jobs on the device */
+    int32_t iters_per_tick;   /* loop iterations per job and tick (>= 1) */
+    int32_t deterministic;    /* run every job in deterministic mode */
+    int32_t dry_run;          /* bookkeeping only, no device work */
+    int32_t reserved[4];
+} fftpl_server_options;
+
+enum { FFTPL_JOB_QUEUED = 0, FFTPL_JOB_ACTIVE = 1, FFTPL_JOB_DONE = 2, FFTPL_JOB_FAILED = 3 };
+
+typedef struct {
+    int64_t id;
+    int32_t state;           /* FFTPL_JOB_* */
+    int32_t iters_done;
+    int32_t m_mov, n;
+    double t_submit, t_admit, t_done;   /* seconds on the server's clock */
+    double hpwl, tau;        /* at the job's last iteration (0 in dry runs) */
+    size_t device_bytes;     /* held while active */
+} fftpl_job_info;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int32_t active, queued, peak_active;
+    size_t peak_device_bytes;
+    double wall_s;                       /* first submit to last completion */
+    double jobs_per_s;                   /* completed / wall_s */
+    double iter_p50_ms, iter_p99_ms;     /* per-iteration latency seen by a job:
+                                            time since its previous iterations
+                                            completed, per iteration */
+    double job_p50_ms, job_p99_ms;       /* submit to completion */
+} fftpl_server_stats;
+
+void fftpl_server_default_options(fftpl_server_options* opt);
+/* Device-memory estimate of one job, used for admission. */
+size_t fftpl_estimate_bytes(int32_t n, int32_t m_mov, int32_t m_fix, int32_t E, int64_t P,
+                            int32_t iters, int32_t deterministic);
+fftpl_status fftpl_server_create(const fftpl_server_options* opt, fftpl_server_t* out);
+void fftpl_server_destroy(fftpl_server_t s);
+/* Queues a job; all host arrays are deep-copied (as fftpl_create); x0, y0
+ * are host start positions (m_mov).  *id receives the job id. */
+fftpl_status fftpl_server_submit(fftpl_server_t s, const fftpl_region* region, int32_t n,
+                                 const fftpl_cells* cells, const fftpl_nets* nets,
+                                 const fftpl_pins* pins, const fftpl_options* opt,
+                                 const float* x0, const float* y0, int32_t iters, int64_t* id);
+/* One round of admit / launch / retire (synchronises the device). */
+fftpl_status fftpl_server_tick(fftpl_server_t s, int32_t* active, int32_t* queued);
+/* Job state; x, y (host, m_mov, may be NULL) receive the final positions
+ * once the job is done. */
+fftpl_status fftpl_server_job(fftpl_server_t s, int64_t id, fftpl_job_info* info, float* x,
+                              float* y);
+fftpl_status fftpl_server_report(fftpl_server_t s, fftpl_server_stats* out);
+/* Uses now_s as the clock from here on (now_s < 0: back to the steady
+ * clock). */
+fftpl_status fftpl_server_set_clock(fftpl_server_t s, double now_s);
+
 /* --------------------------------------------- allocation-free solve */
 
 /* Largest grid fftpl_solve_noalloc accepts. */

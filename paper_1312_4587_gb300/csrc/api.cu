@@ -486,6 +486,16 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     CK(cudaMemcpyAsync(c.tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.ph, ph.data(), (n + 1) * sizeof(float2), cudaMemcpyHostToDevice, s));
     TRY(build_slabs(c, nets, pins, cells->fix_x, cells->fix_y));
+    if (c.opt.deterministic) {
+        // capacity in blocks of every kernel that reduces on each stream
+        long long cap0 = std::max<long long>((long long)n / 4, (2LL * c.m_mov + kCellThreads - 1) / kCellThreads);
+        long long cap1 = ((long long)c.nslabs + kWaThreads / 32 - 1) / (kWaThreads / 32);
+        c.det_cap[0] = (int)std::max<long long>(cap0, 1);
+        c.det_cap[1] = (int)std::max<long long>(cap1, 1);
+        TRY(dalloc(c, &c.det_part, 2 * ((size_t)c.det_cap[0] + c.det_cap[1])));
+        TRY(dalloc(c, &c.det_ticket, 4));
+        CK(cudaMemsetAsync(c.det_ticket, 0, 4 * sizeof(unsigned), s));
+    }
     // fixed-cell map M = rho_t F (Section III-B), order-free int64 sums
     {
         long long* q = nullptr;
@@ -787,7 +797,8 @@ fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
     return FFTPL_OK;
 }
 
-static fftpl_status enqueue_iteration(Ctx& c) {
+extern "C++" {
+fftpl_status fftpl::loop_enqueue(Ctx& c) {
     cudaStream_t s = c.stream;
     size_t nn = (size_t)c.n * c.n;
     const float* vx = c.v;
@@ -821,27 +832,34 @@ static fftpl_status enqueue_iteration(Ctx& c) {
     return FFTPL_OK;
 }
 
+fftpl_status fftpl::loop_records(Ctx& c, int cap, double base_k) {
+    if (c.recs_cap < std::max(cap, 1)) {
+        if (c.recs) {
+            cudaFree(c.recs);
+            c.dev_allocs.erase(std::find(c.dev_allocs.begin(), c.dev_allocs.end(), (void*)c.recs));
+            c.dev_bytes -= (size_t)c.recs_cap * kRecFields * sizeof(double);
+            c.recs = nullptr;
+        }
+        TRY(dalloc(c, &c.recs, (size_t)std::max(cap, 1) * kRecFields));
+        c.recs_cap = std::max(cap, 1);
+    }
+    double hdr[2] = {(double)cap, base_k};
+    CK(cudaMemcpy(c.ctrl + C_REC_CAP, hdr, sizeof(hdr), cudaMemcpyHostToDevice));
+    return FFTPL_OK;
+}
+
+}  // extern "C++"
+
 fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32_t* ran) {
     if (!h) return FFTPL_EINVAL;
     Ctx& c = *h;
     if (!c.placing) return set_err(c, FFTPL_ESTATE, "call fftpl_place_init first");
     if (iters < 0) return set_err(c, FFTPL_EINVAL, "iters must be >= 0");
-    if (c.recs_cap < std::max(iters, 1)) {
-        if (c.recs) {
-            cudaFree(c.recs);
-            c.dev_allocs.erase(std::find(c.dev_allocs.begin(), c.dev_allocs.end(), (void*)c.recs));
-            c.recs = nullptr;
-        }
-        TRY(dalloc(c, &c.recs, (size_t)std::max(iters, 1) * kRecFields));
-        c.recs_cap = std::max(iters, 1);
-    }
     double k0 = 0.0;
     CK(cudaMemcpyAsync(&k0, c.ctrl + C_K, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
-    double hdr[2] = {(double)iters, k0};
-    CK(cudaMemcpyAsync(c.ctrl + C_REC_CAP, hdr, sizeof(hdr), cudaMemcpyHostToDevice, c.stream));
-    CK(cudaStreamSynchronize(c.stream));
-    for (int it = 0; it < iters; ++it) TRY(enqueue_iteration(c));
+    TRY(loop_records(c, iters, k0));
+    for (int it = 0; it < iters; ++it) TRY(loop_enqueue(c));
     double k1 = 0.0;
     CK(cudaMemcpyAsync(&k1, c.ctrl + C_K, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));

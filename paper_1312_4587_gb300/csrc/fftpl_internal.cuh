@@ -262,6 +262,67 @@ __device__ __forceinline__ void block_acc1(float a, double* acc, int qa) {
     block_acc2(a, 0.0f, acc, qa, -1);
 }
 
+// Deterministic (order-free) reduction for the deterministic mode: each
+// block sums its threads in a fixed tree and stores its totals in its own
+// slot of part[]; the block that draws the last ticket (after a fence) adds
+// all slots in index order and stores the totals in stripe 0.  Nothing
+// waits.  part == nullptr selects the striped atomics of block_acc2.
+struct DetRed {
+    double* part;       // [2][cap] block totals
+    unsigned* ticket;   // zero between launches (the last block resets it)
+    int cap;            // capacity in blocks
+};
+
+__device__ __forceinline__ void reduce2(float a, float b, double* acc, int qa, int qb,
+                                        const DetRed& dr) {
+    if (!dr.part) {
+        block_acc2(a, b, acc, qa, qb);
+        return;
+    }
+    __shared__ double s_a[32], s_b[32];
+    __shared__ bool s_last;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    __syncthreads();
+    if (l == 0) { s_a[w] = (double)a; s_b[w] = (double)b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int k = 0; k < nw; ++k) { ta += s_a[k]; tb += s_b[k]; }
+        dr.part[blockIdx.x] = ta;
+        dr.part[dr.cap + blockIdx.x] = tb;
+        __threadfence();
+        unsigned t = atomicAdd(dr.ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+        if (s_last) *dr.ticket = 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double ta = 0.0, tb = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        ta += __ldcg(dr.part + k);
+        tb += __ldcg(dr.part + dr.cap + k);
+    }
+    __syncthreads();
+    // fixed-order tree over the block (warps, then warp totals in order)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ta += __shfl_down_sync(0xffffffffu, ta, o);
+        tb += __shfl_down_sync(0xffffffffu, tb, o);
+    }
+    if (l == 0) { s_a[w] = ta; s_b[w] = tb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double fa = 0.0, fb = 0.0;
+        for (int k = 0; k < nw; ++k) { fa += s_a[k]; fb += s_b[k]; }
+        if (qa >= 0) acc[qa] = fa;
+        if (qb >= 0) acc[qb] = fb;
+        __threadfence();
+    }
+}
+
 // a dfloat collapsed to the nearest float
 __device__ __forceinline__ float df_val(dfloat d) { return d.hi + d.lo; }
 
@@ -327,6 +388,10 @@ struct Ctx {
     float2* gW2 = nullptr;      // interleaved wirelength gradient accumulator (m_mov)
     float2* pxy = nullptr;      // pin coordinates in slab order (slab_slots)
     float2* pos2 = nullptr;     // interleaved cell centres (m_mov)
+    // deterministic reductions: region 0 for the main stream, 1 for WA
+    double* det_part = nullptr;
+    unsigned* det_ticket = nullptr;
+    int det_cap[2] = {0, 0};
     double* acc = nullptr;
     int* err = nullptr;
     double* acc_host = nullptr;   // pinned mirror
@@ -357,6 +422,19 @@ struct Ctx {
     std::vector<void*> dev_allocs;
     size_t dev_bytes = 0;
 };
+
+// Reduction descriptor of region r (0: main stream, 1: WA stream); atomics
+// unless the handle is deterministic.
+inline DetRed det_red(const Ctx& c, int r) {
+    if (!c.det_part) return DetRed{nullptr, nullptr, 0};
+    double* base = c.det_part + (r == 0 ? 0 : 2 * (size_t)c.det_cap[0]);
+    return DetRed{base, c.det_ticket + r, c.det_cap[r]};
+}
+
+// Enqueues one placement-loop iteration on the handle's streams (no sync).
+fftpl_status loop_enqueue(Ctx& c);
+// Makes room for cap iteration records and numbers them from base_k.
+fftpl_status loop_records(Ctx& c, int cap, double base_k);
 
 // Sets the text fftpl_last_error(NULL) returns on this thread.
 void set_global_error(const std::string& msg);

@@ -204,7 +204,8 @@ template <int LOGN, bool QUANT>
 __global__ void __launch_bounds__(kSpecThreads, 2)
 k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
            const float* __restrict__ M, float inv_ab, float cap, float* __restrict__ T1,
-           const float2* __restrict__ tw, const float2* __restrict__ ph, double* __restrict__ acc) {
+           const float2* __restrict__ tw, const float2* __restrict__ ph, double* __restrict__ acc,
+           DetRed dr) {
     constexpr int N = 1 << LOGN;
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = 2 * NB;
@@ -245,7 +246,7 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
             row[2 * pidx(mk_pos(x + t, N)) + (r & 1)] = (d4[t] + m4[t]) * inv_ab;
         }
     }
-    block_acc2(df_val(tau), df_val(charge), acc, ACC_TAU, ACC_CHARGE);
+    reduce2(df_val(tau), df_val(charge), acc, ACC_TAU, ACC_CHARGE, dr);
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, false);
     // split the packed spectra and apply the post-twiddle:
@@ -311,7 +312,7 @@ template <int LOGN>
 __global__ void __launch_bounds__(kSpecThreads, 2)
 k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__ RT,
        const float2* __restrict__ tw, const float2* __restrict__ ph, float pi_lx, float pi_ly,
-       double* __restrict__ acc) {
+       double* __restrict__ acc, DetRed dr) {
     constexpr int N = 1 << LOGN;
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = NB;
@@ -398,7 +399,7 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
             where[i] = f * HALF + v;
         }
     }
-    block_acc1(df_val(energy), acc, ACC_N);
+    reduce2(df_val(energy), 0.0f, acc, ACC_N, -1, dr);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < PI; ++i) {
@@ -517,16 +518,18 @@ static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {
         if (c.opt.deterministic) {
             auto kf = k_rows_fwd<LOGN, true>;
             kf<<<N / (2 * kSpecBuffers), kSpecThreads, smem, s>>>(nullptr, c.Dq, c.M, inv_ab, cap,
-                                                                   c.T1, c.tw, c.ph, c.acc);
+                                                                   c.T1, c.tw, c.ph, c.acc,
+                                                                   det_red(c, 0));
         } else {
             auto kf = k_rows_fwd<LOGN, false>;
             kf<<<N / (2 * kSpecBuffers), kSpecThreads, smem, s>>>(c.D, nullptr, c.M, inv_ab, cap,
-                                                                   c.T1, c.tw, c.ph, c.acc);
+                                                                   c.T1, c.tw, c.ph, c.acc,
+                                                                   det_red(c, 0));
         }
     } else if (which == 1) {
         auto kf = k_cols<LOGN>;
         kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.T1, c.PT, c.RT, c.tw, c.ph, pi_lx, pi_ly,
-                                                        c.acc);
+                                                        c.acc, det_red(c, 0));
     } else {
         auto kf = k_rows_inv<LOGN>;
         size_t smem_inv = smem + (size_t)kSpecBuffers * N * sizeof(float);

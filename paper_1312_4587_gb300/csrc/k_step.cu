@@ -13,6 +13,7 @@ struct LoopBufs {
     const float *w, *h;
     double *ctrl, *acc, *recs;
     unsigned int* counters;
+    DetRed dr;
 };
 
 // gather + pin sums at v (like k_cells) and, in the last CTA, lambda_k.
@@ -45,7 +46,7 @@ k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
         b.gW[i] = wx;
         b.gW[m + i] = wy;
     }
-    block_acc2(fabsf(nx) + fabsf(ny), fabsf(wx) + fabsf(wy), b.acc, ACC_GN_L1, ACC_GW_L1);
+    reduce2(fabsf(nx) + fabsf(ny), fabsf(wx) + fabsf(wy), b.acc, ACC_GN_L1, ACC_GW_L1, b.dr);
     if (last_cta(b.counters + 0) && threadIdx.x == 0) ctrl_lambda(b.ctrl, b.acc);
 }
 
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(kCellThreads) k_loop_g(int m2, LoopBufs b) {
             dv = c * c;
         }
     }
-    block_acc2(dg, dv, b.acc, ACC_DG2, ACC_DV2);
+    reduce2(dg, dv, b.acc, ACC_DG2, ACC_DV2, b.dr);
     block_max(gi, b.acc, ACC_GINF);
     if (last_cta(b.counters + 1) && threadIdx.x == 0) ctrl_alpha(b.ctrl, b.acc);
 }
@@ -129,6 +130,7 @@ LoopBufs loop_bufs(Ctx& c) {
     b.gN = c.gN; b.gW = c.gW; b.w = c.w; b.h = c.h;
     b.ctrl = c.ctrl; b.acc = c.acc; b.recs = c.recs;
     b.counters = reinterpret_cast<unsigned int*>(c.ctrl + C_COUNT);
+    b.dr = det_red(c, 0);
     return b;
 }
 

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kWaThreads, 4)
 k_wa(int nslabs, const int4* __restrict__ slabs, const int* __restrict__ pin_cell,
      const float2* __restrict__ pxy, float gamma, const double* __restrict__ gamma_dev,
      float2* __restrict__ gW, const int* __restrict__ pin_slot, float2* __restrict__ gpin,
-     double* __restrict__ acc, const double* __restrict__ done) {
+     double* __restrict__ acc, const double* __restrict__ done, DetRed dr) {
     if (done && *done != 0.0) return;
     const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -179,7 +179,7 @@ k_wa(int nslabs, const int4* __restrict__ slabs, const int* __restrict__ pin_cel
             default: wa_net<0, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
         }
     }
-    block_acc2(df_val(wsum), df_val(hsum), acc, ACC_W, ACC_HPWL);
+    reduce2(df_val(wsum), df_val(hsum), acc, ACC_W, ACC_HPWL, dr);
 }
 
 // Per-cell kernel: density gradient by the field gather (q.E of Eq. 7),
@@ -192,7 +192,7 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
         float* __restrict__ gNx, float* __restrict__ gNy,
         float* __restrict__ gWx, float* __restrict__ gWy, const int* __restrict__ cell_pin_ptr,
         const float2* __restrict__ gpin, const float2* __restrict__ gW2, double* __restrict__ acc,
-        const double* __restrict__ done) {
+        const double* __restrict__ done, DetRed dr) {
     if (done && *done != 0.0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float nx = 0.0f, ny = 0.0f, wx = 0.0f, wy = 0.0f;
@@ -218,7 +218,7 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
         gWx[i] = wx;
         gWy[i] = wy;
     }
-    block_acc2(fabsf(nx) + fabsf(ny), fabsf(wx) + fabsf(wy), acc, ACC_GN_L1, ACC_GW_L1);
+    reduce2(fabsf(nx) + fabsf(ny), fabsf(wx) + fabsf(wy), acc, ACC_GN_L1, ACC_GW_L1, dr);
 }
 
 // Deterministic pin-to-cell sum on its own (fftpl_wa in CSR mode).
@@ -272,10 +272,12 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
     int nb = nblk(c.nslabs, wpb);
     if (c.opt.deterministic)
         k_wa<true><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, c.pin_cell, c.pxy, gamma,
-                                             gamma_dev, nullptr, c.pin_slot, c.gpin, c.acc, done);
+                                             gamma_dev, nullptr, c.pin_slot, c.gpin, c.acc, done,
+                                             det_red(c, 1));
     else
         k_wa<false><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, c.pin_cell, c.pxy, gamma,
-                                              gamma_dev, c.gW2, nullptr, nullptr, c.acc, done);
+                                              gamma_dev, c.gW2, nullptr, nullptr, c.acc, done,
+                                              det_red(c, 1));
     c.launches++;
     return cudaGetLastError();
 }
@@ -304,11 +306,11 @@ cudaError_t launch_cells_impl(Ctx& c, const float* x, const float* y, float* gNx
     if (c.opt.deterministic)
         k_cells<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.E2, gNx,
                                                   gNy, gWx, gWy, c.cell_pin_ptr, c.gpin, nullptr,
-                                                  c.acc, done);
+                                                  c.acc, done, det_red(c, 0));
     else
         k_cells<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.E2,
                                                    gNx, gNy, gWx, gWy, nullptr, nullptr, c.gW2,
-                                                   c.acc, done);
+                                                   c.acc, done, det_red(c, 0));
     c.launches++;
     return cudaGetLastError();
 }

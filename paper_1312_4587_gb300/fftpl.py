@@ -81,6 +81,36 @@ class fftpl_iter_record(C.Structure):
         return d
 
 
+class fftpl_server_options(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int32),
+                ("iters_per_tick", C.c_int32), ("deterministic", C.c_int32),
+                ("dry_run", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class fftpl_job_info(C.Structure):
+    _fields_ = [("id", C.c_int64), ("state", C.c_int32), ("iters_done", C.c_int32),
+                ("m_mov", C.c_int32), ("n", C.c_int32), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("hpwl", C.c_double),
+                ("tau", C.c_double), ("device_bytes", C.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fftpl_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("active", C.c_int32), ("queued", C.c_int32), ("peak_active", C.c_int32),
+                ("peak_device_bytes", C.c_size_t), ("wall_s", C.c_double),
+                ("jobs_per_s", C.c_double), ("iter_p50_ms", C.c_double),
+                ("iter_p99_ms", C.c_double), ("job_p50_ms", C.c_double),
+                ("job_p99_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+FFTPL_JOB_QUEUED, FFTPL_JOB_ACTIVE, FFTPL_JOB_DONE, FFTPL_JOB_FAILED = range(4)
+
 _lib = None
 _P = C.c_void_p
 _H = C.c_void_p
@@ -123,6 +153,16 @@ def lib():
             "fftpl_launch_count": (C.c_int64, [_H]),
             "fftpl_debug_fail_alloc_after": (None, [C.c_int32]),
             "fftpl_solve_noalloc": (S, [_P, C.c_int32, C.c_double, C.c_double, _P, _P, _P, _P, _P]),
+            "fftpl_server_default_options": (None, [_P]),
+            "fftpl_estimate_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                                  C.c_int64, C.c_int32, C.c_int32]),
+            "fftpl_server_create": (S, [_P, _P]),
+            "fftpl_server_destroy": (None, [_P]),
+            "fftpl_server_submit": (S, [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int32, _P]),
+            "fftpl_server_tick": (S, [_P, _P, _P]),
+            "fftpl_server_job": (S, [_P, C.c_int64, _P, _P, _P]),
+            "fftpl_server_report": (S, [_P, _P]),
+            "fftpl_server_set_clock": (S, [_P, C.c_double]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -365,6 +405,81 @@ def fftpl_solve_noalloc(rho, n, Lx, Ly, psi, ex, ey, want_N=False, stream=None):
                                      C.byref(N) if want_N else None, C.c_void_p(int(stream or 0))),
            None)
     return float(N.value) if want_N else None
+
+
+def fftpl_server_default_options(**overrides):
+    o = fftpl_server_options()
+    lib().fftpl_server_default_options(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def fftpl_estimate_bytes(n, m_mov, m_fix, E, P, iters, deterministic=0):
+    return int(lib().fftpl_estimate_bytes(int(n), int(m_mov), int(m_fix), int(E), int(P),
+                                          int(iters), int(deterministic)))
+
+
+def fftpl_server_create(options=None):
+    out = C.c_void_p()
+    o = options if options is not None else fftpl_server_default_options()
+    _check(lib().fftpl_server_create(C.byref(o), C.byref(out)), None)
+    return out
+
+
+def fftpl_server_destroy(s):
+    if s:
+        lib().fftpl_server_destroy(s)
+
+
+def fftpl_server_submit(s, region, n, w, h, m_mov, fix_x, fix_y, net_ptr, pin_cell, pin_dx,
+                        pin_dy, x0, y0, iters, options=None):
+    """Queues a job (host numpy arrays, deep-copied); returns its id."""
+    w = np.ascontiguousarray(w, np.float32); h = np.ascontiguousarray(h, np.float32)
+    m_fix = int(w.shape[0] - m_mov)
+    fix_x = np.ascontiguousarray(fix_x if fix_x is not None else np.zeros(0), np.float32)
+    fix_y = np.ascontiguousarray(fix_y if fix_y is not None else np.zeros(0), np.float32)
+    net_ptr = np.ascontiguousarray(net_ptr, np.int32)
+    pin_cell = np.ascontiguousarray(pin_cell, np.int32)
+    pin_dx = np.ascontiguousarray(pin_dx, np.float32); pin_dy = np.ascontiguousarray(pin_dy, np.float32)
+    x0 = np.ascontiguousarray(x0, np.float32); y0 = np.ascontiguousarray(y0, np.float32)
+    R = fftpl_region(*[float(v) for v in region])
+    cells = fftpl_cells(int(m_mov), m_fix, _hptr(w, 0), _hptr(h, 0), _hptr(fix_x, 0), _hptr(fix_y, 0))
+    nets = fftpl_nets(int(net_ptr.shape[0] - 1), C.c_void_p(net_ptr.ctypes.data))
+    pins = fftpl_pins(int(pin_cell.shape[0]), _hptr(pin_cell, 0), _hptr(pin_dx, 0), _hptr(pin_dy, 0))
+    o = options if options is not None else fftpl_default_options()
+    jid = C.c_int64(0)
+    _check(lib().fftpl_server_submit(s, C.byref(R), C.c_int32(int(n)), C.byref(cells),
+                                     C.byref(nets), C.byref(pins), C.byref(o), _hptr(x0, 0),
+                                     _hptr(y0, 0), C.c_int32(int(iters)), C.byref(jid)), None)
+    return int(jid.value)
+
+
+def fftpl_server_tick(s):
+    a = C.c_int32(0); q = C.c_int32(0)
+    _check(lib().fftpl_server_tick(s, C.byref(a), C.byref(q)), None)
+    return int(a.value), int(q.value)
+
+
+def fftpl_server_job(s, jid, m_mov=None):
+    """(info dict, x, y); x and y are numpy arrays once the job is done."""
+    info = fftpl_job_info()
+    _check(lib().fftpl_server_job(s, C.c_int64(int(jid)), C.byref(info), None, None), None)
+    x = y = None
+    if info.state == FFTPL_JOB_DONE and m_mov:
+        x = np.empty(m_mov, np.float32); y = np.empty(m_mov, np.float32)
+        _check(lib().fftpl_server_job(s, C.c_int64(int(jid)), None, _hptr(x, 0), _hptr(y, 0)), None)
+    return info.as_dict(), x, y
+
+
+def fftpl_server_report(s):
+    st = fftpl_server_stats()
+    _check(lib().fftpl_server_report(s, C.byref(st)), None)
+    return st.as_dict()
+
+
+def fftpl_server_set_clock(s, now_s):
+    _check(lib().fftpl_server_set_clock(s, C.c_double(float(now_s))), None)
 
 
 def fftpl_debug_fail_alloc_after(k):
