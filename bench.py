@@ -202,6 +202,63 @@ def run_serving(args):
     return out
 
 
+def tc_flops(n):
+    """FLOPs of one tensor-core solve: five products of 7 n^3 multiply-adds
+    in total (G1, G2, G7: n^3 each; G35, G46: 2 n^3 each), three bf16
+    products per multiply-add (hi*hi + hi*lo + lo*hi)."""
+    return 2 * 3 * 7 * n ** 3
+
+
+def run_tc_path(args, inst, x, y, g, flush, stream):
+    """The same step on solve_path FFTPL_SOLVE_TC_BF16X3 (its own handle):
+    per-step time and the tensor-core stages against the bf16 peak."""
+    import torch
+    from paper_1312_4587_gb300 import fftpl as F
+    prob = F.Problem(inst, use_graphs=0 if args.no_graphs else 1,
+                     solve_path=F.FFTPL_SOLVE_TC_BF16X3)
+    h = prob.h
+    for _ in range(max(3, args.warmup)):
+        F.fftpl_eval(h, x, y, inst.gamma, *g, sync=False)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        F.fftpl_eval(h, x, y, inst.gamma, *g, sync=False)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    F.fftpl_set_profiling(h, True)
+    F.fftpl_stage_times(h, reset=True)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        F.fftpl_eval(h, x, y, inst.gamma, *g, sync=False)
+    torch.cuda.synchronize()
+    st, nl = F.fftpl_stage_times(h, reset=True)
+    F.fftpl_check(h)
+    prob.close()
+    solve_ms = sum(st[i] / max(nl[i], 1) for i in (1, 2, 3))
+    _, bf16, _ = load_peaks()
+    sustained = load_peak_sustained()
+    tflops = tc_flops(inst.n) / (solve_ms * 1e-3) / 1e12
+    return {"solve_path": "tc_bf16x3", "ms_per_step": round(ms, 5),
+            "value": round(1000.0 / ms, 2), "unit": UNIT,
+            "solve_ms": round(solve_ms, 5), "solve_flops": tc_flops(inst.n),
+            "roofline": {"bound": "tensor", "achieved": round(tflops, 1),
+                         "peak": sustained, "unit": "TFLOP/s",
+                         "frac": round(tflops / sustained, 4),
+                         "peak_kind": "measured bf16, sustained"}}
+
+
+def load_peak_sustained():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"])
+    except Exception:
+        return 1700.0
+
+
 def cpu_baseline_sample(inst):
     """The oracle as it stands, one evaluation of the same instance."""
     import oracle
@@ -318,6 +375,8 @@ def run_ours(args, ws, rank, local):
         line["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": st["GB/s"], "peak": hbm,
                             "unit": "GB/s", "frac": st["frac"], "traffic": None,
                             "peak_kind": peak_kind}
+    if not args.no_tc_path and n >= F.FFTPL_TC_MIN_N:
+        line["tc_path"] = run_tc_path(args, inst, x, y, g, flush, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(inst)
     if rank == 0 and ws == 1 and args.serving_jobs > 0:
@@ -337,6 +396,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tc-path", action="store_true",
+                    help="skip the tensor-core solve path comparison")
     ap.add_argument("--serving-jobs", type=int, default=200,
                     help="jobs in the serving stream (0: skip; the full stream is 2000)")
     ap.add_argument("--serving-pool", type=int, default=16)

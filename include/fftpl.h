@@ -109,13 +109,22 @@ typedef struct {
     const float* dy;
 } fftpl_pins;
 
-/* Spectral solve paths (Section III-E). */
+/* Spectral solve paths for Eqs. 9-12 (Section III-E names the transform;
+ * both paths compute the same bin-centre cosine/sine sums).
+ * FFTPL_SOLVE_TC_BF16X3 evaluates them as five dense products with the n x n
+ * cosine and sine matrices on the tcgen05 tensor cores: every float32
+ * operand x is split into bf16 x_hi + x_lo and each product sums
+ * hi*hi + hi*lo + lo*hi in float32 (relative error about 1e-5 per product,
+ * against 1e-7 for the FFT path).  It costs 42 n^3 flops per solve (the FFT
+ * path O(n^2 log n)), needs n >= FFTPL_TC_MIN_N, and holds 36 n^2 extra
+ * bytes of device memory (bf16 tables and intermediates). */
 enum {
     FFTPL_SOLVE_FFT = 0,      /* real-to-real transforms built on FP32 FFTs */
     FFTPL_SOLVE_TC_BF16X3 = 1 /* dense DCT matrices on tcgen05 tensor cores,
                                  operands split into bf16 hi+lo, 3 products,
                                  FP32 accumulation */
 };
+#define FFTPL_TC_MIN_N 128
 
 typedef struct {
     double target_density;  /* rho_t (Section III-B, Section V: 1.0) */
@@ -391,6 +400,22 @@ fftpl_status fftpl_solve_noalloc(const float* rho, int32_t n, double Lx, double 
 /* Host-side fault injection: the k-th device allocation from now fails with
  * FFTPL_ENOMEM (k <= 0 disables). */
 void fftpl_debug_fail_alloc_after(int32_t k);
+
+/* The tensor-core product behind FFTPL_SOLVE_TC_BF16X3, on its own:
+ * d[i][j] = sum_k A[i][k] B[j][k] (float32, row-major [M][N]) where
+ * A = a_hi + a_lo ([M][K] bf16 each) and B = b_hi + b_lo ([N][K] bf16 each),
+ * all row-major device arrays with 16-byte aligned bases.  nsplit 3 sums
+ * hi*hi + hi*lo + lo*hi, nsplit 1 hi*hi only (the lo arrays are then not
+ * read but must still be valid).  M and N positive multiples of 128, K of
+ * 64; otherwise FFTPL_EINVAL.  err: device int32 that receives bit 1 when a
+ * wait inside the kernel gives up (after about one second); no_loads != 0
+ * issues no operand loads, so that the kernel's first wait expires and it
+ * returns with err set and d unwritten (the timeout path, exercised without
+ * any fault).  Asynchronous on stream (a cudaStream_t; NULL: the legacy
+ * default stream); allocates no device memory. */
+fftpl_status fftpl_debug_tc_gemm(const void* a_hi, const void* a_lo, const void* b_hi,
+                                 const void* b_lo, int32_t M, int32_t N, int32_t K, float* d,
+                                 int32_t nsplit, int32_t no_loads, int32_t* err, void* stream);
 
 #ifdef __cplusplus
 }

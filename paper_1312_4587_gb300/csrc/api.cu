@@ -77,6 +77,7 @@ void free_ctx(fftpl_ctx* c) {
     if (c->stream || c->side) cudaDeviceSynchronize();
     if (c->eval_graph) cudaGraphExecDestroy(c->eval_graph);
     for (void* p : c->dev_allocs) cudaFree(p);
+    tc_free(*c);
     if (c->acc_host) cudaFreeHost(c->acc_host);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -142,8 +143,8 @@ fftpl_status validate(Ctx& c, const fftpl_region* R, int n, const fftpl_cells* c
             return set_err(c, FFTPL_EINVAL, "target_density must be > 0");
         if (opt->solve_path != FFTPL_SOLVE_FFT && opt->solve_path != FFTPL_SOLVE_TC_BF16X3)
             return set_err(c, FFTPL_EINVAL, "unknown solve_path");
-        if (opt->solve_path == FFTPL_SOLVE_TC_BF16X3)
-            return set_err(c, FFTPL_EUNSUPPORTED, "tensor-core solve path not built");
+        if (opt->solve_path == FFTPL_SOLVE_TC_BF16X3 && n < FFTPL_TC_MIN_N)
+            return set_err(c, FFTPL_EINVAL, "the tensor-core solve path needs n >= 128");
         if (!(opt->dw_ref > 0.0)) return set_err(c, FFTPL_EINVAL, "dw_ref must be > 0");
     }
     return FFTPL_OK;
@@ -183,6 +184,26 @@ struct Stage {
     ~Stage() { prof_end(c, slot, s); }
 };
 
+// Spectral solve of the current D (and M) into psi and E2, with the overflow,
+// charge and energy sums: stages 1-3 of the profile.
+fftpl_status enqueue_solve(Ctx& c, cudaStream_t s) {
+    if (c.tc) {
+        { Stage st(c, 1, s); CK(launch_tc(c, 0, s)); CK(launch_tc(c, 1, s)); }
+        { Stage st(c, 2, s); CK(launch_tc(c, 2, s)); }
+        { Stage st(c, 3, s); CK(launch_tc(c, 3, s)); }
+    } else {
+        { Stage st(c, 1, s); CK(launch_rows_fwd(c, s)); }
+        { Stage st(c, 2, s); CK(launch_cols_spectral(c, s)); }
+        { Stage st(c, 3, s); CK(launch_rows_inv(c, s)); }
+    }
+    return FFTPL_OK;
+}
+
+// The overflow and charge sums of the current D alone.
+cudaError_t launch_tau(Ctx& c, cudaStream_t s) {
+    return c.tc ? launch_tc(c, 0, s) : launch_rows_fwd(c, s);
+}
+
 // ---------------------------------------------------------------- evaluation
 enum { EV_DENSITY = 1, EV_WA = 2, EV_ADJOINT = 4, EV_NO_GATHER = 8 };
 
@@ -209,9 +230,7 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
             else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
             CK(launch_scatter(c, x, y, c.w, c.h, c.m_mov, c.D, c.Dq, s));
         }
-        { Stage st(c, 1, s); CK(launch_rows_fwd(c, s)); }
-        { Stage st(c, 2, s); CK(launch_cols_spectral(c, s)); }
-        { Stage st(c, 3, s); CK(launch_rows_inv(c, s)); }
+        TRY(enqueue_solve(c, s));
     }
     if (wa) CK(cudaStreamWaitEvent(s, c.ev_join, 0));
     if (!(what & EV_NO_GATHER)) {
@@ -283,6 +302,25 @@ void fftpl_default_options(fftpl_options* o) {
 }
 
 void fftpl_debug_fail_alloc_after(int32_t k) { g_fail_after.store(k > 0 ? k : 0); }
+
+fftpl_status fftpl_debug_tc_gemm(const void* a_hi, const void* a_lo, const void* b_hi,
+                                 const void* b_lo, int32_t M, int32_t N, int32_t K, float* d,
+                                 int32_t nsplit, int32_t no_loads, int32_t* err, void* stream) {
+    auto al16 = [](const void* p) { return p && ((uintptr_t)p & 15u) == 0; };
+    if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % 64 ||
+        (nsplit != 1 && nsplit != 3) || !al16(a_hi) || !al16(a_lo) || !al16(b_hi) ||
+        !al16(b_lo) || !al16(d) || !err) {
+        set_global_error("fftpl_debug_tc_gemm: bad sizes, split or pointers");
+        return FFTPL_EINVAL;
+    }
+    cudaError_t e = tc_debug_gemm(a_hi, a_lo, b_hi, b_lo, M, N, K, d, nsplit, no_loads, err,
+                                  (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_global_error(std::string("fftpl_debug_tc_gemm: ") + cudaGetErrorString(e));
+        return FFTPL_ECUDA;
+    }
+    return FFTPL_OK;
+}
 
 const char* fftpl_last_error(fftpl_t h) {
     if (!h) return g_create_error.c_str();
@@ -489,6 +527,9 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     if (c.opt.deterministic) {
         // capacity in blocks of every kernel that reduces on each stream
         long long cap0 = std::max<long long>((long long)n / 4, (2LL * c.m_mov + kCellThreads - 1) / kCellThreads);
+        if (c.opt.solve_path == FFTPL_SOLVE_TC_BF16X3)
+            cap0 = std::max<long long>(cap0, std::max<long long>((long long)n * n / 1024,
+                                                                 (long long)(n / 128) * (n / 128)));
         long long cap1 = ((long long)c.nslabs + kWaThreads / 32 - 1) / (kWaThreads / 32);
         c.det_cap[0] = (int)std::max<long long>(cap0, 1);
         c.det_cap[1] = (int)std::max<long long>(cap1, 1);
@@ -511,6 +552,14 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     }
     CK(cudaMemsetAsync(c.err, 0, sizeof(int), s));
     prepare_spectral(c.logn);
+    if (c.opt.solve_path == FFTPL_SOLVE_TC_BF16X3) {
+        uint16_t* block = nullptr;
+        TRY(dalloc(c, &block, tc_elems(n)));
+        cudaError_t e = tc_setup(c, block, s);
+        if (e == cudaErrorInvalidValue)
+            return set_err(c, FFTPL_ECUDA, "cuTensorMapEncodeTiled unavailable or failed");
+        CK(e);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     return FFTPL_OK;
@@ -789,7 +838,7 @@ fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
         if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
         else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
         CK(launch_scatter(c, c.v, c.v + c.m_mov, c.w, c.h, c.m_mov, c.D, c.Dq, s));
-        CK(launch_rows_fwd(c, s));
+        CK(launch_tau(c, s));
         CK(launch_gamma0(c, s));
     }
     CK(cudaStreamSynchronize(s));
@@ -819,9 +868,7 @@ fftpl_status fftpl::loop_enqueue(Ctx& c) {
         else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
         CK(launch_scatter(c, vx, vy, c.w, c.h, c.m_mov, c.D, c.Dq, s));
     }
-    { Stage st(c, 1, s); CK(launch_rows_fwd(c, s)); }
-    { Stage st(c, 2, s); CK(launch_cols_spectral(c, s)); }
-    { Stage st(c, 3, s); CK(launch_rows_inv(c, s)); }
+    TRY(enqueue_solve(c, s));
     CK(cudaStreamWaitEvent(s, c.ev_join, 0));
     { Stage st(c, 5, s); CK(launch_loop_cells(c, s)); }
     {

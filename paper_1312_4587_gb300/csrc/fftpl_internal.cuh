@@ -408,6 +408,9 @@ struct Ctx {
     // host-side staging for fftpl_eval_host
     float *hx = nullptr, *hy = nullptr, *hg = nullptr;  // device staging (2m, 4m)
 
+    // tensor-core solve path (solve_path FFTPL_SOLVE_TC_BF16X3), k_tc.cu
+    struct TcPlan* tc = nullptr;
+
     // captured CUDA graph of fftpl_eval for one set of buffers
     cudaGraphExec_t eval_graph = nullptr;
     const void* graph_key[7] = {};
@@ -458,6 +461,19 @@ cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, cudaS
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                            const double* gamma_dev, const double* done, cudaStream_t s);
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s);
+
+// tensor-core solve path (k_tc.cu): tc_setup lays the plan out in a device
+// block of tc_elems(n) bf16 elements owned by the handle and fills its
+// cosine/sine tables on stream s; launch_tc part 0 splits rho (with the
+// overflow and charge sums), 1 and 2 the forward contractions (2 with the
+// spectral divide and the energy), 3 the inverse ones (psi, E_x, E_y).
+size_t tc_elems(int n);
+cudaError_t tc_setup(Ctx& c, uint16_t* block, cudaStream_t s);
+void tc_free(Ctx& c);
+cudaError_t launch_tc(Ctx& c, int part, cudaStream_t s);
+cudaError_t tc_debug_gemm(const void* ah, const void* al, const void* bh, const void* bl, int M,
+                          int N, int K, float* d, int nsplit, int no_loads, int* err,
+                          cudaStream_t s);
 cudaError_t launch_cells(Ctx& c, const float* x, const float* y, float* gNx, float* gNy,
                          float* gWx, float* gWy, cudaStream_t s);
 // placement loop

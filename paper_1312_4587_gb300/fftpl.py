@@ -25,6 +25,7 @@ FFTPL_OK, FFTPL_EINVAL, FFTPL_ENOMEM, FFTPL_ECUDA, FFTPL_ETIMEOUT, FFTPL_ESTATE,
 STATUS_NAMES = {0: "FFTPL_OK", 1: "FFTPL_EINVAL", 2: "FFTPL_ENOMEM", 3: "FFTPL_ECUDA",
                 4: "FFTPL_ETIMEOUT", 5: "FFTPL_ESTATE", 6: "FFTPL_EUNSUPPORTED"}
 FFTPL_SOLVE_FFT, FFTPL_SOLVE_TC_BF16X3 = 0, 1
+FFTPL_TC_MIN_N = 128
 FFTPL_NUM_STAGES = 8
 STAGES = ["scatter", "rows_fwd", "cols", "rows_inv", "wa", "cells", "step", "reserved"]
 
@@ -152,6 +153,8 @@ def lib():
             "fftpl_stage_times": (S, [_H, _P, _P, C.c_int32]),
             "fftpl_launch_count": (C.c_int64, [_H]),
             "fftpl_debug_fail_alloc_after": (None, [C.c_int32]),
+            "fftpl_debug_tc_gemm": (S, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P,
+                                        C.c_int32, C.c_int32, _P, _P]),
             "fftpl_solve_noalloc": (S, [_P, C.c_int32, C.c_double, C.c_double, _P, _P, _P, _P, _P]),
             "fftpl_server_default_options": (None, [_P]),
             "fftpl_estimate_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -484,6 +487,20 @@ def fftpl_server_set_clock(s, now_s):
 
 def fftpl_debug_fail_alloc_after(k):
     lib().fftpl_debug_fail_alloc_after(C.c_int32(int(k)))
+
+
+def fftpl_debug_tc_gemm(a_hi, a_lo, b_hi, b_lo, d, err, nsplit=3, no_loads=0, stream=None):
+    """d[M][N] = (a_hi + a_lo) @ (b_hi + b_lo)^T on the tensor cores: bf16 CUDA
+    tensors a_* [M][K], b_* [N][K], float32 d [M][N], int32 err [1]."""
+    M, K = a_hi.shape
+    N = b_hi.shape[0]
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().fftpl_debug_tc_gemm(_dptr(a_hi), _dptr(a_lo), _dptr(b_hi), _dptr(b_lo),
+                                     C.c_int32(M), C.c_int32(N), C.c_int32(K), _dptr(d),
+                                     C.c_int32(nsplit), C.c_int32(no_loads), _dptr(err),
+                                     C.c_void_p(int(stream or 0))), None)
 
 
 # ---------------------------------------------------------------- convenience

@@ -103,3 +103,27 @@ def test_null_handle_calls_are_safe(F):
     assert F.fftpl_launch_count(None) == 0
     assert F.fftpl_device_bytes(None) == 0
     assert F.lib().fftpl_check(None) == F.FFTPL_EINVAL
+
+
+def test_tensor_core_path_validation(F):
+    """The tensor-core solve path needs n >= 128 (128-row tiles); unknown
+    paths are rejected; both before any device work."""
+    inst = _tiny()          # n = 64
+    o = F.fftpl_default_options(solve_path=F.FFTPL_SOLVE_TC_BF16X3)
+    with pytest.raises(F.FFTPLError) as ei:
+        _create(F, inst, options=o)
+    assert ei.value.status == F.FFTPL_EINVAL and "n >= 128" in str(ei.value)
+    o = F.fftpl_default_options(solve_path=7)
+    with pytest.raises(F.FFTPLError, match="unknown solve_path"):
+        _create(F, inst, options=o)
+
+
+@pytest.mark.parametrize("M,N,K,nsplit", [(100, 128, 64, 3), (128, 128, 96, 3),
+                                          (128, 0, 64, 3), (128, 128, 64, 2)])
+def test_debug_tc_gemm_validation(F, M, N, K, nsplit):
+    """Shapes off the 128 x 128 x 64 tiling, or a bad split, return EINVAL on
+    the host (the pointers are never dereferenced)."""
+    p = ctypes.c_void_p(1 << 20)
+    st = F.lib().fftpl_debug_tc_gemm(p, p, p, p, M, N, K, p, nsplit, 0, p, None)
+    assert st == F.FFTPL_EINVAL
+    assert "fftpl_debug_tc_gemm" in F.fftpl_last_error(None)
