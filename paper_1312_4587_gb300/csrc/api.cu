@@ -327,22 +327,83 @@ const char* fftpl_last_error(fftpl_t h) {
     return h->last_error.c_str();
 }
 
+// Internal numbering of the movable cells for the wirelength kernels: cells
+// in breadth-first order over the nets (nets of more than kRankMaxDegree
+// pins are not followed), so that the cells of a net, and of nets that share
+// cells, get nearby numbers.  The pin gathers and gradient atomics of the WA
+// kernels then touch a few cache lines per warp instead of one per pin.
+// The numbering is internal: positions and gradients keep the caller's order.
+constexpr int kRankMaxDegree = 64;
+
+static std::vector<int32_t> cell_ranks(int m, int E, const int32_t* np, const int32_t* pc) {
+    std::vector<int32_t> cnt((size_t)m + 1, 0);
+    for (int e = 0; e < E; ++e) {
+        int d = np[e + 1] - np[e];
+        if (d < 2 || d > kRankMaxDegree) continue;
+        for (int p = np[e]; p < np[e + 1]; ++p)
+            if (pc[p] < m) cnt[pc[p] + 1]++;
+    }
+    for (int i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
+    std::vector<int32_t> nets_of(cnt[m]), fill(cnt.begin(), cnt.end() - 1);
+    for (int e = 0; e < E; ++e) {
+        int d = np[e + 1] - np[e];
+        if (d < 2 || d > kRankMaxDegree) continue;
+        for (int p = np[e]; p < np[e + 1]; ++p)
+            if (pc[p] < m) nets_of[fill[pc[p]]++] = e;
+    }
+    std::vector<int32_t> rank((size_t)m, -1), queue;
+    std::vector<char> seen((size_t)E, 0);
+    queue.reserve(m);
+    int next = 0;
+    size_t head = 0;
+    for (int s0 = 0; s0 < m; ++s0) {
+        if (rank[s0] >= 0) continue;
+        rank[s0] = next++;
+        queue.push_back(s0);
+        while (head < queue.size()) {
+            int cc = queue[head++];
+            for (int q = cnt[cc]; q < cnt[cc + 1]; ++q) {
+                int e = nets_of[q];
+                if (seen[e]) continue;
+                seen[e] = 1;
+                for (int p = np[e]; p < np[e + 1]; ++p) {
+                    int c2 = pc[p];
+                    if (c2 < m && rank[c2] < 0) {
+                        rank[c2] = next++;
+                        queue.push_back(c2);
+                    }
+                }
+            }
+        }
+    }
+    return rank;
+}
+
 // Re-lays the netlist for the WA kernel: nets of degree >= 2 grouped by
-// degree, largest first (original order kept within a degree), into slabs of
-// up to 32 nets;
-// pin k of slab net j at slot base + 32 k + j.  Degree-1 nets have no
+// degree, largest first, into slabs of up to 32 nets, nets of one degree in
+// the order of their lowest cell number and the pins of a net by cell
+// number; pin k of slab net j at slot base + 32 k + j.  Degree-1 nets have no
 // wirelength and are left out.  In deterministic mode also builds the
 // cell-ordered pin slots (pins of each movable cell contiguous, in net order).
 static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins* pins,
                                 const float* fix_x, const float* fix_y) {
     const int32_t* np = nets->net_ptr;
+    const int32_t* pc = pins->pin_cell;
+    const int m = c.m_mov;
+    std::vector<int32_t> rank = cell_ranks(m, c.E, np, pc);
+    auto key_of = [&](int p) { return pc[p] < m ? rank[pc[p]] : m; };
     int maxd = 0;
     for (int e = 0; e < c.E; ++e) maxd = std::max(maxd, np[e + 1] - np[e]);
     std::vector<std::vector<int32_t>> by_deg((size_t)maxd + 1);
+    std::vector<int32_t> net_key((size_t)c.E, m);
     for (int e = 0; e < c.E; ++e) {
         int d = np[e + 1] - np[e];
-        if (d >= 2) by_deg[d].push_back(e);
+        if (d < 2) continue;
+        by_deg[d].push_back(e);
+        for (int p = np[e]; p < np[e + 1]; ++p) net_key[e] = std::min(net_key[e], key_of(p));
     }
+    for (auto& v : by_deg)
+        std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return net_key[a] < net_key[b]; });
     // heaviest slabs first: the long nets start early and overlap with the
     // many short ones instead of forming a tail
     std::vector<int4> slabs;
@@ -358,45 +419,53 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     if (slots > 0x7fffffffLL) return set_err(c, FFTPL_EINVAL, "too many pins");
     c.nslabs = (int)slabs.size();
     c.slab_slots = slots;
-    // cell-ordered slots for the deterministic reduction
+    // cell-ordered slots (by internal cell number) for the deterministic
+    // reduction
     std::vector<int32_t> cslot;
     if (c.opt.deterministic) {
-        std::vector<int32_t> cnt((size_t)c.m_mov + 1, 0);
+        std::vector<int32_t> cnt((size_t)m + 1, 0);
         for (int e = 0; e < c.E; ++e) {
             if (np[e + 1] - np[e] < 2) continue;
             for (int p = np[e]; p < np[e + 1]; ++p)
-                if (pins->pin_cell[p] < c.m_mov) cnt[pins->pin_cell[p] + 1]++;
+                if (pc[p] < m) cnt[rank[pc[p]] + 1]++;
         }
-        for (int i = 0; i < c.m_mov; ++i) cnt[i + 1] += cnt[i];
+        for (int i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
         std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
         cslot.assign((size_t)c.P, -1);
         for (int e = 0; e < c.E; ++e) {
             if (np[e + 1] - np[e] < 2) continue;
-            for (int p = np[e]; p < np[e + 1]; ++p) {
-                int cc = pins->pin_cell[p];
-                if (cc < c.m_mov) cslot[p] = fill[cc]++;
-            }
+            for (int p = np[e]; p < np[e + 1]; ++p)
+                if (pc[p] < m) cslot[p] = fill[rank[pc[p]]]++;
         }
         CK(cudaMemcpy(c.cell_pin_ptr, cnt.data(), cnt.size() * sizeof(int32_t),
                       cudaMemcpyHostToDevice));
+    }
+    if (m > 0) {
+        TRY(dalloc(c, &c.cell_rank, (size_t)m));
+        CK(cudaMemcpy(c.cell_rank, rank.data(), (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
     std::vector<int32_t> spc((size_t)std::max<int64_t>(slots, 1), -1), sslot;
     std::vector<float> sdx((size_t)std::max<int64_t>(slots, 1), 0.0f), sdy(sdx.size(), 0.0f);
     if (c.opt.deterministic) sslot.assign(spc.size(), -1);
     {
         size_t si = 0;
+        std::vector<int32_t> order;
         for (int d = maxd; d >= 2; --d) {
             const auto& v = by_deg[d];
             for (size_t s0 = 0; s0 < v.size(); s0 += 32, ++si) {
                 const int4& sl = slabs[si];
                 for (int j = 0; j < sl.z; ++j) {
                     int e = v[s0 + j];
+                    order.resize(d);
+                    for (int k = 0; k < d; ++k) order[k] = np[e] + k;
+                    std::stable_sort(order.begin(), order.end(),
+                                     [&](int a, int b) { return key_of(a) < key_of(b); });
                     for (int k = 0; k < d; ++k) {
-                        int p = np[e] + k;
+                        int p = order[k];
                         size_t slot = (size_t)sl.x + 32 * (size_t)k + j;
                         int cc = pins->pin_cell[p];
                         if (cc < c.m_mov) {
-                            spc[slot] = cc;
+                            spc[slot] = rank[cc];
                             sdx[slot] = pins->dx[p];
                             sdy[slot] = pins->dy[p];
                         } else {

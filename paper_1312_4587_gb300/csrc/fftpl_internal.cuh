@@ -385,9 +385,11 @@ struct Ctx {
     int32_t *pin_cell = nullptr, *pin_slot = nullptr, *cell_pin_ptr = nullptr;
     float *pin_dx = nullptr, *pin_dy = nullptr;
     float2* gpin = nullptr;
-    float2* gW2 = nullptr;      // interleaved wirelength gradient accumulator (m_mov)
+    float2* gW2 = nullptr;      // interleaved wirelength gradient accumulator (m_mov),
+                                // by internal number
     float2* pxy = nullptr;      // pin coordinates in slab order (slab_slots)
-    float2* pos2 = nullptr;     // interleaved cell centres (m_mov)
+    float2* pos2 = nullptr;     // interleaved cell centres (m_mov), by internal number
+    int32_t* cell_rank = nullptr;  // internal number of each movable cell (m_mov)
     // deterministic reductions: region 0 for the main stream, 1 for WA
     double* det_part = nullptr;
     unsigned* det_ticket = nullptr;

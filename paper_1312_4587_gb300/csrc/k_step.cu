@@ -20,7 +20,7 @@ struct LoopBufs {
 template <bool CSR>
 __global__ void __launch_bounds__(kCellThreads)
 k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
-             const int* __restrict__ cell_pin_ptr,
+             const int* __restrict__ rank, const int* __restrict__ cell_pin_ptr,
              const float2* __restrict__ gpin, const float2* __restrict__ gW2) {
     if (b.ctrl[C_DONE] != 0.0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -32,14 +32,15 @@ k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
         ny = -e.y;
         b.gN[i] = nx;
         b.gN[m + i] = ny;
+        const int r = rank[i];
         if (CSR) {
-            for (int q = cell_pin_ptr[i]; q < cell_pin_ptr[i + 1]; ++q) {
+            for (int q = cell_pin_ptr[r]; q < cell_pin_ptr[r + 1]; ++q) {
                 float2 p = gpin[q];
                 wx += p.x;
                 wy += p.y;
             }
         } else {
-            float2 v = gW2[i];
+            float2 v = gW2[r];
             wx = v.x;
             wy = v.y;
         }
@@ -138,11 +139,11 @@ cudaError_t launch_loop_cells(Ctx& c, cudaStream_t s) {
     LoopBufs b = loop_bufs(c);
     int nb = nblk(c.m_mov, kCellThreads);
     if (c.opt.deterministic)
-        k_loop_cells<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.E2,
+        k_loop_cells<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.E2, c.cell_rank,
                                                        c.cell_pin_ptr, c.gpin, nullptr);
     else
-        k_loop_cells<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.E2, nullptr,
-                                                        nullptr, c.gW2);
+        k_loop_cells<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.E2, c.cell_rank,
+                                                        nullptr, nullptr, c.gW2);
     c.launches++;
     return cudaGetLastError();
 }

@@ -50,14 +50,16 @@ k_pins(int64_t slots4, const int4* __restrict__ pin_cell, const float4* __restri
                                  __fadd_rn(p3.x, dx.w), __fadd_rn(p3.y, dy.w));
 }
 
-// (x, y) -> interleaved positions, so that one random 8-byte load (one
-// sector) fetches a pin's cell centre.
+// (x, y) -> interleaved positions at each cell's internal number, so that
+// one 8-byte load (one sector) fetches a pin's cell centre and the pins of a
+// slab read nearby sectors.
 __global__ void __launch_bounds__(256)
 k_interleave(int m, const float* __restrict__ x, const float* __restrict__ y,
-             float2* __restrict__ pos, const double* __restrict__ done) {
+             const int* __restrict__ rank, float2* __restrict__ pos,
+             const double* __restrict__ done) {
     if (done && *done != 0.0) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) pos[i] = make_float2(x[i], y[i]);
+    if (i < m) pos[rank[i]] = make_float2(x[i], y[i]);
 }
 
 // Per-net WA of one lane's net, D known at compile time (D > 0) or not
@@ -72,7 +74,7 @@ struct WaOut {
 
 template <int D, bool CSR>
 __device__ __forceinline__ void wa_net(const float2* __restrict__ pxy, int base, int d, float l2g,
-                                       float inv_g, const WaOut& o, dfloat& wsum, dfloat& hsum) {
+                                       float inv_g, const WaOut& o, float& wsum, float& hsum) {
     constexpr int R = D > 0 ? D : 1;
     float rx[R], ry[R], ex_p[R], ex_m[R], ey_p[R], ey_m[R];
     const int dd = D > 0 ? D : d;
@@ -116,19 +118,26 @@ __device__ __forceinline__ void wa_net(const float2* __restrict__ pxy, int base,
             sums(p.x, p.y, a, b, c2, e);
         }
     }
-    const float Wpx = Tpx / Spx, Wmx = Tmx / Smx, Wpy = Tpy / Spy, Wmy = Tmy / Smy;
-    const float isx = 1.0f / Spx, imx = 1.0f / Smx, isy = 1.0f / Spy, imy = 1.0f / Smy;
-    dfloat spanx = df_add({Mx, 0.0f}, -mx);
-    dfloat spany = df_add({My, 0.0f}, -my);
-    dfloat span = df_add(spanx, spany);
-    hsum = df_add(hsum, span);
-    wsum = df_add(df_add(wsum, span), (Wpx - Wmx) + (Wpy - Wmy));
+    // every S is in [1, d] (its largest term is exp(0) = 1): the fast
+    // reciprocal (2 ulp) is accurate over that whole range
+    const float isx = __fdividef(1.0f, Spx), imx = __fdividef(1.0f, Smx);
+    const float isy = __fdividef(1.0f, Spy), imy = __fdividef(1.0f, Smy);
+    const float Wpx = Tpx * isx, Wmx = Tmx * imx, Wpy = Tpy * isy, Wmy = Tmy * imy;
+    // one net per lane: its span and W~ in float32 (the FP64 sums start at
+    // the warp totals)
+    const float span = (Mx - mx) + (My - my);
+    hsum += span;
+    wsum += span + ((Wpx - Wmx) + (Wpy - Wmy));
+    // dW~/dp = a+ (P0 + t+ P1) - a- (Q0 - t- Q1) per axis, with
+    // P0 = (1 - W+/g)/S+, P1 = 1/(g S+), Q0 = (1 + W-/g)/S-, Q1 = 1/(g S-)
+    const float P0x = isx * fmaf(-Wpx, inv_g, 1.0f), P1x = isx * inv_g;
+    const float Q0x = imx * fmaf(Wmx, inv_g, 1.0f), Q1x = imx * inv_g;
+    const float P0y = isy * fmaf(-Wpy, inv_g, 1.0f), P1y = isy * inv_g;
+    const float Q0y = imy * fmaf(Wmy, inv_g, 1.0f), Q1y = imy * inv_g;
     auto emit = [&](int k, float px, float py, float apx, float amx, float apy, float amy) {
         float tpx = px - Mx, tmx = px - mx, tpy = py - My, tmy = py - my;
-        float gxj = apx * isx * (1.0f + (tpx - Wpx) * inv_g) -
-                    amx * imx * (1.0f - (tmx - Wmx) * inv_g);
-        float gyj = apy * isy * (1.0f + (tpy - Wpy) * inv_g) -
-                    amy * imy * (1.0f - (tmy - Wmy) * inv_g);
+        float gxj = apx * fmaf(tpx, P1x, P0x) - amx * fmaf(-tmx, Q1x, Q0x);
+        float gyj = apy * fmaf(tpy, P1y, P0y) - amy * fmaf(-tmy, Q1y, Q0y);
         if (CSR) {
             int sl = o.pin_slot[base + 32 * k];
             if (sl >= 0) o.gpin[sl] = make_float2(gxj, gyj);
@@ -167,7 +176,7 @@ k_wa(int nslabs, const int4* __restrict__ slabs, const int* __restrict__ pin_cel
     const int4 sl = warp < nslabs ? slabs[warp] : make_int4(0, 0, 0, 0);
     const int base = sl.x + lane, d = sl.y;
     const WaOut o{gW, pin_cell, pin_slot, gpin};
-    dfloat wsum = df_zero(), hsum = df_zero();
+    float wsum = 0.0f, hsum = 0.0f;
     if (lane < sl.z) {
         // d is the same for the whole warp, so this switch does not diverge
         switch (d) {
@@ -179,7 +188,7 @@ k_wa(int nslabs, const int4* __restrict__ slabs, const int* __restrict__ pin_cel
             default: wa_net<0, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
         }
     }
-    reduce2(df_val(wsum), df_val(hsum), acc, ACC_W, ACC_HPWL, dr);
+    reduce2(wsum, hsum, acc, ACC_W, ACC_HPWL, dr);
 }
 
 // Per-cell kernel: density gradient by the field gather (q.E of Eq. 7),
@@ -190,8 +199,9 @@ __global__ void __launch_bounds__(kCellThreads)
 k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
         const float* __restrict__ w, const float* __restrict__ h, const float2* __restrict__ E2,
         float* __restrict__ gNx, float* __restrict__ gNy,
-        float* __restrict__ gWx, float* __restrict__ gWy, const int* __restrict__ cell_pin_ptr,
-        const float2* __restrict__ gpin, const float2* __restrict__ gW2, double* __restrict__ acc,
+        float* __restrict__ gWx, float* __restrict__ gWy, const int* __restrict__ rank,
+        const int* __restrict__ cell_pin_ptr, const float2* __restrict__ gpin,
+        const float2* __restrict__ gW2, double* __restrict__ acc,
         const double* __restrict__ done, DetRed dr) {
     if (done && *done != 0.0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,15 +213,16 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
         ny = -e.y;
         gNx[i] = nx;
         gNy[i] = ny;
+        const int r = rank[i];
         if (CSR) {
-            int q0 = cell_pin_ptr[i], q1 = cell_pin_ptr[i + 1];
+            int q0 = cell_pin_ptr[r], q1 = cell_pin_ptr[r + 1];
             for (int q = q0; q < q1; ++q) {
                 float2 v = gpin[q];
                 wx += v.x;
                 wy += v.y;
             }
         } else {
-            float2 v = gW2[i];
+            float2 v = gW2[r];
             wx = v.x;
             wy = v.y;
         }
@@ -223,12 +234,14 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
 
 // Deterministic pin-to-cell sum on its own (fftpl_wa in CSR mode).
 __global__ void __launch_bounds__(kCellThreads)
-k_pin_sum(int m, const int* __restrict__ cell_pin_ptr, const float2* __restrict__ gpin,
-          float* __restrict__ gx, float* __restrict__ gy, double* __restrict__ acc) {
+k_pin_sum(int m, const int* __restrict__ rank, const int* __restrict__ cell_pin_ptr,
+          const float2* __restrict__ gpin, float* __restrict__ gx, float* __restrict__ gy,
+          double* __restrict__ acc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float wx = 0.0f, wy = 0.0f;
     if (i < m) {
-        for (int q = cell_pin_ptr[i]; q < cell_pin_ptr[i + 1]; ++q) {
+        const int r = rank[i];
+        for (int q = cell_pin_ptr[r]; q < cell_pin_ptr[r + 1]; ++q) {
             float2 v = gpin[q];
             wx += v.x;
             wy += v.y;
@@ -241,12 +254,12 @@ k_pin_sum(int m, const int* __restrict__ cell_pin_ptr, const float2* __restrict_
 
 // Splits the interleaved atomic accumulator into gx, gy and adds ||g||_1.
 __global__ void __launch_bounds__(kCellThreads)
-k_split(int m, const float2* __restrict__ gW2, float* __restrict__ gx, float* __restrict__ gy,
-        double* __restrict__ acc) {
+k_split(int m, const int* __restrict__ rank, const float2* __restrict__ gW2,
+        float* __restrict__ gx, float* __restrict__ gy, double* __restrict__ acc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float v = 0.0f;
     if (i < m) {
-        float2 g = gW2[i];
+        float2 g = gW2[rank[i]];
         gx[i] = g.x;
         gy[i] = g.y;
         v = fabsf(g.x) + fabsf(g.y);
@@ -260,7 +273,8 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                            const double* gamma_dev, const double* done, cudaStream_t s) {
     if (c.nslabs <= 0) return cudaSuccess;
     if (c.m_mov > 0) {
-        k_interleave<<<nblk(c.m_mov, 256), 256, 0, s>>>(c.m_mov, x, y, c.pos2, done);
+        k_interleave<<<nblk(c.m_mov, 256), 256, 0, s>>>(c.m_mov, x, y, c.cell_rank, c.pos2,
+                                                         done);
         c.launches++;
     }
     int64_t slots4 = c.slab_slots / 4;   // slab sizes are multiples of 64 slots
@@ -289,12 +303,11 @@ cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, cudaS
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s) {
     if (c.m_mov <= 0) return cudaSuccess;
     if (c.opt.deterministic)
-        k_pin_sum<<<nblk(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(c.m_mov, c.cell_pin_ptr,
-                                                                      c.gpin, gx, gy,
-                                                                      c.acc);
+        k_pin_sum<<<nblk(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
+            c.m_mov, c.cell_rank, c.cell_pin_ptr, c.gpin, gx, gy, c.acc);
     else
-        k_split<<<nblk(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(c.m_mov, c.gW2, gx, gy,
-                                                                    c.acc);
+        k_split<<<nblk(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(c.m_mov, c.cell_rank,
+                                                                    c.gW2, gx, gy, c.acc);
     c.launches++;
     return cudaGetLastError();
 }
@@ -305,11 +318,13 @@ cudaError_t launch_cells_impl(Ctx& c, const float* x, const float* y, float* gNx
     int nb = nblk(c.m_mov, kCellThreads);
     if (c.opt.deterministic)
         k_cells<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.E2, gNx,
-                                                  gNy, gWx, gWy, c.cell_pin_ptr, c.gpin, nullptr,
+                                                  gNy, gWx, gWy, c.cell_rank, c.cell_pin_ptr,
+                                                  c.gpin, nullptr,
                                                   c.acc, done, det_red(c, 0));
     else
         k_cells<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.E2,
-                                                   gNx, gNy, gWx, gWy, nullptr, nullptr, c.gW2,
+                                                   gNx, gNy, gWx, gWy, c.cell_rank, nullptr,
+                                                   nullptr, c.gW2,
                                                    c.acc, done, det_red(c, 0));
     c.launches++;
     return cudaGetLastError();
