@@ -18,37 +18,12 @@ namespace fftpl {
 
 // Nets are re-laid at create time into slabs of up to 32 nets of one degree
 // d (slab = {first pin slot, d, net count}); pin k of the slab's net j sits
-// at slot base + 32 k + j.  Two kernels:
-//   k_pins  one thread per slot: pin coordinate = fl32(cell centre + offset)
-//           into pxy[slot] (independent loads, so the random position
-//           gathers overlap fully);
-//   k_wa    one warp per slab, one lane per net: every lane walks the same d
-//           pins (no divergence) and each pin read of the warp is one
-//           contiguous 256-byte access.
+// at slot base + 32 k + j.  k_wa runs one warp per slab, one lane per net:
+// every lane walks the same d pins (no divergence), each pin-record read of
+// the warp is one contiguous access, and the cell-centre gathers of a slab
+// touch nearby lines (cells are numbered breadth-first over the nets).
 // Slabs of degree 2..6 (the bulk of the nets) run a body specialised for
 // their degree with the pins and exponentials held in registers.
-
-// A pin on a fixed cell carries cell -1 and its absolute coordinate
-// fl32(fixed centre + offset) in place of the offset; padding slots carry -1
-// and offset 0.  Four consecutive slots per thread (16-byte loads), all
-// record loads issued before the position gathers.
-__global__ void __launch_bounds__(256)
-k_pins(int64_t slots4, const int4* __restrict__ pin_cell, const float4* __restrict__ pdx,
-       const float4* __restrict__ pdy, const float2* __restrict__ pos, float4* __restrict__ pxy,
-       const double* __restrict__ done) {
-    if (done && *done != 0.0) return;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= slots4) return;
-    int4 c = pin_cell[i];
-    float4 dx = pdx[i], dy = pdy[i];
-    const float2 z = make_float2(0.0f, 0.0f);
-    float2 p0 = c.x >= 0 ? pos[c.x] : z, p1 = c.y >= 0 ? pos[c.y] : z;
-    float2 p2 = c.z >= 0 ? pos[c.z] : z, p3 = c.w >= 0 ? pos[c.w] : z;
-    pxy[2 * i] = make_float4(__fadd_rn(p0.x, dx.x), __fadd_rn(p0.y, dy.x),
-                             __fadd_rn(p1.x, dx.y), __fadd_rn(p1.y, dy.y));
-    pxy[2 * i + 1] = make_float4(__fadd_rn(p2.x, dx.z), __fadd_rn(p2.y, dy.z),
-                                 __fadd_rn(p3.x, dx.w), __fadd_rn(p3.y, dy.w));
-}
 
 // (x, y) -> interleaved positions at each cell's internal number, so that
 // one 8-byte load (one sector) fetches a pin's cell centre and the pins of a
@@ -63,26 +38,47 @@ k_interleave(int m, const float* __restrict__ x, const float* __restrict__ y,
 }
 
 // Per-net WA of one lane's net, D known at compile time (D > 0) or not
-// (D == 0: runtime degree d, pins re-read in each pass).  Adds W~ and the
-// HPWL term to wsum/hsum and sends each pin's gradient out.
-struct WaOut {
-    float2* gW;
+// (D == 0: runtime degree d).  Pin coordinate = fl32(cell centre + offset),
+// the centre gathered from pos by the pin's internal cell number (a pin on a
+// fixed cell carries -1 and its absolute coordinate as the offset).  For
+// D > 0 the pins live in registers; for D == 0 the first pass stores the pin
+// coordinates in the pin's own slot of pxy and the later passes re-read them.
+// Adds W~ and the HPWL term to wsum/hsum and sends each pin's gradient out.
+struct WaIo {
     const int* pin_cell;
+    const float* pin_dx;
+    const float* pin_dy;
+    const float2* pos;
+    float2* pxy;
+    float2* gW;
     const int* pin_slot;
     float2* gpin;
 };
 
+__device__ __forceinline__ float2 pin_xy(const WaIo& io, int c, float ox, float oy) {
+    const float2 p = c >= 0 ? io.pos[c] : make_float2(0.0f, 0.0f);
+    return make_float2(__fadd_rn(p.x, ox), __fadd_rn(p.y, oy));
+}
+
 template <int D, bool CSR>
-__device__ __forceinline__ void wa_net(const float2* __restrict__ pxy, int base, int d, float l2g,
-                                       float inv_g, const WaOut& o, float& wsum, float& hsum) {
+__device__ __forceinline__ void wa_net(const WaIo& io, int base, int d, float l2g, float inv_g,
+                                       float& wsum, float& hsum) {
     constexpr int R = D > 0 ? D : 1;
     float rx[R], ry[R], ex_p[R], ex_m[R], ey_p[R], ey_m[R];
     const int dd = D > 0 ? D : d;
     float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
     if (D > 0) {
+        int cr[R];
+        float ox[R], oy[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            float2 p = pxy[base + 32 * k];
+            cr[k] = io.pin_cell[base + 32 * k];
+            ox[k] = io.pin_dx[base + 32 * k];
+            oy[k] = io.pin_dy[base + 32 * k];
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            float2 p = pin_xy(io, cr[k], ox[k], oy[k]);
             rx[k] = p.x;
             ry[k] = p.y;
         }
@@ -94,7 +90,9 @@ __device__ __forceinline__ void wa_net(const float2* __restrict__ pxy, int base,
     } else {
 #pragma unroll 4
         for (int k = 0; k < dd; ++k) {
-            float2 p = pxy[base + 32 * k];
+            const int sl = base + 32 * k;
+            float2 p = pin_xy(io, io.pin_cell[sl], io.pin_dx[sl], io.pin_dy[sl]);
+            io.pxy[sl] = p;
             Mx = fmaxf(Mx, p.x); mx = fminf(mx, p.x);
             My = fmaxf(My, p.y); my = fminf(my, p.y);
         }
@@ -113,7 +111,7 @@ __device__ __forceinline__ void wa_net(const float2* __restrict__ pxy, int base,
     } else {
 #pragma unroll 4
         for (int k = 0; k < dd; ++k) {
-            float2 p = pxy[base + 32 * k];
+            float2 p = io.pxy[base + 32 * k];
             float a, b, c2, e;
             sums(p.x, p.y, a, b, c2, e);
         }
@@ -139,20 +137,24 @@ __device__ __forceinline__ void wa_net(const float2* __restrict__ pxy, int base,
         float gxj = apx * fmaf(tpx, P1x, P0x) - amx * fmaf(-tmx, Q1x, Q0x);
         float gyj = apy * fmaf(tpy, P1y, P0y) - amy * fmaf(-tmy, Q1y, Q0y);
         if (CSR) {
-            int sl = o.pin_slot[base + 32 * k];
-            if (sl >= 0) o.gpin[sl] = make_float2(gxj, gyj);
+            int sl = io.pin_slot[base + 32 * k];
+            if (sl >= 0) io.gpin[sl] = make_float2(gxj, gyj);
         } else {
-            int c = o.pin_cell[base + 32 * k];
-            if (c >= 0) atomicAdd(o.gW + c, make_float2(gxj, gyj));
+            // the cell number is re-read (an L1 hit) rather than held in
+            // registers through the exponentials
+            int c = io.pin_cell[base + 32 * k];
+            if (c >= 0) atomicAdd(io.gW + c, make_float2(gxj, gyj));
         }
     };
     if (D > 0) {
 #pragma unroll
-        for (int k = 0; k < R; ++k) emit(k, rx[k], ry[k], ex_p[k], ex_m[k], ey_p[k], ey_m[k]);
+        for (int k = 0; k < R; ++k)
+            emit(k, rx[k], ry[k], ex_p[k], ex_m[k], ey_p[k], ey_m[k]);
     } else {
 #pragma unroll 4
         for (int k = 0; k < dd; ++k) {
-            float2 p = pxy[base + 32 * k];
+            const int sl = base + 32 * k;
+            float2 p = io.pxy[sl];
             float tpx = p.x - Mx, tmx = p.x - mx, tpy = p.y - My, tmy = p.y - my;
             emit(k, p.x, p.y, exp2f(tpx * l2g), exp2f(-tmx * l2g), exp2f(tpy * l2g),
                  exp2f(-tmy * l2g));
@@ -162,10 +164,9 @@ __device__ __forceinline__ void wa_net(const float2* __restrict__ pxy, int base,
 
 template <bool CSR>
 __global__ void __launch_bounds__(kWaThreads, 4)
-k_wa(int nslabs, const int4* __restrict__ slabs, const int* __restrict__ pin_cell,
-     const float2* __restrict__ pxy, float gamma, const double* __restrict__ gamma_dev,
-     float2* __restrict__ gW, const int* __restrict__ pin_slot, float2* __restrict__ gpin,
-     double* __restrict__ acc, const double* __restrict__ done, DetRed dr) {
+k_wa(int nslabs, const int4* __restrict__ slabs, WaIo io, float gamma,
+     const double* __restrict__ gamma_dev, double* __restrict__ acc,
+     const double* __restrict__ done, DetRed dr) {
     if (done && *done != 0.0) return;
     const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -175,17 +176,16 @@ k_wa(int nslabs, const int4* __restrict__ slabs, const int* __restrict__ pin_cel
     const float l2g = (float)(1.4426950408889634 / (double)gamma);
     const int4 sl = warp < nslabs ? slabs[warp] : make_int4(0, 0, 0, 0);
     const int base = sl.x + lane, d = sl.y;
-    const WaOut o{gW, pin_cell, pin_slot, gpin};
     float wsum = 0.0f, hsum = 0.0f;
     if (lane < sl.z) {
         // d is the same for the whole warp, so this switch does not diverge
         switch (d) {
-            case 2: wa_net<2, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
-            case 3: wa_net<3, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
-            case 4: wa_net<4, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
-            case 5: wa_net<5, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
-            case 6: wa_net<6, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
-            default: wa_net<0, CSR>(pxy, base, d, l2g, inv_g, o, wsum, hsum); break;
+            case 2: wa_net<2, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
+            case 3: wa_net<3, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
+            case 4: wa_net<4, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
+            case 5: wa_net<5, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
+            case 6: wa_net<6, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
+            default: wa_net<0, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
         }
     }
     reduce2(wsum, hsum, acc, ACC_W, ACC_HPWL, dr);
@@ -277,21 +277,16 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                                                          done);
         c.launches++;
     }
-    int64_t slots4 = c.slab_slots / 4;   // slab sizes are multiples of 64 slots
-    k_pins<<<(int)((slots4 + 255) / 256), 256, 0, s>>>(
-        slots4, reinterpret_cast<const int4*>(c.pin_cell), reinterpret_cast<const float4*>(c.pin_dx),
-        reinterpret_cast<const float4*>(c.pin_dy), c.pos2, reinterpret_cast<float4*>(c.pxy), done);
-    c.launches++;
+    const WaIo io{c.pin_cell, c.pin_dx, c.pin_dy, c.pos2, c.pxy,
+                  c.opt.deterministic ? nullptr : c.gW2, c.pin_slot, c.gpin};
     const int wpb = kWaThreads / 32;
     int nb = nblk(c.nslabs, wpb);
     if (c.opt.deterministic)
-        k_wa<true><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, c.pin_cell, c.pxy, gamma,
-                                             gamma_dev, nullptr, c.pin_slot, c.gpin, c.acc, done,
+        k_wa<true><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, io, gamma, gamma_dev, c.acc, done,
                                              det_red(c, 1));
     else
-        k_wa<false><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, c.pin_cell, c.pxy, gamma,
-                                              gamma_dev, c.gW2, nullptr, nullptr, c.acc, done,
-                                              det_red(c, 1));
+        k_wa<false><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, io, gamma, gamma_dev, c.acc,
+                                              done, det_red(c, 1));
     c.launches++;
     return cudaGetLastError();
 }
