@@ -49,6 +49,38 @@ def stage_bytes(m, n, P, E):
 
 STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "cells": 5}
 
+# DRAM traffic per stage launch on the 2.2M-cell instance, dram__bytes_read.sum
+# + dram__bytes_write.sum of the stage's kernels from one ncu --set full
+# capture (profiles/eval_precision_kernels.md), valid only while the kernel
+# source it was taken from is unchanged: key = first 16 hex digits of the
+# SHA-256 of the kernel file followed by fftpl_internal.cuh.
+STAGE_TRAFFIC = {
+    "scatter": ("k_density.cu", "13027c5984583aff", 41772032 + 256),
+    "rows_fwd": ("k_spectral.cu", "3ecd272d697f20ea", 33655808 + 1280),
+    "cols": ("k_spectral.cu", "3ecd272d697f20ea", 17454592 + 588288),
+    "rows_inv": ("k_spectral.cu", "3ecd272d697f20ea", 33650432 + 2417408),
+    "wa": ("k_wire.cu", "8b57baf50d9e5db5", 28479232 + 2088960 + 138113280 + 22430208),
+    "cells": ("k_wire.cu", "8b57baf50d9e5db5", 75812608 + 15020544),
+}
+
+
+def source_key(fname):
+    import hashlib
+    h = hashlib.sha256()
+    for p in (fname, "fftpl_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1312_4587_gb300", "csrc", p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def stage_traffic(stage, workload):
+    """ncu DRAM bytes per launch of a stage, or None if the kernel changed
+    since the capture or the workload is another one."""
+    if workload != "precision" or stage not in STAGE_TRAFFIC:
+        return None
+    fname, key, nbytes = STAGE_TRAFFIC[stage]
+    return nbytes if source_key(fname) == key else None
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -366,8 +398,9 @@ def run_ours(args, ws, rank, local):
     if dom:
         st = stages[dom]
         line["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": st["GB/s"], "peak": hbm,
-                            "unit": "GB/s", "frac": st["frac"], "traffic": None,
-                            "peak_kind": peak_kind}
+                            "unit": "GB/s", "frac": st["frac"],
+                            "traffic": stage_traffic(dom, args.workload),
+                            "algorithmic_bytes": st["bytes"], "peak_kind": peak_kind}
     if not args.no_tc_path and n >= F.FFTPL_TC_MIN_N:
         line["tc_path"] = run_tc_path(args, inst, x, y, g, flush, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

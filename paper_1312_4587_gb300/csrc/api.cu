@@ -64,6 +64,22 @@ fftpl_status dalloc(Ctx& c, T** p, size_t count) {
     return FFTPL_OK;
 }
 
+// Device temporaries of one create call, freed when it returns.
+struct TempDev {
+    std::vector<void*> ptrs;
+    ~TempDev() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    cudaError_t alloc(T** p, size_t count) {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back((void*)*p);
+        else cudaGetLastError();
+        return e;
+    }
+};
+
 #define TRY(x)                              \
     do {                                    \
         fftpl_status s_ = (x);              \
@@ -327,177 +343,152 @@ const char* fftpl_last_error(fftpl_t h) {
     return h->last_error.c_str();
 }
 
-// Internal numbering of the movable cells for the wirelength kernels: cells
-// in breadth-first order over the nets (nets of more than kRankMaxDegree
-// pins are not followed), so that the cells of a net, and of nets that share
-// cells, get nearby numbers.  The pin gathers and gradient atomics of the WA
-// kernels then touch a few cache lines per warp instead of one per pin.
-// The numbering is internal: positions and gradients keep the caller's order.
-constexpr int kRankMaxDegree = 64;
-
-static std::vector<int32_t> cell_ranks(int m, int E, const int32_t* np, const int32_t* pc) {
-    std::vector<int32_t> cnt((size_t)m + 1, 0);
-    for (int e = 0; e < E; ++e) {
-        int d = np[e + 1] - np[e];
-        if (d < 2 || d > kRankMaxDegree) continue;
-        for (int p = np[e]; p < np[e + 1]; ++p)
-            if (pc[p] < m) cnt[pc[p] + 1]++;
-    }
-    for (int i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
-    std::vector<int32_t> nets_of(cnt[m]), fill(cnt.begin(), cnt.end() - 1);
-    for (int e = 0; e < E; ++e) {
-        int d = np[e + 1] - np[e];
-        if (d < 2 || d > kRankMaxDegree) continue;
-        for (int p = np[e]; p < np[e + 1]; ++p)
-            if (pc[p] < m) nets_of[fill[pc[p]]++] = e;
-    }
-    std::vector<int32_t> rank((size_t)m, -1), queue;
-    std::vector<char> seen((size_t)E, 0);
-    queue.reserve(m);
-    int next = 0;
-    size_t head = 0;
-    for (int s0 = 0; s0 < m; ++s0) {
-        if (rank[s0] >= 0) continue;
-        rank[s0] = next++;
-        queue.push_back(s0);
-        while (head < queue.size()) {
-            int cc = queue[head++];
-            for (int q = cnt[cc]; q < cnt[cc + 1]; ++q) {
-                int e = nets_of[q];
-                if (seen[e]) continue;
-                seen[e] = 1;
-                for (int p = np[e]; p < np[e + 1]; ++p) {
-                    int c2 = pc[p];
-                    if (c2 < m && rank[c2] < 0) {
-                        rank[c2] = next++;
-                        queue.push_back(c2);
-                    }
-                }
-            }
-        }
-    }
-    return rank;
-}
-
-// Re-lays the netlist for the WA kernel: nets of degree >= 2 grouped by
-// degree, largest first, into slabs of up to 32 nets, nets of one degree in
-// the order of their lowest cell number and the pins of a net by cell
-// number; pin k of slab net j at slot base + 32 k + j.  Degree-1 nets have no
-// wirelength and are left out.  In deterministic mode also builds the
-// cell-ordered pin slots (pins of each movable cell contiguous, in net order).
-static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins* pins,
-                                const float* fix_x, const float* fix_y) {
+// Re-lays the netlist for the WA kernel.
+//  1. Internal cell numbers (label rounds on the device, k_setup.cu; then
+//     cells ordered by (label, distance, index) with two counting sorts).
+//  2. Nets of degree >= 2 ordered by their lowest cell number (counting
+//     sort), grouped by degree, largest first, into slabs of up to 32 nets;
+//     pin k of slab net j at slot base + 32 k + j.  Degree-1 nets have no
+//     wirelength and are left out.
+//  3. The pin records written in slab layout on the device.
+// In deterministic mode also the cell-ordered pin slots (pins of each cell,
+// by internal number, contiguous and in net order).
+static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins* pins) {
     const int32_t* np = nets->net_ptr;
     const int32_t* pc = pins->pin_cell;
-    const int m = c.m_mov;
-    std::vector<int32_t> rank = cell_ranks(m, c.E, np, pc);
-    auto key_of = [&](int p) { return pc[p] < m ? rank[pc[p]] : m; };
-    int maxd = 0;
-    for (int e = 0; e < c.E; ++e) maxd = std::max(maxd, np[e + 1] - np[e]);
-    std::vector<std::vector<int32_t>> by_deg((size_t)maxd + 1);
-    std::vector<int32_t> net_key((size_t)c.E, m);
-    for (int e = 0; e < c.E; ++e) {
-        int d = np[e + 1] - np[e];
-        if (d < 2) continue;
-        by_deg[d].push_back(e);
-        for (int p = np[e]; p < np[e + 1]; ++p) net_key[e] = std::min(net_key[e], key_of(p));
+    const int m = c.m_mov, E = c.E;
+    const int64_t P = c.P;
+    cudaStream_t s = c.stream;
+    TempDev tmp;
+    int *d_np = nullptr, *d_pc = nullptr, *d_key = nullptr, *d_slot = nullptr;
+    float *d_dx = nullptr, *d_dy = nullptr;
+    CK(tmp.alloc(&d_np, (size_t)E + 1));
+    CK(tmp.alloc(&d_pc, (size_t)P));
+    CK(tmp.alloc(&d_dx, (size_t)P));
+    CK(tmp.alloc(&d_dy, (size_t)P));
+    CK(tmp.alloc(&d_key, (size_t)E));
+    CK(tmp.alloc(&d_slot, (size_t)E));
+    CK(cudaMemcpyAsync(d_np, np, ((size_t)E + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (P > 0) {
+        CK(cudaMemcpyAsync(d_pc, pc, (size_t)P * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_dx, pins->dx, (size_t)P * sizeof(float), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_dy, pins->dy, (size_t)P * sizeof(float), cudaMemcpyHostToDevice, s));
     }
-    for (auto& v : by_deg)
-        std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return net_key[a] < net_key[b]; });
+    // 1. internal cell numbers
+    std::vector<int32_t> rank((size_t)m);
+    if (m > 0) {
+        int *lab = nullptr, *next = nullptr, *dist = nullptr, *netlab = nullptr;
+        CK(tmp.alloc(&lab, (size_t)m));
+        CK(tmp.alloc(&next, (size_t)m));
+        CK(tmp.alloc(&dist, (size_t)m));
+        CK(tmp.alloc(&netlab, (size_t)E));
+        CK(launch_label_rounds(m, E, d_np, d_pc, lab, next, dist, netlab, s));
+        std::vector<int32_t> hl((size_t)m), hd((size_t)m);
+        CK(cudaMemcpyAsync(hl.data(), lab, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hd.data(), dist, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        // stable counting sorts: by distance, then by label (unreached cells,
+        // label and distance "infinite", last in index order)
+        const int nd = kLabelRounds + 2;
+        std::vector<int32_t> cnt((size_t)std::max(nd, m + 1) + 1, 0), o1((size_t)m), o2((size_t)m);
+        auto dkey = [&](int i) { return hd[i] > kLabelRounds ? kLabelRounds + 1 : hd[i]; };
+        auto lkey = [&](int i) { return hl[i] >= m ? m : hl[i]; };
+        for (int i = 0; i < m; ++i) cnt[dkey(i) + 1]++;
+        for (int k = 0; k < nd; ++k) cnt[k + 1] += cnt[k];
+        for (int i = 0; i < m; ++i) o1[cnt[dkey(i)]++] = i;
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int i = 0; i < m; ++i) cnt[lkey(i) + 1]++;
+        for (int k = 0; k <= m; ++k) cnt[k + 1] += cnt[k];
+        for (int q = 0; q < m; ++q) o2[cnt[lkey(o1[q])]++] = o1[q];
+        for (int q = 0; q < m; ++q) rank[o2[q]] = q;
+        TRY(dalloc(c, &c.cell_rank, (size_t)m));
+        CK(cudaMemcpyAsync(c.cell_rank, rank.data(), (size_t)m * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+    }
+    // 2. nets by lowest cell number, then slabs by degree
+    std::vector<int32_t> key((size_t)E);
+    CK(launch_net_key(m, E, d_np, d_pc, c.cell_rank, d_key, s));
+    if (E > 0)
+        CK(cudaMemcpyAsync(key.data(), d_key, (size_t)E * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int maxd = 0;
+    for (int e = 0; e < E; ++e) maxd = std::max(maxd, np[e + 1] - np[e]);
+    std::vector<int32_t> kcnt((size_t)m + 2, 0);
+    for (int e = 0; e < E; ++e)
+        if (np[e + 1] - np[e] >= 2) kcnt[key[e] + 1]++;
+    for (int k = 0; k <= m; ++k) kcnt[k + 1] += kcnt[k];
+    std::vector<int32_t> by_key((size_t)kcnt[m + 1]);
+    for (int e = 0; e < E; ++e)
+        if (np[e + 1] - np[e] >= 2) by_key[kcnt[key[e]]++] = e;
+    std::vector<int32_t> dcnt((size_t)maxd + 2, 0);
+    for (int e : by_key) dcnt[np[e + 1] - np[e]]++;
     // heaviest slabs first: the long nets start early and overlap with the
     // many short ones instead of forming a tail
     std::vector<int4> slabs;
+    std::vector<int64_t> first_slab((size_t)maxd + 1, 0);
     int64_t slots = 0;
     for (int d = maxd; d >= 2; --d) {
-        const auto& v = by_deg[d];
-        for (size_t s0 = 0; s0 < v.size(); s0 += 32) {
-            int cnt = (int)std::min<size_t>(32, v.size() - s0);
-            slabs.push_back(make_int4((int)slots, d, cnt, 0));
+        first_slab[d] = (int64_t)slabs.size();
+        for (int s0 = 0; s0 < dcnt[d]; s0 += 32) {
+            slabs.push_back(make_int4((int)slots, d, std::min(32, dcnt[d] - s0), 0));
             slots += 32LL * d;
         }
     }
     if (slots > 0x7fffffffLL) return set_err(c, FFTPL_EINVAL, "too many pins");
     c.nslabs = (int)slabs.size();
     c.slab_slots = slots;
+    std::vector<int32_t> net_slot((size_t)E, -1), seen((size_t)maxd + 1, 0);
+    for (int e : by_key) {
+        int d = np[e + 1] - np[e], j = seen[d]++;
+        net_slot[e] = slabs[(size_t)(first_slab[d] + j / 32)].x + (j % 32);
+    }
     // cell-ordered slots (by internal cell number) for the deterministic
     // reduction
     std::vector<int32_t> cslot;
+    int* d_cslot = nullptr;
     if (c.opt.deterministic) {
         std::vector<int32_t> cnt((size_t)m + 1, 0);
-        for (int e = 0; e < c.E; ++e) {
+        for (int e = 0; e < E; ++e) {
             if (np[e + 1] - np[e] < 2) continue;
             for (int p = np[e]; p < np[e + 1]; ++p)
                 if (pc[p] < m) cnt[rank[pc[p]] + 1]++;
         }
         for (int i = 0; i < m; ++i) cnt[i + 1] += cnt[i];
         std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
-        cslot.assign((size_t)c.P, -1);
-        for (int e = 0; e < c.E; ++e) {
+        cslot.assign((size_t)P, -1);
+        for (int e = 0; e < E; ++e) {
             if (np[e + 1] - np[e] < 2) continue;
             for (int p = np[e]; p < np[e + 1]; ++p)
                 if (pc[p] < m) cslot[p] = fill[rank[pc[p]]]++;
         }
-        CK(cudaMemcpy(c.cell_pin_ptr, cnt.data(), cnt.size() * sizeof(int32_t),
-                      cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(c.cell_pin_ptr, cnt.data(), cnt.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+        CK(tmp.alloc(&d_cslot, (size_t)P));
+        if (P > 0)
+            CK(cudaMemcpyAsync(d_cslot, cslot.data(), (size_t)P * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s));
     }
-    if (m > 0) {
-        TRY(dalloc(c, &c.cell_rank, (size_t)m));
-        CK(cudaMemcpy(c.cell_rank, rank.data(), (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice));
-    }
-    std::vector<int32_t> spc((size_t)std::max<int64_t>(slots, 1), -1), sslot;
-    std::vector<float> sdx((size_t)std::max<int64_t>(slots, 1), 0.0f), sdy(sdx.size(), 0.0f);
-    if (c.opt.deterministic) sslot.assign(spc.size(), -1);
-    {
-        size_t si = 0;
-        std::vector<int32_t> order;
-        for (int d = maxd; d >= 2; --d) {
-            const auto& v = by_deg[d];
-            for (size_t s0 = 0; s0 < v.size(); s0 += 32, ++si) {
-                const int4& sl = slabs[si];
-                for (int j = 0; j < sl.z; ++j) {
-                    int e = v[s0 + j];
-                    order.resize(d);
-                    for (int k = 0; k < d; ++k) order[k] = np[e] + k;
-                    std::stable_sort(order.begin(), order.end(),
-                                     [&](int a, int b) { return key_of(a) < key_of(b); });
-                    for (int k = 0; k < d; ++k) {
-                        int p = order[k];
-                        size_t slot = (size_t)sl.x + 32 * (size_t)k + j;
-                        int cc = pins->pin_cell[p];
-                        if (cc < c.m_mov) {
-                            spc[slot] = rank[cc];
-                            sdx[slot] = pins->dx[p];
-                            sdy[slot] = pins->dy[p];
-                        } else {
-                            // pin on a fixed cell: its coordinate never
-                            // changes; store fl32(centre + offset) itself
-                            volatile float ax = fix_x[cc - c.m_mov] + pins->dx[p];
-                            volatile float ay = fix_y[cc - c.m_mov] + pins->dy[p];
-                            spc[slot] = -1;
-                            sdx[slot] = ax;
-                            sdy[slot] = ay;
-                        }
-                        if (c.opt.deterministic) sslot[slot] = cslot[p];
-                    }
-                }
-            }
-        }
-    }
+    // 3. pin records in slab layout (padding slots: cell -1, offsets 0)
+    const size_t ns = (size_t)std::max<int64_t>(slots, 1);
     TRY(dalloc(c, &c.slabs, std::max<size_t>(slabs.size(), 1)));
-    TRY(dalloc(c, &c.pin_cell, spc.size()));
-    TRY(dalloc(c, &c.pin_dx, sdx.size()));
-    TRY(dalloc(c, &c.pin_dy, sdy.size()));
-    TRY(dalloc(c, &c.pxy, sdy.size()));
+    TRY(dalloc(c, &c.pin_cell, ns));
+    TRY(dalloc(c, &c.pin_dx, ns));
+    TRY(dalloc(c, &c.pin_dy, ns));
+    TRY(dalloc(c, &c.pxy, ns));
+    if (c.opt.deterministic) TRY(dalloc(c, &c.pin_slot, ns));
     if (!slabs.empty())
-        CK(cudaMemcpy(c.slabs, slabs.data(), slabs.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c.pin_cell, spc.data(), spc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c.pin_dx, sdx.data(), sdx.size() * sizeof(float), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c.pin_dy, sdy.data(), sdy.size() * sizeof(float), cudaMemcpyHostToDevice));
-    if (c.opt.deterministic) {
-        TRY(dalloc(c, &c.pin_slot, sslot.size()));
-        CK(cudaMemcpy(c.pin_slot, sslot.data(), sslot.size() * sizeof(int32_t),
-                      cudaMemcpyHostToDevice));
-    }
+        CK(cudaMemcpyAsync(c.slabs, slabs.data(), slabs.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c.pin_cell, 0xff, ns * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(c.pin_dx, 0, ns * sizeof(float), s));
+    CK(cudaMemsetAsync(c.pin_dy, 0, ns * sizeof(float), s));
+    if (c.pin_slot) CK(cudaMemsetAsync(c.pin_slot, 0xff, ns * sizeof(int32_t), s));
+    if (E > 0)
+        CK(cudaMemcpyAsync(d_slot, net_slot.data(), (size_t)E * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+    CK(launch_fill_slabs(m, E, d_np, d_pc, d_dx, d_dy, c.cell_rank, c.fix_x, c.fix_y, d_slot,
+                         d_cslot, c.pin_cell, c.pin_dx, c.pin_dy, c.pin_slot, s));
+    CK(cudaStreamSynchronize(s));
     return FFTPL_OK;
 }
 
@@ -592,7 +583,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     }
     CK(cudaMemcpyAsync(c.tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.ph, ph.data(), (n + 1) * sizeof(float2), cudaMemcpyHostToDevice, s));
-    TRY(build_slabs(c, nets, pins, cells->fix_x, cells->fix_y));
+    TRY(build_slabs(c, nets, pins));
     if (c.opt.deterministic) {
         // capacity in blocks of every kernel that reduces on each stream
         long long cap0 = std::max<long long>((long long)n / 4, (2LL * c.m_mov + kCellThreads - 1) / kCellThreads);

@@ -464,6 +464,22 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                            const double* gamma_dev, const double* done, cudaStream_t s);
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s);
 
+// create-time netlist layout (k_setup.cu): label rounds for the internal
+// cell numbers (seeds every kSeedStride cells, kLabelRounds rounds, nets of
+// more than kRankMaxDegree pins not followed), each net's lowest cell
+// number, and the pin records in slab layout
+constexpr int kSeedStride = 64;
+constexpr int kLabelRounds = 6;
+constexpr int kRankMaxDegree = 64;
+cudaError_t launch_label_rounds(int m, int E, const int* np, const int* pc, int* lab, int* next,
+                                int* dist, int* netlab, cudaStream_t s);
+cudaError_t launch_net_key(int m, int E, const int* np, const int* pc, const int* rank, int* key,
+                           cudaStream_t s);
+cudaError_t launch_fill_slabs(int m, int E, const int* np, const int* pc, const float* dx,
+                              const float* dy, const int* rank, const float* fix_x,
+                              const float* fix_y, const int* net_slot, const int* cslot, int* spc,
+                              float* sdx, float* sdy, int* sslot, cudaStream_t s);
+
 // tensor-core solve path (k_tc.cu): tc_setup lays the plan out in a device
 // block of tc_elems(n) bf16 elements owned by the handle and fills its
 // cosine/sine tables on stream s; launch_tc part 0 splits rho (with the
