@@ -230,22 +230,30 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
     size_t nn = (size_t)c.n * c.n;
     CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
     bool dens = (what & EV_DENSITY) != 0, wa = (what & EV_WA) != 0;
-    if (wa) {
+    // with both branches the scatter also writes the WA kernel's positions,
+    // and the WA branch forks after it
+    const bool pos_from_scatter = dens && wa;
+    auto wa_branch = [&](bool interleave) -> fftpl_status {
         CK(cudaEventRecord(c.ev_fork, s));
         CK(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
-        Stage st(c, 4, c.side);
-        if (!c.opt.deterministic)
-            CK(cudaMemsetAsync(c.gW2, 0, (size_t)c.m_mov * sizeof(float2), c.side));
-        CK(launch_wa(c, x, y, gamma, c.side));
-    }
-    if (wa) CK(cudaEventRecord(c.ev_join, c.side));
+        {
+            Stage st(c, 4, c.side);
+            if (!c.opt.deterministic)
+                CK(cudaMemsetAsync(c.gW2, 0, (size_t)c.m_mov * sizeof(float2), c.side));
+            CK(launch_wa_impl(c, x, y, gamma, nullptr, nullptr, interleave, c.side));
+        }
+        CK(cudaEventRecord(c.ev_join, c.side));
+        return FFTPL_OK;
+    };
+    if (wa && !pos_from_scatter) TRY(wa_branch(true));
     if (dens) {
         {
             Stage st(c, 0, s);
             if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
             else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
-            CK(launch_scatter(c, x, y, c.w, c.h, c.m_mov, c.D, c.Dq, s));
+            CK(launch_scatter_mov(c, x, y, pos_from_scatter, s));
         }
+        if (pos_from_scatter) TRY(wa_branch(false));
         TRY(enqueue_solve(c, s));
     }
     if (wa) CK(cudaStreamWaitEvent(s, c.ev_join, 0));
@@ -897,7 +905,7 @@ fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
         CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
         if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
         else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
-        CK(launch_scatter(c, c.v, c.v + c.m_mov, c.w, c.h, c.m_mov, c.D, c.Dq, s));
+        CK(launch_scatter_mov(c, c.v, c.v + c.m_mov, false, s));
         CK(launch_tau(c, s));
         CK(launch_gamma0(c, s));
     }
@@ -913,21 +921,22 @@ fftpl_status fftpl::loop_enqueue(Ctx& c) {
     const float* vx = c.v;
     const float* vy = c.v + c.m_mov;
     CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
+    {
+        Stage st(c, 0, s);
+        if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
+        else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
+        CK(launch_scatter_mov(c, vx, vy, true, s));
+    }
+    // the WA branch forks after the scatter, which wrote its positions
     CK(cudaEventRecord(c.ev_fork, s));
     CK(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
     {
         Stage st(c, 4, c.side);
         if (!c.opt.deterministic)
             CK(cudaMemsetAsync(c.gW2, 0, (size_t)c.m_mov * sizeof(float2), c.side));
-        CK(launch_wa_impl(c, vx, vy, 1.0f, c.ctrl + C_GAMMA, c.ctrl + C_DONE, c.side));
+        CK(launch_wa_impl(c, vx, vy, 1.0f, c.ctrl + C_GAMMA, c.ctrl + C_DONE, false, c.side));
     }
     CK(cudaEventRecord(c.ev_join, c.side));
-    {
-        Stage st(c, 0, s);
-        if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
-        else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
-        CK(launch_scatter(c, vx, vy, c.w, c.h, c.m_mov, c.D, c.Dq, s));
-    }
     TRY(enqueue_solve(c, s));
     CK(cudaStreamWaitEvent(s, c.ev_join, 0));
     { Stage st(c, 5, s); CK(launch_loop_cells(c, s)); }

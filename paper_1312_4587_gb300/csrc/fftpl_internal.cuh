@@ -449,6 +449,10 @@ void set_global_error(const std::string& msg);
 void prepare_spectral(int logn);
 cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* w,
                            const float* h, int m, float* D, long long* Dq, cudaStream_t s);
+// movable cells into the handle's D / Dq; write_pos: also the interleaved
+// centres pos2 (by internal cell number) for the WA kernel
+cudaError_t launch_scatter_mov(Ctx& c, const float* x, const float* y, bool write_pos,
+                               cudaStream_t s);
 cudaError_t launch_bin_ranges(Ctx& c, const float* x, const float* y, int32_t* ranges,
                               cudaStream_t s);
 cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s);
@@ -460,8 +464,10 @@ cudaError_t launch_q_to_f(const long long* q, float scale, float* out, int count
 cudaError_t launch_gather(Ctx& c, const float* x, const float* y, float* gx, float* gy,
                           bool adjoint, cudaStream_t s);
 cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, cudaStream_t s);
+// interleave = false: pos2 already written (by launch_scatter_mov)
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
-                           const double* gamma_dev, const double* done, cudaStream_t s);
+                           const double* gamma_dev, const double* done, bool interleave,
+                           cudaStream_t s);
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s);
 
 // create-time netlist layout (k_setup.cu): label rounds for the internal

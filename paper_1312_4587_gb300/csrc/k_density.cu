@@ -18,14 +18,18 @@ namespace fftpl {
 // Deterministic mode: ov is formed in float32 (x and y lengths, then their
 // product), scaled by 2^32 (exact) and rounded to the nearest integer (ties to
 // even); int64 atomics make the bin sums independent of order.
+// pos, if given, receives the interleaved centre at the cell's internal
+// number for the WA kernel (so that it needs no pass of its own).
 template <bool QUANT>
 __global__ void __launch_bounds__(kCellThreads)
 k_scatter(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
-          const float* __restrict__ w, const float* __restrict__ h, float* __restrict__ D,
-          unsigned long long* __restrict__ Dq) {
+          const float* __restrict__ w, const float* __restrict__ h, const int* __restrict__ rank,
+          float2* __restrict__ pos, float* __restrict__ D, unsigned long long* __restrict__ Dq) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    Span s = cell_span(g, x[i], y[i], w[i], h[i]);
+    const float xi = x[i], yi = y[i];
+    if (pos) pos[rank[i]] = make_float2(xi, yi);
+    Span s = cell_span(g, xi, yi, w[i], h[i]);
     if (s.ilo > s.ihi || s.jlo > s.jhi) return;
     const AxisOv ax = axis_ov(g.x0, g.wb, s.ilo, s.ihi, s.xl, s.xh);
     const AxisOv ay = axis_ov(g.y0, g.hb, s.jlo, s.jhi, s.yl, s.yh);
@@ -148,10 +152,29 @@ cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* 
     if (m <= 0) return cudaSuccess;
     int nb = blocks_for(m, kCellThreads);
     if (Dq)
-        k_scatter<true><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, nullptr,
+        k_scatter<true><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, nullptr, nullptr,
+                                                   nullptr,
                                                    reinterpret_cast<unsigned long long*>(Dq));
     else
-        k_scatter<false><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, D, nullptr);
+        k_scatter<false><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, nullptr, nullptr, D,
+                                                    nullptr);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_mov(Ctx& c, const float* x, const float* y, bool write_pos,
+                               cudaStream_t s) {
+    const int m = c.m_mov;
+    if (m <= 0) return cudaSuccess;
+    float2* pos = write_pos ? c.pos2 : nullptr;
+    int nb = blocks_for(m, kCellThreads);
+    if (c.opt.deterministic)
+        k_scatter<true><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, c.w, c.h, c.cell_rank, pos,
+                                                   nullptr,
+                                                   reinterpret_cast<unsigned long long*>(c.Dq));
+    else
+        k_scatter<false><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, c.w, c.h, c.cell_rank, pos,
+                                                    c.D, nullptr);
     c.launches++;
     return cudaGetLastError();
 }

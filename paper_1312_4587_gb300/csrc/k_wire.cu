@@ -270,9 +270,10 @@ k_split(int m, const int* __restrict__ rank, const float2* __restrict__ gW2,
 static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }
 
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
-                           const double* gamma_dev, const double* done, cudaStream_t s) {
+                           const double* gamma_dev, const double* done, bool interleave,
+                           cudaStream_t s) {
     if (c.nslabs <= 0) return cudaSuccess;
-    if (c.m_mov > 0) {
+    if (c.m_mov > 0 && interleave) {
         k_interleave<<<nblk(c.m_mov, 256), 256, 0, s>>>(c.m_mov, x, y, c.cell_rank, c.pos2,
                                                          done);
         c.launches++;
@@ -292,7 +293,7 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
 }
 
 cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, cudaStream_t s) {
-    return launch_wa_impl(c, x, y, gamma, nullptr, nullptr, s);
+    return launch_wa_impl(c, x, y, gamma, nullptr, nullptr, true, s);
 }
 
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s) {
