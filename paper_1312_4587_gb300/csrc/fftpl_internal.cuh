@@ -143,48 +143,40 @@ __device__ __forceinline__ float ov_at(const AxisOv& r, int k) {
 }
 
 // Field gather of one cell: sum_b ov(i,b) E2[b] over its bin span, E2 the
-// interleaved (E_x, E_y) map.  Spans of at most 2 rows x 4 columns (nearly
-// every cell) issue all their loads at once, predicated, before any use.
+// interleaved (E_x, E_y) map, in chunks of 2 rows x 4 columns whose loads
+// are all issued (predicated) before any use.  Nearly every cell is one
+// chunk; a wider cell only adds chunks, so a warp's lanes run the same body.
 __device__ __forceinline__ float2 gather_span(const Grid& g, const Span& s,
                                               const float2* __restrict__ E2) {
-    const int nr = s.jhi - s.jlo + 1, nc = s.ihi - s.ilo + 1;
     float sx = 0.0f, sy = 0.0f;
-    if (nr <= 0 || nc <= 0) return make_float2(0.0f, 0.0f);
+    if (s.jlo > s.jhi || s.ilo > s.ihi) return make_float2(0.0f, 0.0f);
     const AxisOv ax = axis_ov(g.x0, g.wb, s.ilo, s.ihi, s.xl, s.xh);
     const AxisOv ay = axis_ov(g.y0, g.hb, s.jlo, s.jhi, s.yl, s.yh);
-    if (nr <= 2 && nc <= 4) {
-        float2 e[2][4];
+    for (int j0 = s.jlo; j0 <= s.jhi; j0 += 2) {
+        for (int k0 = s.ilo; k0 <= s.ihi; k0 += 4) {
+            float2 e[2][4];
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int j = min(s.jlo + a, s.jhi);
+            for (int a = 0; a < 2; ++a) {
+                const int j = min(j0 + a, s.jhi);
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int k = min(s.ilo + b, s.ihi);
-                e[a][b] = (a < nr && b < nc) ? __ldg(E2 + (size_t)j * g.n + k)
-                                             : make_float2(0.0f, 0.0f);
+                for (int b = 0; b < 4; ++b) {
+                    const int k = min(k0 + b, s.ihi);
+                    e[a][b] = (j0 + a <= s.jhi && k0 + b <= s.ihi)
+                                  ? __ldg(E2 + (size_t)j * g.n + k)
+                                  : make_float2(0.0f, 0.0f);
+                }
             }
-        }
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            if (a >= nr) break;
-            float oy = ov_at(ay, s.jlo + a);
+            for (int a = 0; a < 2; ++a) {
+                if (j0 + a > s.jhi) break;
+                const float oy = ov_at(ay, j0 + a);
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                if (b >= nc) break;
-                float o = __fmul_rn(ov_at(ax, s.ilo + b), oy);
-                sx = fmaf(o, e[a][b].x, sx);
-                sy = fmaf(o, e[a][b].y, sy);
-            }
-        }
-    } else {
-        for (int j = s.jlo; j <= s.jhi; ++j) {
-            float oy = ov_at(ay, j);
-            const float2* r = E2 + (size_t)j * g.n;
-            for (int k = s.ilo; k <= s.ihi; ++k) {
-                float o = __fmul_rn(ov_at(ax, k), oy);
-                float2 e = __ldg(r + k);
-                sx = fmaf(o, e.x, sx);
-                sy = fmaf(o, e.y, sy);
+                for (int b = 0; b < 4; ++b) {
+                    if (k0 + b > s.ihi) break;
+                    const float o = __fmul_rn(ov_at(ax, k0 + b), oy);
+                    sx = fmaf(o, e[a][b].x, sx);
+                    sy = fmaf(o, e[a][b].y, sy);
+                }
             }
         }
     }

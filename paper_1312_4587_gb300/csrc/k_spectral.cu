@@ -144,9 +144,14 @@ __device__ __forceinline__ void stockham_stage(float2* __restrict__ buf, const f
             v[i][0] = src[pidx(j)];
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[r * st];
-                if (inv) w.y = -w.y;
-                v[i][r] = cmul(src[pidx(j + r * NR)], w);
+                if (Ns == 1) {
+                    // first stage: every twiddle is exp(0) = 1
+                    v[i][r] = src[pidx(j + r * NR)];
+                } else {
+                    float2 w = tw[r * st];
+                    if (inv) w.y = -w.y;
+                    v[i][r] = cmul(src[pidx(j + r * NR)], w);
+                }
             }
             dst[i] = (f << 24) | ((j - k) * R + k);   // buffer and element index
         }
