@@ -60,61 +60,29 @@ __device__ __forceinline__ float2 pin_xy(const WaIo& io, int c, float ox, float 
     return make_float2(__fadd_rn(p.x, ox), __fadd_rn(p.y, oy));
 }
 
+// WA of one net whose D pin coordinates are in registers: max/min, the
+// exponential sums, W~ and HPWL into wsum/hsum, and the pin gradients out
+// (the pin's cell number, or its deterministic slot, is re-read at the pin's
+// slot base + 32 k: an L1 hit, cheaper than holding it in registers).
 template <int D, bool CSR>
-__device__ __forceinline__ void wa_net(const WaIo& io, int base, int d, float l2g, float inv_g,
-                                       float& wsum, float& hsum) {
-    constexpr int R = D > 0 ? D : 1;
-    float rx[R], ry[R], ex_p[R], ex_m[R], ey_p[R], ey_m[R];
-    const int dd = D > 0 ? D : d;
+__device__ __forceinline__ void wa_core(const float (&rx)[D], const float (&ry)[D], int base,
+                                        const WaIo& io, float l2g, float inv_g, float& wsum,
+                                        float& hsum) {
+    float ex_p[D], ex_m[D], ey_p[D], ey_m[D];
     float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
-    if (D > 0) {
-        int cr[R];
-        float ox[R], oy[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            cr[k] = io.pin_cell[base + 32 * k];
-            ox[k] = io.pin_dx[base + 32 * k];
-            oy[k] = io.pin_dy[base + 32 * k];
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            float2 p = pin_xy(io, cr[k], ox[k], oy[k]);
-            rx[k] = p.x;
-            ry[k] = p.y;
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            Mx = fmaxf(Mx, rx[k]); mx = fminf(mx, rx[k]);
-            My = fmaxf(My, ry[k]); my = fminf(my, ry[k]);
-        }
-    } else {
-#pragma unroll 4
-        for (int k = 0; k < dd; ++k) {
-            const int sl = base + 32 * k;
-            float2 p = pin_xy(io, io.pin_cell[sl], io.pin_dx[sl], io.pin_dy[sl]);
-            io.pxy[sl] = p;
-            Mx = fmaxf(Mx, p.x); mx = fminf(mx, p.x);
-            My = fmaxf(My, p.y); my = fminf(my, p.y);
-        }
+    for (int k = 0; k < D; ++k) {
+        Mx = fmaxf(Mx, rx[k]); mx = fminf(mx, rx[k]);
+        My = fmaxf(My, ry[k]); my = fminf(my, ry[k]);
     }
     float Spx = 0, Tpx = 0, Smx = 0, Tmx = 0, Spy = 0, Tpy = 0, Smy = 0, Tmy = 0;
-    auto sums = [&](float px, float py, float& apx, float& amx, float& apy, float& amy) {
-        float tpx = px - Mx, tmx = px - mx, tpy = py - My, tmy = py - my;
-        apx = exp2f(tpx * l2g); amx = exp2f(-tmx * l2g);
-        apy = exp2f(tpy * l2g); amy = exp2f(-tmy * l2g);
-        Spx += apx; Tpx = fmaf(tpx, apx, Tpx); Smx += amx; Tmx = fmaf(tmx, amx, Tmx);
-        Spy += apy; Tpy = fmaf(tpy, apy, Tpy); Smy += amy; Tmy = fmaf(tmy, amy, Tmy);
-    };
-    if (D > 0) {
 #pragma unroll
-        for (int k = 0; k < R; ++k) sums(rx[k], ry[k], ex_p[k], ex_m[k], ey_p[k], ey_m[k]);
-    } else {
-#pragma unroll 4
-        for (int k = 0; k < dd; ++k) {
-            float2 p = io.pxy[base + 32 * k];
-            float a, b, c2, e;
-            sums(p.x, p.y, a, b, c2, e);
-        }
+    for (int k = 0; k < D; ++k) {
+        float tpx = rx[k] - Mx, tmx = rx[k] - mx, tpy = ry[k] - My, tmy = ry[k] - my;
+        ex_p[k] = exp2f(tpx * l2g); ex_m[k] = exp2f(-tmx * l2g);
+        ey_p[k] = exp2f(tpy * l2g); ey_m[k] = exp2f(-tmy * l2g);
+        Spx += ex_p[k]; Tpx = fmaf(tpx, ex_p[k], Tpx); Smx += ex_m[k]; Tmx = fmaf(tmx, ex_m[k], Tmx);
+        Spy += ey_p[k]; Tpy = fmaf(tpy, ey_p[k], Tpy); Smy += ey_m[k]; Tmy = fmaf(tmy, ey_m[k], Tmy);
     }
     // every S is in [1, d] (its largest term is exp(0) = 1): the fast
     // reciprocal (2 ulp) is accurate over that whole range
@@ -132,36 +100,133 @@ __device__ __forceinline__ void wa_net(const WaIo& io, int base, int d, float l2
     const float Q0x = imx * fmaf(Wmx, inv_g, 1.0f), Q1x = imx * inv_g;
     const float P0y = isy * fmaf(-Wpy, inv_g, 1.0f), P1y = isy * inv_g;
     const float Q0y = imy * fmaf(Wmy, inv_g, 1.0f), Q1y = imy * inv_g;
-    auto emit = [&](int k, float px, float py, float apx, float amx, float apy, float amy) {
-        float tpx = px - Mx, tmx = px - mx, tpy = py - My, tmy = py - my;
-        float gxj = apx * fmaf(tpx, P1x, P0x) - amx * fmaf(-tmx, Q1x, Q0x);
-        float gyj = apy * fmaf(tpy, P1y, P0y) - amy * fmaf(-tmy, Q1y, Q0y);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float tpx = rx[k] - Mx, tmx = rx[k] - mx, tpy = ry[k] - My, tmy = ry[k] - my;
+        float gxj = ex_p[k] * fmaf(tpx, P1x, P0x) - ex_m[k] * fmaf(-tmx, Q1x, Q0x);
+        float gyj = ey_p[k] * fmaf(tpy, P1y, P0y) - ey_m[k] * fmaf(-tmy, Q1y, Q0y);
         if (CSR) {
             int sl = io.pin_slot[base + 32 * k];
             if (sl >= 0) io.gpin[sl] = make_float2(gxj, gyj);
         } else {
-            // the cell number is re-read (an L1 hit) rather than held in
-            // registers through the exponentials
             int c = io.pin_cell[base + 32 * k];
             if (c >= 0) atomicAdd(io.gW + c, make_float2(gxj, gyj));
-        }
-    };
-    if (D > 0) {
-#pragma unroll
-        for (int k = 0; k < R; ++k)
-            emit(k, rx[k], ry[k], ex_p[k], ex_m[k], ey_p[k], ey_m[k]);
-    } else {
-#pragma unroll 4
-        for (int k = 0; k < dd; ++k) {
-            const int sl = base + 32 * k;
-            float2 p = io.pxy[sl];
-            float tpx = p.x - Mx, tmx = p.x - mx, tpy = p.y - My, tmy = p.y - my;
-            emit(k, p.x, p.y, exp2f(tpx * l2g), exp2f(-tmx * l2g), exp2f(tpy * l2g),
-                 exp2f(-tmy * l2g));
         }
     }
 }
 
+// Pin coordinates of a net of degree D at slot base: all record loads
+// first, then all centre gathers.
+template <int D>
+__device__ __forceinline__ void wa_load(const WaIo& io, int base, float (&rx)[D], float (&ry)[D]) {
+    int cr[D];
+    float ox[D], oy[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        cr[k] = io.pin_cell[base + 32 * k];
+        ox[k] = io.pin_dx[base + 32 * k];
+        oy[k] = io.pin_dy[base + 32 * k];
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float2 p = pin_xy(io, cr[k], ox[k], oy[k]);
+        rx[k] = p.x;
+        ry[k] = p.y;
+    }
+}
+
+template <int D, bool CSR>
+__device__ __forceinline__ void wa_net(const WaIo& io, int base, float l2g, float inv_g,
+                                       float& wsum, float& hsum) {
+    float rx[D], ry[D];
+    wa_load<D>(io, base, rx, ry);
+    wa_core<D, CSR>(rx, ry, base, io, l2g, inv_g, wsum, hsum);
+}
+
+// Two nets of the same degree per lane (from two slabs): both nets' loads
+// are in flight together.  A lane outside a slab's net count reads that
+// slab's padding slots (cell -1) and skips the net.
+template <int D, bool CSR>
+__device__ __forceinline__ void wa_pair(const WaIo& io, int base_a, bool live_a, int base_b,
+                                        bool live_b, float l2g, float inv_g, float& wsum,
+                                        float& hsum) {
+    float ax[D], ay[D], bx[D], by[D];
+    wa_load<D>(io, base_a, ax, ay);
+    wa_load<D>(io, base_b, bx, by);
+    if (live_a) wa_core<D, CSR>(ax, ay, base_a, io, l2g, inv_g, wsum, hsum);
+    if (live_b) wa_core<D, CSR>(bx, by, base_b, io, l2g, inv_g, wsum, hsum);
+}
+
+// Runtime degree d (slabs of degree > 6): the first pass stores the pin
+// coordinates in the pins' own slots of pxy, the later passes re-read them.
+template <bool CSR>
+__device__ __forceinline__ void wa_net_any(const WaIo& io, int base, int d, float l2g,
+                                           float inv_g, float& wsum, float& hsum) {
+    float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
+#pragma unroll 4
+    for (int k = 0; k < d; ++k) {
+        const int sl = base + 32 * k;
+        float2 p = pin_xy(io, io.pin_cell[sl], io.pin_dx[sl], io.pin_dy[sl]);
+        io.pxy[sl] = p;
+        Mx = fmaxf(Mx, p.x); mx = fminf(mx, p.x);
+        My = fmaxf(My, p.y); my = fminf(my, p.y);
+    }
+    float Spx = 0, Tpx = 0, Smx = 0, Tmx = 0, Spy = 0, Tpy = 0, Smy = 0, Tmy = 0;
+#pragma unroll 4
+    for (int k = 0; k < d; ++k) {
+        float2 p = io.pxy[base + 32 * k];
+        float tpx = p.x - Mx, tmx = p.x - mx, tpy = p.y - My, tmy = p.y - my;
+        float apx = exp2f(tpx * l2g), amx = exp2f(-tmx * l2g);
+        float apy = exp2f(tpy * l2g), amy = exp2f(-tmy * l2g);
+        Spx += apx; Tpx = fmaf(tpx, apx, Tpx); Smx += amx; Tmx = fmaf(tmx, amx, Tmx);
+        Spy += apy; Tpy = fmaf(tpy, apy, Tpy); Smy += amy; Tmy = fmaf(tmy, amy, Tmy);
+    }
+    const float isx = __fdividef(1.0f, Spx), imx = __fdividef(1.0f, Smx);
+    const float isy = __fdividef(1.0f, Spy), imy = __fdividef(1.0f, Smy);
+    const float Wpx = Tpx * isx, Wmx = Tmx * imx, Wpy = Tpy * isy, Wmy = Tmy * imy;
+    const float span = (Mx - mx) + (My - my);
+    hsum += span;
+    wsum += span + ((Wpx - Wmx) + (Wpy - Wmy));
+    const float P0x = isx * fmaf(-Wpx, inv_g, 1.0f), P1x = isx * inv_g;
+    const float Q0x = imx * fmaf(Wmx, inv_g, 1.0f), Q1x = imx * inv_g;
+    const float P0y = isy * fmaf(-Wpy, inv_g, 1.0f), P1y = isy * inv_g;
+    const float Q0y = imy * fmaf(Wmy, inv_g, 1.0f), Q1y = imy * inv_g;
+#pragma unroll 4
+    for (int k = 0; k < d; ++k) {
+        const int sl = base + 32 * k;
+        float2 p = io.pxy[sl];
+        float tpx = p.x - Mx, tmx = p.x - mx, tpy = p.y - My, tmy = p.y - my;
+        float gxj = exp2f(tpx * l2g) * fmaf(tpx, P1x, P0x) - exp2f(-tmx * l2g) * fmaf(-tmx, Q1x, Q0x);
+        float gyj = exp2f(tpy * l2g) * fmaf(tpy, P1y, P0y) - exp2f(-tmy * l2g) * fmaf(-tmy, Q1y, Q0y);
+        if (CSR) {
+            int q = io.pin_slot[sl];
+            if (q >= 0) io.gpin[q] = make_float2(gxj, gyj);
+        } else {
+            int c = io.pin_cell[sl];
+            if (c >= 0) atomicAdd(io.gW + c, make_float2(gxj, gyj));
+        }
+    }
+}
+
+template <bool CSR>
+__device__ __forceinline__ void wa_slab(const WaIo& io, const int4& sl, int lane, float l2g,
+                                        float inv_g, float& wsum, float& hsum) {
+    if (lane >= sl.z) return;
+    const int base = sl.x + lane;
+    // the degree is the same for the whole warp, so this switch does not diverge
+    switch (sl.y) {
+        case 2: wa_net<2, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
+        case 3: wa_net<3, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
+        case 4: wa_net<4, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
+        case 5: wa_net<5, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
+        case 6: wa_net<6, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
+        default: wa_net_any<CSR>(io, base, sl.y, l2g, inv_g, wsum, hsum); break;
+    }
+}
+
+// One warp per pair of consecutive slabs (2w, 2w+1).  When both have the
+// same degree 2..4 (most nets) each lane runs its two nets with their loads
+// in flight together; otherwise the slabs go one after the other.
 template <bool CSR>
 __global__ void __launch_bounds__(kWaThreads, 4)
 k_wa(int nslabs, const int4* __restrict__ slabs, WaIo io, float gamma,
@@ -174,19 +239,20 @@ k_wa(int nslabs, const int4* __restrict__ slabs, WaIo io, float gamma,
     const float inv_g = 1.0f / gamma;
     // exp(t / g) = exp2(t * log2(e) / g)
     const float l2g = (float)(1.4426950408889634 / (double)gamma);
-    const int4 sl = warp < nslabs ? slabs[warp] : make_int4(0, 0, 0, 0);
-    const int base = sl.x + lane, d = sl.y;
+    const int4 zero = make_int4(0, 0, 0, 0);
+    const int4 sa = 2 * warp < nslabs ? slabs[2 * warp] : zero;
+    const int4 sb = 2 * warp + 1 < nslabs ? slabs[2 * warp + 1] : zero;
     float wsum = 0.0f, hsum = 0.0f;
-    if (lane < sl.z) {
-        // d is the same for the whole warp, so this switch does not diverge
-        switch (d) {
-            case 2: wa_net<2, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
-            case 3: wa_net<3, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
-            case 4: wa_net<4, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
-            case 5: wa_net<5, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
-            case 6: wa_net<6, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
-            default: wa_net<0, CSR>(io, base, d, l2g, inv_g, wsum, hsum); break;
+    if (sa.y == sb.y && sa.y >= 2 && sa.y <= 4) {
+        const bool la = lane < sa.z, lb = lane < sb.z;
+        switch (sa.y) {
+            case 2: wa_pair<2, CSR>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
+            case 3: wa_pair<3, CSR>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
+            default: wa_pair<4, CSR>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
         }
+    } else {
+        wa_slab<CSR>(io, sa, lane, l2g, inv_g, wsum, hsum);
+        wa_slab<CSR>(io, sb, lane, l2g, inv_g, wsum, hsum);
     }
     reduce2(wsum, hsum, acc, ACC_W, ACC_HPWL, dr);
 }
@@ -281,7 +347,7 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
     const WaIo io{c.pin_cell, c.pin_dx, c.pin_dy, c.pos2, c.pxy,
                   c.opt.deterministic ? nullptr : c.gW2, c.pin_slot, c.gpin};
     const int wpb = kWaThreads / 32;
-    int nb = nblk(c.nslabs, wpb);
+    int nb = nblk((c.nslabs + 1) / 2, wpb);   // one warp per pair of slabs
     if (c.opt.deterministic)
         k_wa<true><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, io, gamma, gamma_dev, c.acc, done,
                                              det_red(c, 1));
