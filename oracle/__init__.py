@@ -59,7 +59,11 @@ class IterRec(C.Structure):
 class LoopOpts(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("gamma_fixed", C.c_double),
                 ("dw_ref", C.c_double), ("alpha_max0_bins", C.c_double),
-                ("stop_on_tau", C.c_int), ("tau_stop", C.c_double)]
+                ("stop_on_tau", C.c_int), ("tau_stop", C.c_double),
+                ("wirelength", C.c_int), ("helmholtz_eps", C.c_double)]
+
+# wirelength models
+WL_WA, WL_LSE = 0, 1
 
 
 _P = C.c_void_p
@@ -75,6 +79,7 @@ def lib():
             L.orc_energy.restype = C.c_double
             L.orc_overflow.restype = C.c_double
             L.orc_wa.restype = C.c_double
+            L.orc_wl.restype = C.c_double
             L.orc_mu.restype = C.c_double
             L.orc_mu.argtypes = [C.c_double, C.c_double]
             L.orc_gamma.restype = C.c_double
@@ -161,20 +166,26 @@ def density(region, n, rho_t, x, y, w, h, fx=None, fy=None, fw=None, fh=None):
     return rho, D, F
 
 
-def dct_coeffs(rho):
+def dct_coeffs(rho, keep_dc=False):
+    """Eq. 10 coefficients a[v][u]; the (0,0) one zeroed unless keep_dc."""
     rho = _f64(rho)
     n = rho.shape[0]
     a = np.zeros((n, n))
-    lib().orc_dct_coeffs(C.c_int(n), _ptr(rho), _ptr(a))
+    if keep_dc:
+        lib().orc_dct_coeffs_dc(C.c_int(n), _ptr(rho), _ptr(a))
+    else:
+        lib().orc_dct_coeffs(C.c_int(n), _ptr(rho), _ptr(a))
     return a
 
 
-def potential_field(a, Lx, Ly):
+def potential_field(a, Lx, Ly, eps=0.0):
+    """psi, E_x, E_y (Eqs. 11-12); eps > 0: Helmholtz divisor w^2 + eps
+    with the (0,0) mode a_00/eps (Eq. 4)."""
     a = _f64(a)
     n = a.shape[0]
     psi = np.zeros((n, n)); ex = np.zeros((n, n)); ey = np.zeros((n, n))
-    lib().orc_potential_field(C.c_int(n), C.c_double(Lx), C.c_double(Ly), _ptr(a),
-                              _ptr(psi), _ptr(ex), _ptr(ey))
+    lib().orc_potential_field_eps(C.c_int(n), C.c_double(Lx), C.c_double(Ly), _ptr(a),
+                                  C.c_double(eps), _ptr(psi), _ptr(ex), _ptr(ey))
     return psi, ex, ey
 
 
@@ -190,10 +201,11 @@ def potential_at(a, Lx, Ly, xs, ys):
     return psi, ex, ey
 
 
-def solve(rho, Lx, Ly):
-    """rho -> (a, psi, E_x, E_y) by the explicit cosine sums of Eqs. 9-12."""
-    a = dct_coeffs(rho)
-    psi, ex, ey = potential_field(a, Lx, Ly)
+def solve(rho, Lx, Ly, eps=0.0):
+    """rho -> (a, psi, E_x, E_y) by the explicit cosine sums of Eqs. 9-12
+    (eps > 0: the Helmholtz equation of Eq. 4)."""
+    a = dct_coeffs(rho, keep_dc=eps > 0)
+    psi, ex, ey = potential_field(a, Lx, Ly, eps)
     return a, psi, ex, ey
 
 
@@ -231,8 +243,10 @@ def overflow(D, F, Ab, rho_t, total_mov_area):
                                     _ptr(D), _ptr(F), C.c_double(total_mov_area)))
 
 
-def wa(net_ptr, pin_cell, dx, dy, m_mov, x, y, gamma, fx=None, fy=None, per_pin=False):
-    """Weighted-average wirelength.  Returns dict with W (sum), hpwl, net_w [E],
+def wa(net_ptr, pin_cell, dx, dy, m_mov, x, y, gamma, fx=None, fy=None, per_pin=False,
+       model=WL_WA):
+    """Smoothed wirelength: weighted average (Eq. 3, model WL_WA) or
+    log-sum-exp (WL_LSE).  Returns dict with W (sum), hpwl, net_w [E],
     gcx/gcy [m_mov] and, if per_pin, gpx/gpy [P]."""
     net_ptr, pin_cell = _i32(net_ptr), _i32(pin_cell)
     dx, dy, x, y = map(_f32, (dx, dy, x, y))
@@ -245,7 +259,7 @@ def wa(net_ptr, pin_cell, dx, dy, m_mov, x, y, gamma, fx=None, fy=None, per_pin=
     gpx = np.zeros(max(P, 1)) if per_pin else None
     gpy = np.zeros(max(P, 1)) if per_pin else None
     hp = C.c_double(0.0)
-    W = lib().orc_wa(C.c_int(E), _ptr(net_ptr), _ptr(pin_cell), _ptr(dx), _ptr(dy),
+    W = lib().orc_wl(C.c_int(model), C.c_int(E), _ptr(net_ptr), _ptr(pin_cell), _ptr(dx), _ptr(dy),
                      C.c_int(m_mov), _ptr(x), _ptr(y), _ptr(fx), _ptr(fy), C.c_double(gamma),
                      _ptr(net_w), _ptr(gpx), _ptr(gpy), _ptr(gcx), _ptr(gcy), C.byref(hp))
     out = dict(W=float(W), hpwl=float(hp.value), net_w=net_w[:E], gcx=gcx[:m_mov],
@@ -275,8 +289,10 @@ def _inst_arrays(inst):
     return m, k, w, h, fw, fh
 
 
-def eval_instance(inst, x=None, y=None, gamma=None, maps=False):
-    """One full objective-gradient evaluation of a synth.Instance."""
+def eval_instance(inst, x=None, y=None, gamma=None, maps=False, wirelength=WL_WA,
+                  helmholtz_eps=0.0):
+    """One full objective-gradient evaluation of a synth.Instance
+    (wirelength WL_WA or WL_LSE; helmholtz_eps > 0: Eq. 4 in place of Eq. 8)."""
     m, k, w, h, fw, fh = _inst_arrays(inst)
     x = _f32(inst.x if x is None else x)
     y = _f32(inst.y if y is None else y)
@@ -290,11 +306,12 @@ def eval_instance(inst, x=None, y=None, gamma=None, maps=False):
     mp = [np.zeros((n, n)) for _ in range(4)] if maps else [None] * 4
     out = EvalOut()
     R = _region(inst.region)
-    lib().orc_eval(C.byref(R), C.c_int(n), C.c_double(inst.target_density), C.c_int(m),
-                   _ptr(x), _ptr(y), _ptr(w), _ptr(h), C.c_int(k), _ptr(fx), _ptr(fy),
-                   _ptr(fw), _ptr(fh), C.c_int(net_ptr.shape[0] - 1), _ptr(net_ptr),
-                   _ptr(pin_cell), _ptr(dx), _ptr(dy), C.c_double(gamma),
-                   _ptr(gNx), _ptr(gNy), _ptr(gWx), _ptr(gWy),
+    lib().orc_eval2(C.byref(R), C.c_int(n), C.c_double(inst.target_density), C.c_int(m),
+                    _ptr(x), _ptr(y), _ptr(w), _ptr(h), C.c_int(k), _ptr(fx), _ptr(fy),
+                    _ptr(fw), _ptr(fh), C.c_int(net_ptr.shape[0] - 1), _ptr(net_ptr),
+                    _ptr(pin_cell), _ptr(dx), _ptr(dy), C.c_double(gamma),
+                    C.c_int(wirelength), C.c_double(helmholtz_eps),
+                    _ptr(gNx), _ptr(gNy), _ptr(gWx), _ptr(gWy),
                    _ptr(mp[0]), _ptr(mp[1]), _ptr(mp[2]), _ptr(mp[3]), C.byref(out))
     res = dict(N=out.N, W=out.W, hpwl=out.hpwl, tau=out.tau, total_mov_area=out.total_mov_area,
                gN_l1=out.gN_l1, gW_l1=out.gW_l1, gNx=gNx, gNy=gNy, gWx=gWx, gWy=gWy)
@@ -304,7 +321,8 @@ def eval_instance(inst, x=None, y=None, gamma=None, maps=False):
 
 
 def nesterov(inst, iters, lambda0=0.0, gamma_fixed=None, dw_ref=3.5e5, alpha_max0_bins=0.044,
-             stop_on_tau=False, tau_stop=0.1, x=None, y=None):
+             stop_on_tau=False, tau_stop=0.1, x=None, y=None, wirelength=WL_WA,
+             helmholtz_eps=0.0):
     """Global placement loop (Algorithm 1 with a Nesterov step).  Returns
     (x, y, records[k] dicts, iterations run)."""
     m, k, w, h, fw, fh = _inst_arrays(inst)
@@ -316,7 +334,7 @@ def nesterov(inst, iters, lambda0=0.0, gamma_fixed=None, dw_ref=3.5e5, alpha_max
     dx, dy = _f32(inst.pin_dx), _f32(inst.pin_dy)
     gf = inst.gamma if gamma_fixed is None else gamma_fixed
     opts = LoopOpts(float(lambda0), float(gf), float(dw_ref), float(alpha_max0_bins),
-                    int(stop_on_tau), float(tau_stop))
+                    int(stop_on_tau), float(tau_stop), int(wirelength), float(helmholtz_eps))
     recs = (IterRec * max(iters, 1))()
     R = _region(inst.region)
     ran = lib().orc_nesterov(C.byref(R), C.c_int(inst.n), C.c_double(inst.target_density),

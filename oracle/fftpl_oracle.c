@@ -22,6 +22,12 @@
  *   - cell edges and pin coordinates are rounded to float32 before use, as the
  *     inputs are float32 arrays: xl = fl32(x - w/2), xh = fl32(x + w/2),
  *     px = fl32(x + dx).  Bins are half-open [e_k, e_k+1).
+ *   - the LSE wirelength that Section II names (without a formula) is the
+ *     usual g ln sum exp(p/g) + g ln sum exp(-p/g) per axis;
+ *   - the Helmholtz smoothing of Eq. 4 is taken with the right-hand side of
+ *     Eq. 8 (laplacian psi - eps psi = -rho), so each mode is divided by
+ *     w_u^2 + w_v^2 + eps and, for eps > 0, the (0,0) mode is kept (a_00/eps:
+ *     the unique solution).
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (see build.py).
  */
@@ -242,8 +248,8 @@ static double eps(int u) { return u == 0 ? 1.0 : 2.0; }
 /* Eq. 10 (normalised so that Eq. 9 is its inverse):
  *   a[v][u] = (eps_u eps_v / n^2) sum_y sum_x rho[y][x] cos(w_u x) cos(w_v y)
  * The double sum is taken one index at a time (the sum of products factors).
- * The (0,0) coefficient is then set to zero (DC removal, Section III-A). */
-void orc_dct_coeffs(int n, const double* rho, double* a) {
+ * All coefficients, the (0,0) one included. */
+void orc_dct_coeffs_dc(int n, const double* rho, double* a) {
     double* C = cos_table(n, 0);                   /* C[u][x] */
     double* t = (double*)malloc((size_t)n * n * sizeof(double)); /* t[u][y] */
 #pragma omp parallel for schedule(static)
@@ -260,27 +266,39 @@ void orc_dct_coeffs(int n, const double* rho, double* a) {
             for (int y = 0; y < n; ++y) s += C[(size_t)v * n + y] * t[(size_t)u * n + y];
             a[(size_t)v * n + u] = eps(u) * eps(v) / ((double)n * n) * s;
         }
-    a[0] = 0.0;
     free(C);
     free(t);
+}
+
+/* Eq. 10 with the (0,0) coefficient set to zero (DC removal, Section III-A). */
+void orc_dct_coeffs(int n, const double* rho, double* a) {
+    orc_dct_coeffs_dc(n, rho, a);
+    a[0] = 0.0;
+}
+
+/* Spectral divide: a/(w_u^2 + w_v^2 + eps); the (0,0) mode is a_00/eps for
+ * eps > 0 (Helmholtz, Eq. 4) and left out for eps = 0 (Poisson, Eq. 8). */
+static double spectral_hat(double a, int u, int v, double Lx, double Ly, double eps_h) {
+    double wu = M_PI * u / Lx, wv = M_PI * v / Ly;
+    if (u == 0 && v == 0) return eps_h > 0.0 ? a / eps_h : 0.0;
+    return a / (wu * wu + wv * wv + eps_h);
 }
 
 /* Eqs. 11 and 12 at the bin centres:
  *   psi = sum_{u,v} a/(w_u^2+w_v^2) cos(w_u x) cos(w_v y)
  *   E_x = sum_{u,v} a w_u/(w_u^2+w_v^2) sin(w_u x) cos(w_v y)
  *   E_y = sum_{u,v} a w_v/(w_u^2+w_v^2) cos(w_u x) sin(w_v y)
- * with w_u = pi u / Lx, w_v = pi v / Ly and the (0,0) term left out.
- * a is indexed a[v][u]; outputs are [y][x].  Any output may be NULL. */
-void orc_potential_field(int n, double Lx, double Ly, const double* a,
-                         double* psi, double* ex, double* ey) {
+ * with w_u = pi u / Lx, w_v = pi v / Ly and the (0,0) term left out; with
+ * eps_h > 0 the divisor is w_u^2 + w_v^2 + eps_h and the (0,0) term is kept
+ * (Helmholtz, Eq. 4).  a is indexed a[v][u]; outputs are [y][x].  Any output
+ * may be NULL. */
+void orc_potential_field_eps(int n, double Lx, double Ly, const double* a, double eps_h,
+                             double* psi, double* ex, double* ey) {
     size_t nn = (size_t)n * n;
     double* hat = (double*)malloc(nn * sizeof(double));  /* hat[u][v] = a/(w^2) */
     for (int v = 0; v < n; ++v)
-        for (int u = 0; u < n; ++u) {
-            double wu = M_PI * u / Lx, wv = M_PI * v / Ly;
-            double d = wu * wu + wv * wv;
-            hat[(size_t)u * n + v] = (u == 0 && v == 0) ? 0.0 : a[(size_t)v * n + u] / d;
-        }
+        for (int u = 0; u < n; ++u)
+            hat[(size_t)u * n + v] = spectral_hat(a[(size_t)v * n + u], u, v, Lx, Ly, eps_h);
     double* Ct = cos_table(n, 1);  /* Ct[x][u] = cos(w_u x) */
     double* St = sin_table_t(n);   /* St[x][u] = sin(w_u x) */
     /* inner sums over v for each (u, y) */
@@ -322,6 +340,11 @@ void orc_potential_field(int n, double Lx, double Ly, const double* a,
             if (ey) ey[(size_t)y * n + x] = s_ey;
         }
     free(hat); free(Ct); free(St); free(pc); free(ps); free(pcT); free(psT);
+}
+
+void orc_potential_field(int n, double Lx, double Ly, const double* a,
+                         double* psi, double* ex, double* ey) {
+    orc_potential_field_eps(n, Lx, Ly, a, 0.0, psi, ex, ey);
 }
 
 /* Eqs. 11 and 12 at chosen bin centres only: for each k < count the sums
@@ -486,6 +509,28 @@ static double wa_axis(int deg, const double* p, double g, double* grad, double* 
     return Wp - Wm;
 }
 
+/* Log-sum-exp wirelength of one net along one axis (the LSE model Section II
+ * names): g ln sum_j exp(p_j/g) + g ln sum_j exp(-p_j/g), evaluated with the
+ * exponentials shifted by the max (resp. min):
+ *   = (M - mu) + g (ln S+ + ln S-),  S+ = sum exp((p_j - M)/g),
+ *                                    S- = sum exp((mu - p_j)/g)
+ *   d/dp_j = exp((p_j - M)/g)/S+ - exp((mu - p_j)/g)/S-
+ * Same interface as wa_axis. */
+static double lse_axis(int deg, const double* p, double g, double* grad, double* span) {
+    double M = p[0], mu = p[0];
+    for (int j = 1; j < deg; ++j) { M = dmax(M, p[j]); mu = dmin(mu, p[j]); }
+    *span = M - mu;
+    double Sp = 0, Sm = 0;
+    for (int j = 0; j < deg; ++j) {
+        Sp += exp((p[j] - M) / g);
+        Sm += exp((mu - p[j]) / g);
+    }
+    if (grad)
+        for (int j = 0; j < deg; ++j)
+            grad[j] = exp((p[j] - M) / g) / Sp - exp((mu - p[j]) / g) / Sm;
+    return (M - mu) + g * (log(Sp) + log(Sm));
+}
+
 /* Smoothed wirelength of all nets and its gradient.  Pin j of net e sits on
  * cell pin_cell[j] (movable if < m_mov, else macro pin_cell[j]-m_mov) at offset
  * (dx, dy) from the centre.  Degree-1 nets contribute nothing (W~ = 0, zero
@@ -494,11 +539,12 @@ static double wa_axis(int deg, const double* p, double g, double* grad, double* 
  *   gpx/gpy[P]    dW~/d(pin coordinate)
  *   gcx/gcy[m]    dW~/d(cell centre) = sum over that cell's pins
  * Returns sum_e W~_e; *hpwl receives the HPWL of Eq. 1 on pin coordinates. */
-double orc_wa(int E, const int32_t* net_ptr, const int32_t* pin_cell,
+double orc_wl(int model, int E, const int32_t* net_ptr, const int32_t* pin_cell,
               const float* dx, const float* dy, int m_mov,
               const float* x, const float* y, const float* fx, const float* fy,
               double gamma, double* net_w, double* gpx, double* gpy,
               double* gcx, double* gcy, double* hpwl) {
+    double (*axis)(int, const double*, double, double*, double*) = model ? lse_axis : wa_axis;
     double total = 0.0, hp = 0.0;
     if (gcx) memset(gcx, 0, (size_t)m_mov * sizeof(double));
     if (gcy) memset(gcy, 0, (size_t)m_mov * sizeof(double));
@@ -523,7 +569,7 @@ double orc_wa(int E, const int32_t* net_ptr, const int32_t* pin_cell,
         double we = 0.0;
         if (d >= 2) {
             double sx, sy;
-            we = wa_axis(d, px, gamma, gx, &sx) + wa_axis(d, py, gamma, gy, &sy);
+            we = axis(d, px, gamma, gx, &sx) + axis(d, py, gamma, gy, &sy);
             hp += sx + sy;
         } else {
             for (int j = 0; j < d; ++j) { gx[j] = 0.0; gy[j] = 0.0; }
@@ -545,6 +591,16 @@ double orc_wa(int E, const int32_t* net_ptr, const int32_t* pin_cell,
     return total;
 }
 
+/* The weighted-average model (Eq. 3) of orc_wl. */
+double orc_wa(int E, const int32_t* net_ptr, const int32_t* pin_cell,
+              const float* dx, const float* dy, int m_mov,
+              const float* x, const float* y, const float* fx, const float* fy,
+              double gamma, double* net_w, double* gpx, double* gpy,
+              double* gcx, double* gcy, double* hpwl) {
+    return orc_wl(0, E, net_ptr, pin_cell, dx, dy, m_mov, x, y, fx, fy, gamma, net_w, gpx, gpy,
+                  gcx, gcy, hpwl);
+}
+
 /* ------------------------------------------------------------------------ */
 /* One full objective-gradient evaluation (Algorithm 1, steps f, rho, FFT    */
 /* solve and gradient).                                                     */
@@ -555,15 +611,17 @@ typedef struct {
     double gN_l1, gW_l1;
 } orc_eval_out;
 
-/* Evaluates density energy + gradient and WA wirelength + gradient at (x, y).
- * Any of the map outputs (rho, psi, ex, ey) may be NULL. */
-void orc_eval(const orc_region* R, int n, double rho_t,
-              int m_mov, const float* x, const float* y, const float* w, const float* h,
-              int m_fix, const float* fx, const float* fy, const float* fw, const float* fh,
-              int E, const int32_t* net_ptr, const int32_t* pin_cell,
-              const float* pdx, const float* pdy, double gamma,
-              double* gNx, double* gNy, double* gWx, double* gWy,
-              double* rho_o, double* psi_o, double* ex_o, double* ey_o, orc_eval_out* out) {
+/* Evaluates density energy + gradient and the wirelength + gradient at
+ * (x, y): model 0 weighted average (Eq. 3), 1 log-sum-exp; eps_h 0 the
+ * Poisson solve (Eq. 8), > 0 the Helmholtz solve (Eq. 4).  Any of the map
+ * outputs (rho, psi, ex, ey) may be NULL. */
+void orc_eval2(const orc_region* R, int n, double rho_t,
+               int m_mov, const float* x, const float* y, const float* w, const float* h,
+               int m_fix, const float* fx, const float* fy, const float* fw, const float* fh,
+               int E, const int32_t* net_ptr, const int32_t* pin_cell,
+               const float* pdx, const float* pdy, double gamma, int model, double eps_h,
+               double* gNx, double* gNy, double* gWx, double* gWy,
+               double* rho_o, double* psi_o, double* ex_o, double* ey_o, orc_eval_out* out) {
     size_t nn = (size_t)n * n;
     double Lx = R->x1 - R->x0, Ly = R->y1 - R->y0;
     double Ab = (Lx / n) * (Ly / n);
@@ -575,15 +633,16 @@ void orc_eval(const orc_region* R, int n, double rho_t,
     double* ex = (double*)malloc(nn * sizeof(double));
     double* ey = (double*)malloc(nn * sizeof(double));
     orc_density(R, n, rho_t, m_mov, x, y, w, h, m_fix, fx, fy, fw, fh, rho, D, F);
-    orc_dct_coeffs(n, rho, a);
-    orc_potential_field(n, Lx, Ly, a, psi, ex, ey);
+    if (eps_h > 0.0) orc_dct_coeffs_dc(n, rho, a);
+    else orc_dct_coeffs(n, rho, a);
+    orc_potential_field_eps(n, Lx, Ly, a, eps_h, psi, ex, ey);
     double q = 0.0;
     for (int i = 0; i < m_mov; ++i) q += (double)w[i] * (double)h[i];
     out->total_mov_area = q;
     out->N = orc_energy(n, Ab, rho, psi);
     out->tau = orc_overflow(n, Ab, rho_t, D, F, q);
     orc_gather(R, n, m_mov, x, y, w, h, ex, ey, gNx, gNy);
-    out->W = orc_wa(E, net_ptr, pin_cell, pdx, pdy, m_mov, x, y, fx, fy, gamma,
+    out->W = orc_wl(model, E, net_ptr, pin_cell, pdx, pdy, m_mov, x, y, fx, fy, gamma,
                     NULL, NULL, NULL, gWx, gWy, &out->hpwl);
     double l1n = 0.0, l1w = 0.0;
     for (int i = 0; i < m_mov; ++i) {
@@ -597,6 +656,18 @@ void orc_eval(const orc_region* R, int n, double rho_t,
     if (ex_o) memcpy(ex_o, ex, nn * sizeof(double));
     if (ey_o) memcpy(ey_o, ey, nn * sizeof(double));
     free(rho); free(D); free(F); free(a); free(psi); free(ex); free(ey);
+}
+
+/* orc_eval2 with the weighted-average model and the Poisson solve. */
+void orc_eval(const orc_region* R, int n, double rho_t,
+              int m_mov, const float* x, const float* y, const float* w, const float* h,
+              int m_fix, const float* fx, const float* fy, const float* fw, const float* fh,
+              int E, const int32_t* net_ptr, const int32_t* pin_cell,
+              const float* pdx, const float* pdy, double gamma,
+              double* gNx, double* gNy, double* gWx, double* gWy,
+              double* rho_o, double* psi_o, double* ex_o, double* ey_o, orc_eval_out* out) {
+    orc_eval2(R, n, rho_t, m_mov, x, y, w, h, m_fix, fx, fy, fw, fh, E, net_ptr, pin_cell, pdx,
+              pdy, gamma, 0, 0.0, gNx, gNy, gWx, gWy, rho_o, psi_o, ex_o, ey_o, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -629,6 +700,8 @@ typedef struct {
     double alpha_max0_bins; /* 0.044 */
     int stop_on_tau;     /* stop when tau <= tau_stop */
     double tau_stop;     /* 0.1 */
+    int wirelength;      /* 0 weighted average (Eq. 3), 1 log-sum-exp */
+    double helmholtz_eps; /* 0 Poisson (Eq. 8), > 0 Helmholtz (Eq. 4) */
 } orc_loop_opts;
 
 /* Global placement loop (Algorithm 1 with the CG step replaced by Nesterov's
@@ -694,8 +767,9 @@ int orc_nesterov(const orc_region* R, int n, double rho_t,
             gamma = orc_gamma(orc_overflow(n, wb * ((R->y1 - R->y0) / n), rho_t, D, F, q), wb);
             free(rho); free(D); free(F);
         }
-        orc_eval(R, n, rho_t, m_mov, xf, yf, w, h, m_fix, fx, fy, fw, fh, E, net_ptr, pin_cell,
-                 pdx, pdy, gamma, gN, gN + m_mov, gW, gW + m_mov, NULL, NULL, NULL, NULL, &ev);
+        orc_eval2(R, n, rho_t, m_mov, xf, yf, w, h, m_fix, fx, fy, fw, fh, E, net_ptr, pin_cell,
+                  pdx, pdy, gamma, o->wirelength, o->helmholtz_eps, gN, gN + m_mov, gW,
+                  gW + m_mov, NULL, NULL, NULL, NULL, &ev);
         if (k == 0 && lambda <= 0.0) lambda = ev.gN_l1 > 0 ? ev.gW_l1 / ev.gN_l1 : 1.0;
         if (k >= 1) lambda *= orc_mu(ev.hpwl - hp_prev, o->dw_ref);
         hp_prev = ev.hpwl;
