@@ -284,6 +284,38 @@ def run_tc_path(args, inst, x, y, g, flush, stream):
                          "peak_kind": f"{kind} bf16 burst (solve timed alone)"}}
 
 
+def run_variants(args, inst, x, y, g, flush, stream):
+    """The same step with the model variants (each its own handle): the LSE
+    wirelength and the Helmholtz smoothing of Eq. 4."""
+    import math
+
+    import torch
+    from paper_1312_4587_gb300 import fftpl as F
+    L = inst.region[2] - inst.region[0]
+    out = {}
+    for name, opts in (("lse", dict(wirelength=F.FFTPL_WL_LSE)),
+                       ("helmholtz", dict(helmholtz_eps=4.0 * (math.pi / L) ** 2))):
+        prob = F.Problem(inst, use_graphs=0 if args.no_graphs else 1, **opts)
+        for _ in range(max(3, args.warmup)):
+            F.fftpl_eval(prob.h, x, y, inst.gamma, *g, sync=False)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            F.fftpl_eval(prob.h, x, y, inst.gamma, *g, sync=False)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        F.fftpl_check(prob.h)
+        prob.close()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        out[name] = {"value": round(1000.0 / ms, 2), "unit": UNIT, "ms_per_step": round(ms, 5),
+                     "options": {k: (round(v, 9) if isinstance(v, float) else v)
+                                 for k, v in opts.items()}}
+    return out
+
+
 def cpu_baseline_sample(inst):
     """The oracle as it stands, one evaluation of the same instance."""
     import oracle
@@ -401,6 +433,8 @@ def run_ours(args, ws, rank, local):
                             "unit": "GB/s", "frac": st["frac"],
                             "traffic": stage_traffic(dom, args.workload),
                             "algorithmic_bytes": st["bytes"], "peak_kind": peak_kind}
+    if not args.no_variants:
+        line["variants"] = run_variants(args, inst, x, y, g, flush, stream)
     if not args.no_tc_path and n >= F.FFTPL_TC_MIN_N:
         line["tc_path"] = run_tc_path(args, inst, x, y, g, flush, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -422,6 +456,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the LSE / Helmholtz variant timings")
     ap.add_argument("--no-tc-path", action="store_true",
                     help="skip the tensor-core solve path comparison")
     ap.add_argument("--serving-jobs", type=int, default=200,

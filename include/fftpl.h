@@ -126,6 +126,12 @@ enum {
 };
 #define FFTPL_TC_MIN_N 128
 
+/* Wirelength models.  FFTPL_WL_WA: the weighted average of Eq. 3.
+ * FFTPL_WL_LSE: the log-sum-exp model Section II names, per net and axis
+ * g ln sum exp(p/g) + g ln sum exp(-p/g), with gradient
+ * softmax(p/g) - softmax(-p/g). */
+enum { FFTPL_WL_WA = 0, FFTPL_WL_LSE = 1 };
+
 typedef struct {
     double target_density;  /* rho_t (Section III-B, Section V: 1.0) */
     int32_t solve_path;     /* FFTPL_SOLVE_* */
@@ -142,7 +148,15 @@ typedef struct {
     int32_t stop_on_tau;    /* 1: fftpl_step stops when tau <= tau_stop */
     int32_t use_graphs;     /* 1: replay captured CUDA graphs for repeated
                                calls with the same buffers */
-    int32_t reserved[6];
+    int32_t wirelength;     /* FFTPL_WL_WA (default) or FFTPL_WL_LSE */
+    int32_t reserved0;
+    double helmholtz_eps;   /* 0: the Poisson equation of Eq. 8 (the (0,0)
+                               mode dropped); > 0: the Helmholtz smoothing of
+                               Eq. 4, laplacian psi - eps psi = -rho: every
+                               mode divided by w_u^2 + w_v^2 + eps and the
+                               (0,0) mode kept as a_00 / eps (placement
+                               units^-2; finite, >= 0, else FFTPL_EINVAL) */
+    int32_t reserved[2];
 } fftpl_options;
 
 /* FP64 scalars of one evaluation. */

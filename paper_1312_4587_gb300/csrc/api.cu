@@ -162,6 +162,10 @@ fftpl_status validate(Ctx& c, const fftpl_region* R, int n, const fftpl_cells* c
         if (opt->solve_path == FFTPL_SOLVE_TC_BF16X3 && n < FFTPL_TC_MIN_N)
             return set_err(c, FFTPL_EINVAL, "the tensor-core solve path needs n >= 128");
         if (!(opt->dw_ref > 0.0)) return set_err(c, FFTPL_EINVAL, "dw_ref must be > 0");
+        if (opt->wirelength != FFTPL_WL_WA && opt->wirelength != FFTPL_WL_LSE)
+            return set_err(c, FFTPL_EINVAL, "unknown wirelength model");
+        if (!(opt->helmholtz_eps >= 0.0) || !isfinite(opt->helmholtz_eps))
+            return set_err(c, FFTPL_EINVAL, "helmholtz_eps must be finite and >= 0");
     }
     return FFTPL_OK;
 }
@@ -323,6 +327,8 @@ void fftpl_default_options(fftpl_options* o) {
     o->tau_stop = 0.1;
     o->stop_on_tau = 0;
     o->use_graphs = 0;
+    o->wirelength = FFTPL_WL_WA;
+    o->helmholtz_eps = 0.0;
 }
 
 void fftpl_debug_fail_alloc_after(int32_t k) { g_fail_after.store(k > 0 ? k : 0); }

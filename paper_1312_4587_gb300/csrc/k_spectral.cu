@@ -317,7 +317,7 @@ template <int LOGN>
 __global__ void __launch_bounds__(kSpecThreads, 2)
 k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__ RT,
        const float2* __restrict__ tw, const float2* __restrict__ ph, float pi_lx, float pi_ly,
-       double* __restrict__ acc, DetRed dr) {
+       float eps, double* __restrict__ acc, DetRed dr) {
     constexpr int N = 1 << LOGN;
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = NB;
@@ -377,11 +377,15 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
                 float wu = pi_lx * (float)u;
                 float eu = (u == 0) ? 1.0f : 2.0f;
                 float a0 = eu * ev * invn2 * B[rr][0];
-                float psi0 = (u == 0 && v == 0) ? 0.0f : a0 / (wu * wu + wv * wv);
+                // Poisson: (0,0) mode dropped; Helmholtz (eps > 0): divisor
+                // w^2 + eps and the (0,0) mode kept
+                float psi0 = (u == 0 && v == 0 && !(eps > 0.0f))
+                                 ? 0.0f
+                                 : a0 / (wu * wu + wv * wv + eps);
                 float psin = 0.0f;
                 if (has_n) {
                     float an = eu * 2.0f * invn2 * B[rr][1];
-                    psin = an / (wu * wu + wvn * wvn);
+                    psin = an / (wu * wu + wvn * wvn + eps);
                     energy = df_add(energy, B[rr][1] * psin);
                 }
                 energy = df_add(energy, B[rr][0] * psi0);
@@ -534,7 +538,8 @@ static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {
     } else if (which == 1) {
         auto kf = k_cols<LOGN>;
         kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.T1, c.PT, c.RT, c.tw, c.ph, pi_lx, pi_ly,
-                                                        c.acc, det_red(c, 0));
+                                                        (float)c.opt.helmholtz_eps, c.acc,
+                                                        det_red(c, 0));
     } else {
         auto kf = k_rows_inv<LOGN>;
         size_t smem_inv = smem + (size_t)kSpecBuffers * N * sizeof(float);

@@ -51,6 +51,7 @@ struct EpiArgs {
     float2* E2;          // EPI_PSI_EX (.x) and EPI_EY (.y), [row][n]
     int n;
     float pi_lx, pi_ly, invn2;
+    float eps;           // EPI_SPECTRAL: Helmholtz term (0: Poisson)
     double* acc;
     DetRed dr;
     int* err;
@@ -291,7 +292,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
                         const float wu = ep.pi_lx * (float)u;
                         const float eu = u == 0 ? 1.0f : 2.0f;
                         const float a = eu * ev * ep.invn2 * v[j];
-                        const float p = (u == 0 && vv == 0) ? 0.0f : a / (wu * wu + wv * wv);
+                        const float p = (u == 0 && vv == 0 && !(ep.eps > 0.0f))
+                                            ? 0.0f
+                                            : a / (wu * wu + wv * wv + ep.eps);
                         energy = df_add(energy, v[j] * p);
                         v[j] = p;
                     }
@@ -542,6 +545,7 @@ cudaError_t launch_tc(Ctx& c, int part, cudaStream_t s) {
         ep.pi_lx = (float)(M_PI / c.Lx);
         ep.pi_ly = (float)(M_PI / c.Ly);
         ep.invn2 = 1.0f / ((float)n * (float)n);
+        ep.eps = (float)c.opt.helmholtz_eps;
         e = gemm<tc::EPI_SPECTRAL>(p.mC, p.mA1, n, n, n, 3, ep, s);
         c.launches++;
     } else {

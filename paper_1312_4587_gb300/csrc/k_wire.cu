@@ -64,7 +64,7 @@ __device__ __forceinline__ float2 pin_xy(const WaIo& io, int c, float ox, float 
 // exponential sums, W~ and HPWL into wsum/hsum, and the pin gradients out
 // (the pin's cell number, or its deterministic slot, is re-read at the pin's
 // slot base + 32 k: an L1 hit, cheaper than holding it in registers).
-template <int D, bool CSR>
+template <int D, bool CSR, bool LSE>
 __device__ __forceinline__ void wa_core(const float (&rx)[D], const float (&ry)[D], int base,
                                         const WaIo& io, float l2g, float inv_g, float& wsum,
                                         float& hsum) {
@@ -93,6 +93,25 @@ __device__ __forceinline__ void wa_core(const float (&rx)[D], const float (&ry)[
     // the warp totals)
     const float span = (Mx - mx) + (My - my);
     hsum += span;
+    if (LSE) {
+        // g (ln S+ + ln S-) per axis on top of the span; gradient
+        // a+/S+ - a-/S- (softmax difference)
+        wsum += span + __fdividef(1.0f, inv_g) * ((logf(Spx) + logf(Smx)) +
+                                                  (logf(Spy) + logf(Smy)));
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            float gxj = ex_p[k] * isx - ex_m[k] * imx;
+            float gyj = ey_p[k] * isy - ey_m[k] * imy;
+            if (CSR) {
+                int sl = io.pin_slot[base + 32 * k];
+                if (sl >= 0) io.gpin[sl] = make_float2(gxj, gyj);
+            } else {
+                int c = io.pin_cell[base + 32 * k];
+                if (c >= 0) atomicAdd(io.gW + c, make_float2(gxj, gyj));
+            }
+        }
+        return;
+    }
     wsum += span + ((Wpx - Wmx) + (Wpy - Wmy));
     // dW~/dp = a+ (P0 + t+ P1) - a- (Q0 - t- Q1) per axis, with
     // P0 = (1 - W+/g)/S+, P1 = 1/(g S+), Q0 = (1 + W-/g)/S-, Q1 = 1/(g S-)
@@ -135,31 +154,31 @@ __device__ __forceinline__ void wa_load(const WaIo& io, int base, float (&rx)[D]
     }
 }
 
-template <int D, bool CSR>
+template <int D, bool CSR, bool LSE>
 __device__ __forceinline__ void wa_net(const WaIo& io, int base, float l2g, float inv_g,
                                        float& wsum, float& hsum) {
     float rx[D], ry[D];
     wa_load<D>(io, base, rx, ry);
-    wa_core<D, CSR>(rx, ry, base, io, l2g, inv_g, wsum, hsum);
+    wa_core<D, CSR, LSE>(rx, ry, base, io, l2g, inv_g, wsum, hsum);
 }
 
 // Two nets of the same degree per lane (from two slabs): both nets' loads
 // are in flight together.  A lane outside a slab's net count reads that
 // slab's padding slots (cell -1) and skips the net.
-template <int D, bool CSR>
+template <int D, bool CSR, bool LSE>
 __device__ __forceinline__ void wa_pair(const WaIo& io, int base_a, bool live_a, int base_b,
                                         bool live_b, float l2g, float inv_g, float& wsum,
                                         float& hsum) {
     float ax[D], ay[D], bx[D], by[D];
     wa_load<D>(io, base_a, ax, ay);
     wa_load<D>(io, base_b, bx, by);
-    if (live_a) wa_core<D, CSR>(ax, ay, base_a, io, l2g, inv_g, wsum, hsum);
-    if (live_b) wa_core<D, CSR>(bx, by, base_b, io, l2g, inv_g, wsum, hsum);
+    if (live_a) wa_core<D, CSR, LSE>(ax, ay, base_a, io, l2g, inv_g, wsum, hsum);
+    if (live_b) wa_core<D, CSR, LSE>(bx, by, base_b, io, l2g, inv_g, wsum, hsum);
 }
 
 // Runtime degree d (slabs of degree > 6): the first pass stores the pin
 // coordinates in the pins' own slots of pxy, the later passes re-read them.
-template <bool CSR>
+template <bool CSR, bool LSE>
 __device__ __forceinline__ void wa_net_any(const WaIo& io, int base, int d, float l2g,
                                            float inv_g, float& wsum, float& hsum) {
     float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
@@ -186,7 +205,11 @@ __device__ __forceinline__ void wa_net_any(const WaIo& io, int base, int d, floa
     const float Wpx = Tpx * isx, Wmx = Tmx * imx, Wpy = Tpy * isy, Wmy = Tmy * imy;
     const float span = (Mx - mx) + (My - my);
     hsum += span;
-    wsum += span + ((Wpx - Wmx) + (Wpy - Wmy));
+    if (LSE)
+        wsum += span + __fdividef(1.0f, inv_g) * ((logf(Spx) + logf(Smx)) +
+                                                  (logf(Spy) + logf(Smy)));
+    else
+        wsum += span + ((Wpx - Wmx) + (Wpy - Wmy));
     const float P0x = isx * fmaf(-Wpx, inv_g, 1.0f), P1x = isx * inv_g;
     const float Q0x = imx * fmaf(Wmx, inv_g, 1.0f), Q1x = imx * inv_g;
     const float P0y = isy * fmaf(-Wpy, inv_g, 1.0f), P1y = isy * inv_g;
@@ -196,8 +219,14 @@ __device__ __forceinline__ void wa_net_any(const WaIo& io, int base, int d, floa
         const int sl = base + 32 * k;
         float2 p = io.pxy[sl];
         float tpx = p.x - Mx, tmx = p.x - mx, tpy = p.y - My, tmy = p.y - my;
-        float gxj = exp2f(tpx * l2g) * fmaf(tpx, P1x, P0x) - exp2f(-tmx * l2g) * fmaf(-tmx, Q1x, Q0x);
-        float gyj = exp2f(tpy * l2g) * fmaf(tpy, P1y, P0y) - exp2f(-tmy * l2g) * fmaf(-tmy, Q1y, Q0y);
+        float gxj, gyj;
+        if (LSE) {
+            gxj = exp2f(tpx * l2g) * isx - exp2f(-tmx * l2g) * imx;
+            gyj = exp2f(tpy * l2g) * isy - exp2f(-tmy * l2g) * imy;
+        } else {
+            gxj = exp2f(tpx * l2g) * fmaf(tpx, P1x, P0x) - exp2f(-tmx * l2g) * fmaf(-tmx, Q1x, Q0x);
+            gyj = exp2f(tpy * l2g) * fmaf(tpy, P1y, P0y) - exp2f(-tmy * l2g) * fmaf(-tmy, Q1y, Q0y);
+        }
         if (CSR) {
             int q = io.pin_slot[sl];
             if (q >= 0) io.gpin[q] = make_float2(gxj, gyj);
@@ -208,26 +237,26 @@ __device__ __forceinline__ void wa_net_any(const WaIo& io, int base, int d, floa
     }
 }
 
-template <bool CSR>
+template <bool CSR, bool LSE>
 __device__ __forceinline__ void wa_slab(const WaIo& io, const int4& sl, int lane, float l2g,
                                         float inv_g, float& wsum, float& hsum) {
     if (lane >= sl.z) return;
     const int base = sl.x + lane;
     // the degree is the same for the whole warp, so this switch does not diverge
     switch (sl.y) {
-        case 2: wa_net<2, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
-        case 3: wa_net<3, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
-        case 4: wa_net<4, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
-        case 5: wa_net<5, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
-        case 6: wa_net<6, CSR>(io, base, l2g, inv_g, wsum, hsum); break;
-        default: wa_net_any<CSR>(io, base, sl.y, l2g, inv_g, wsum, hsum); break;
+        case 2: wa_net<2, CSR, LSE>(io, base, l2g, inv_g, wsum, hsum); break;
+        case 3: wa_net<3, CSR, LSE>(io, base, l2g, inv_g, wsum, hsum); break;
+        case 4: wa_net<4, CSR, LSE>(io, base, l2g, inv_g, wsum, hsum); break;
+        case 5: wa_net<5, CSR, LSE>(io, base, l2g, inv_g, wsum, hsum); break;
+        case 6: wa_net<6, CSR, LSE>(io, base, l2g, inv_g, wsum, hsum); break;
+        default: wa_net_any<CSR, LSE>(io, base, sl.y, l2g, inv_g, wsum, hsum); break;
     }
 }
 
 // One warp per pair of consecutive slabs (2w, 2w+1).  When both have the
 // same degree 2..4 (most nets) each lane runs its two nets with their loads
 // in flight together; otherwise the slabs go one after the other.
-template <bool CSR>
+template <bool CSR, bool LSE>
 __global__ void __launch_bounds__(kWaThreads, 4)
 k_wa(int nslabs, const int4* __restrict__ slabs, WaIo io, float gamma,
      const double* __restrict__ gamma_dev, double* __restrict__ acc,
@@ -246,13 +275,13 @@ k_wa(int nslabs, const int4* __restrict__ slabs, WaIo io, float gamma,
     if (sa.y == sb.y && sa.y >= 2 && sa.y <= 4) {
         const bool la = lane < sa.z, lb = lane < sb.z;
         switch (sa.y) {
-            case 2: wa_pair<2, CSR>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
-            case 3: wa_pair<3, CSR>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
-            default: wa_pair<4, CSR>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
+            case 2: wa_pair<2, CSR, LSE>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
+            case 3: wa_pair<3, CSR, LSE>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
+            default: wa_pair<4, CSR, LSE>(io, sa.x + lane, la, sb.x + lane, lb, l2g, inv_g, wsum, hsum); break;
         }
     } else {
-        wa_slab<CSR>(io, sa, lane, l2g, inv_g, wsum, hsum);
-        wa_slab<CSR>(io, sb, lane, l2g, inv_g, wsum, hsum);
+        wa_slab<CSR, LSE>(io, sa, lane, l2g, inv_g, wsum, hsum);
+        wa_slab<CSR, LSE>(io, sb, lane, l2g, inv_g, wsum, hsum);
     }
     reduce2(wsum, hsum, acc, ACC_W, ACC_HPWL, dr);
 }
@@ -348,12 +377,18 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                   c.opt.deterministic ? nullptr : c.gW2, c.pin_slot, c.gpin};
     const int wpb = kWaThreads / 32;
     int nb = nblk((c.nslabs + 1) / 2, wpb);   // one warp per pair of slabs
-    if (c.opt.deterministic)
-        k_wa<true><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, io, gamma, gamma_dev, c.acc, done,
-                                             det_red(c, 1));
-    else
-        k_wa<false><<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, io, gamma, gamma_dev, c.acc,
-                                              done, det_red(c, 1));
+    const bool lse = c.opt.wirelength == FFTPL_WL_LSE;
+    auto go = [&](auto kern) {
+        kern<<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, io, gamma, gamma_dev, c.acc, done,
+                                       det_red(c, 1));
+    };
+    if (c.opt.deterministic) {
+        if (lse) go(k_wa<true, true>);
+        else go(k_wa<true, false>);
+    } else {
+        if (lse) go(k_wa<false, true>);
+        else go(k_wa<false, false>);
+    }
     c.launches++;
     return cudaGetLastError();
 }

@@ -127,3 +127,23 @@ def test_debug_tc_gemm_validation(F, M, N, K, nsplit):
     st = F.lib().fftpl_debug_tc_gemm(p, p, p, p, M, N, K, p, nsplit, 0, p, None)
     assert st == F.FFTPL_EINVAL
     assert "fftpl_debug_tc_gemm" in F.fftpl_last_error(None)
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("wirelength", 5, "unknown wirelength model"),
+    ("helmholtz_eps", -1e-3, "helmholtz_eps"),
+    ("helmholtz_eps", float("nan"), "helmholtz_eps"),
+])
+def test_variant_options_validated(F, field, value, needle):
+    """Model-variant options are checked on the host before device work."""
+    o = F.fftpl_default_options(**{field: value})
+    with pytest.raises(F.FFTPLError) as ei:
+        _create(F, _tiny(), options=o)
+    assert ei.value.status == F.FFTPL_EINVAL and needle in str(ei.value)
+
+
+def test_options_struct_layout(F):
+    """The options struct keeps its size (88 bytes) with the variant fields."""
+    assert ctypes.sizeof(F.fftpl_options) == 88
+    o = F.fftpl_default_options()
+    assert o.wirelength == F.FFTPL_WL_WA and o.helmholtz_eps == 0.0
