@@ -87,6 +87,7 @@ def lib():
             L.orc_nesterov_a.restype = C.c_double
             L.orc_nesterov_a.argtypes = [C.c_double]
             L.orc_nesterov.restype = C.c_int
+            L.orc_cg.restype = C.c_int
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -320,11 +321,22 @@ def eval_instance(inst, x=None, y=None, gamma=None, maps=False, wirelength=WL_WA
     return res
 
 
-def nesterov(inst, iters, lambda0=0.0, gamma_fixed=None, dw_ref=3.5e5, alpha_max0_bins=0.044,
-             stop_on_tau=False, tau_stop=0.1, x=None, y=None, wirelength=WL_WA,
-             helmholtz_eps=0.0):
+def nesterov(inst, iters, **kw):
     """Global placement loop (Algorithm 1 with a Nesterov step).  Returns
     (x, y, records[k] dicts, iterations run)."""
+    return _loop("orc_nesterov", inst, iters, **kw)
+
+
+def cg(inst, iters, **kw):
+    """Global placement loop with the nonlinear CG step of Algorithm 1
+    (Polak-Ribiere+ direction, one quadratic-fit line search in
+    [0.01 a_max, a_max]).  Same arguments and results as nesterov."""
+    return _loop("orc_cg", inst, iters, **kw)
+
+
+def _loop(fn, inst, iters, lambda0=0.0, gamma_fixed=None, dw_ref=3.5e5, alpha_max0_bins=0.044,
+          stop_on_tau=False, tau_stop=0.1, x=None, y=None, wirelength=WL_WA,
+          helmholtz_eps=0.0):
     m, k, w, h, fw, fh = _inst_arrays(inst)
     x = _f32(inst.x if x is None else x).copy()
     y = _f32(inst.y if y is None else y).copy()
@@ -337,7 +349,7 @@ def nesterov(inst, iters, lambda0=0.0, gamma_fixed=None, dw_ref=3.5e5, alpha_max
                     int(stop_on_tau), float(tau_stop), int(wirelength), float(helmholtz_eps))
     recs = (IterRec * max(iters, 1))()
     R = _region(inst.region)
-    ran = lib().orc_nesterov(C.byref(R), C.c_int(inst.n), C.c_double(inst.target_density),
+    ran = getattr(lib(), fn)(C.byref(R), C.c_int(inst.n), C.c_double(inst.target_density),
                              C.c_int(m), _ptr(x), _ptr(y), _ptr(w), _ptr(h), C.c_int(k),
                              _ptr(fx), _ptr(fy), _ptr(fw), _ptr(fh),
                              C.c_int(net_ptr.shape[0] - 1), _ptr(net_ptr), _ptr(pin_cell),

@@ -819,3 +819,121 @@ int orc_nesterov(const orc_region* R, int n, double rho_t,
     free(xf); free(yf);
     return k;
 }
+
+/* Global placement loop with the nonlinear conjugate-gradient step of
+ * Algorithm 1 ("CGsolver" with the search interval [0.01 a_max, a_max] of
+ * Section IV-A).  Same options, records and clamping as orc_nesterov.
+ * The paper does not spell the CG step out; this is the reading:
+ *   g_k = grad W~(x_k; gamma_k) + lambda_k grad N(x_k),
+ *   f_k = W~(x_k) + lambda_k N(x_k)
+ *   d_k = -g_k + beta_k d_{k-1},  beta_k = max(0, g_k.(g_k - g_{k-1}) / |g_{k-1}|^2)
+ *         (Polak-Ribiere+; d_0 = -g_0; restart d_k = -g_k if g_k.d_k >= 0)
+ *   dh = d_k / |d_k|_inf  (so a step a moves the farthest cell by a)
+ *   slope s = g_k.dh;  trial f_t = f(clamp(x_k + a_max dh)) with the same
+ *   lambda_k, gamma_k;  quadratic fit c = (f_t - f_k - s a_max) / a_max^2,
+ *   a* = -s / (2c) if c > 0 else a_max;  a_k = min(a_max, max(0.01 a_max, a*))
+ *   x_{k+1} = clamp(x_k + a_k dh)
+ *   a_max_{k+1} = max(a_max_0, 2 a_k)  (Section IV-A)
+ *   lambda, gamma and the stop test as in orc_nesterov (HPWL at the x_k).
+ * recs[k].alpha = a_k; recs[k].step_max = a_k (the farthest move). */
+int orc_cg(const orc_region* R, int n, double rho_t,
+           int m_mov, float* x, float* y, const float* w, const float* h,
+           int m_fix, const float* fx, const float* fy, const float* fw, const float* fh,
+           int E, const int32_t* net_ptr, const int32_t* pin_cell,
+           const float* pdx, const float* pdy, const orc_loop_opts* o,
+           int iters, orc_iter_rec* recs) {
+    size_t m2 = (size_t)2 * m_mov;
+    double wb = (R->x1 - R->x0) / n;
+    double* u = (double*)malloc(m2 * sizeof(double));
+    double* d = (double*)malloc(m2 * sizeof(double));
+    double* g = (double*)malloc(m2 * sizeof(double));
+    double* gp = (double*)malloc(m2 * sizeof(double));
+    double* gN = (double*)malloc(m2 * sizeof(double));
+    double* gW = (double*)malloc(m2 * sizeof(double));
+    double* lo = (double*)malloc(m2 * sizeof(double));
+    double* hi = (double*)malloc(m2 * sizeof(double));
+    float* xf = (float*)malloc((size_t)m_mov * sizeof(float));
+    float* yf = (float*)malloc((size_t)m_mov * sizeof(float));
+    for (int i = 0; i < m_mov; ++i) {
+        lo[i] = R->x0 + 0.5 * w[i]; hi[i] = R->x1 - 0.5 * w[i];
+        lo[m_mov + i] = R->y0 + 0.5 * h[i]; hi[m_mov + i] = R->y1 - 0.5 * h[i];
+        u[i] = dmin(hi[i], dmax(lo[i], (double)x[i]));
+        u[m_mov + i] = dmin(hi[m_mov + i], dmax(lo[m_mov + i], (double)y[i]));
+    }
+    double lambda = o->lambda0, alpha_max0 = o->alpha_max0_bins * wb;
+    double alpha_max = alpha_max0, hp_prev = 0.0, gg_prev = 0.0;
+    double gamma = o->gamma_fixed;
+    int k;
+    for (k = 0; k < iters; ++k) {
+        for (int i = 0; i < m_mov; ++i) { xf[i] = (float)u[i]; yf[i] = (float)u[m_mov + i]; }
+        orc_eval_out ev;
+        if (k == 0 && gamma <= 0.0) {
+            size_t nn = (size_t)n * n;
+            double* rho = (double*)malloc(nn * sizeof(double));
+            double* D = (double*)malloc(nn * sizeof(double));
+            double* F = (double*)malloc(nn * sizeof(double));
+            orc_density(R, n, rho_t, m_mov, xf, yf, w, h, m_fix, fx, fy, fw, fh, rho, D, F);
+            double q = 0.0;
+            for (int i = 0; i < m_mov; ++i) q += (double)w[i] * (double)h[i];
+            gamma = orc_gamma(orc_overflow(n, wb * ((R->y1 - R->y0) / n), rho_t, D, F, q), wb);
+            free(rho); free(D); free(F);
+        }
+        orc_eval2(R, n, rho_t, m_mov, xf, yf, w, h, m_fix, fx, fy, fw, fh, E, net_ptr, pin_cell,
+                  pdx, pdy, gamma, o->wirelength, o->helmholtz_eps, gN, gN + m_mov, gW,
+                  gW + m_mov, NULL, NULL, NULL, NULL, &ev);
+        if (k == 0 && lambda <= 0.0) lambda = ev.gN_l1 > 0 ? ev.gW_l1 / ev.gN_l1 : 1.0;
+        if (k >= 1) lambda *= orc_mu(ev.hpwl - hp_prev, o->dw_ref);
+        hp_prev = ev.hpwl;
+        double fk = ev.W + lambda * ev.N;
+        double gg = 0.0, ggp = 0.0;
+        for (size_t i = 0; i < m2; ++i) {
+            g[i] = gW[i] + lambda * gN[i];
+            gg += g[i] * g[i];
+            if (k > 0) ggp += g[i] * gp[i];
+        }
+        double beta = (k > 0 && gg_prev > 0.0) ? dmax(0.0, (gg - ggp) / gg_prev) : 0.0;
+        double gd = 0.0, dinf = 0.0;
+        for (size_t i = 0; i < m2; ++i) {
+            d[i] = -g[i] + beta * (k > 0 ? d[i] : 0.0);
+            gd += g[i] * d[i];
+        }
+        if (!(gd < 0.0)) {   /* not a descent direction: restart */
+            gd = 0.0;
+            for (size_t i = 0; i < m2; ++i) { d[i] = -g[i]; gd -= g[i] * g[i]; }
+        }
+        for (size_t i = 0; i < m2; ++i) dinf = dmax(dinf, fabs(d[i]));
+        double alpha = 0.0;
+        if (dinf > 0.0) {
+            double slope = gd / dinf;
+            for (int i = 0; i < m_mov; ++i) {
+                xf[i] = (float)dmin(hi[i], dmax(lo[i], u[i] + alpha_max * d[i] / dinf));
+                yf[i] = (float)dmin(hi[m_mov + i],
+                                    dmax(lo[m_mov + i], u[m_mov + i] + alpha_max * d[m_mov + i] / dinf));
+            }
+            orc_eval_out et;
+            orc_eval2(R, n, rho_t, m_mov, xf, yf, w, h, m_fix, fx, fy, fw, fh, E, net_ptr,
+                      pin_cell, pdx, pdy, gamma, o->wirelength, o->helmholtz_eps, gp, gp + m_mov,
+                      gp, gp + m_mov, NULL, NULL, NULL, NULL, &et);
+            double ft = et.W + lambda * et.N;
+            double c = (ft - fk - slope * alpha_max) / (alpha_max * alpha_max);
+            double as = c > 0.0 ? -slope / (2.0 * c) : alpha_max;
+            alpha = dmin(alpha_max, dmax(0.01 * alpha_max, as));
+            for (size_t i = 0; i < m2; ++i)
+                u[i] = dmin(hi[i], dmax(lo[i], u[i] + alpha * d[i] / dinf));
+        }
+        for (size_t i = 0; i < m2; ++i) gp[i] = g[i];
+        gg_prev = gg;
+        if (recs) {
+            recs[k].W = ev.W; recs[k].hpwl = ev.hpwl; recs[k].N = ev.N; recs[k].tau = ev.tau;
+            recs[k].lambda = lambda; recs[k].gamma = gamma; recs[k].alpha = alpha;
+            recs[k].step_max = alpha;
+        }
+        alpha_max = dmax(alpha_max0, 2.0 * alpha);
+        if (o->gamma_fixed <= 0.0) gamma = orc_gamma(ev.tau, wb);
+        if (o->stop_on_tau && ev.tau <= o->tau_stop) { ++k; break; }
+    }
+    for (int i = 0; i < m_mov; ++i) { x[i] = (float)u[i]; y[i] = (float)u[m_mov + i]; }
+    free(u); free(d); free(g); free(gp); free(gN); free(gW); free(lo); free(hi);
+    free(xf); free(yf);
+    return k;
+}
