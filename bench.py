@@ -316,6 +316,36 @@ def run_variants(args, inst, x, y, g, flush, stream):
     return out
 
 
+def run_optimizers(args, x_inst):
+    """Convergence of the two loop steps (Nesterov, and Algorithm 1's CG) on
+    the 210K-cell and 2.2M-cell instances: iterations to tau <= 0.1 (at most
+    1000), final HPWL, and time per iteration."""
+    import time as _time
+
+    import torch
+
+    import synth
+    from paper_1312_4587_gb300 import fftpl as F
+    out = {}
+    for inst in (synth.make_instance("large"), x_inst):
+        x0 = torch.from_numpy(inst.x).cuda()
+        y0 = torch.from_numpy(inst.y).cuda()
+        res = {}
+        for name, opt in (("nesterov", F.FFTPL_OPT_NESTEROV), ("cg", F.FFTPL_OPT_CG)):
+            with F.Problem(inst, optimizer=opt, stop_on_tau=1) as p:
+                F.fftpl_place_init(p.h, x0, y0)
+                torch.cuda.synchronize()
+                t0 = _time.perf_counter()
+                rows, ran = F.fftpl_step(p.h, 1000)
+                dt = _time.perf_counter() - t0
+                F.fftpl_check(p.h)
+            res[name] = {"iterations": ran, "tau": round(rows[-1]["tau"], 4),
+                         "hpwl": round(rows[-1]["hpwl"], 1), "seconds": round(dt, 4),
+                         "ms_per_iteration": round(1000.0 * dt / max(ran, 1), 4)}
+        out[inst.name] = res
+    return out
+
+
 def cpu_baseline_sample(inst):
     """The oracle as it stands, one evaluation of the same instance."""
     import oracle
@@ -433,6 +463,8 @@ def run_ours(args, ws, rank, local):
                             "unit": "GB/s", "frac": st["frac"],
                             "traffic": stage_traffic(dom, args.workload),
                             "algorithmic_bytes": st["bytes"], "peak_kind": peak_kind}
+    if rank == 0 and ws == 1 and not args.no_optimizers:
+        line["optimizers"] = run_optimizers(args, inst)
     if not args.no_variants:
         line["variants"] = run_variants(args, inst, x, y, g, flush, stream)
     if not args.no_tc_path and n >= F.FFTPL_TC_MIN_N:
@@ -456,6 +488,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-optimizers", action="store_true",
+                    help="skip the Nesterov / CG convergence comparison")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the LSE / Helmholtz variant timings")
     ap.add_argument("--no-tc-path", action="store_true",

@@ -10,9 +10,10 @@
  * with W~ the weighted-average wirelength (Eq. 3) and N the electrostatic
  * potential energy (Eq. 6) of the bin density rho.  The potential psi and the
  * field E solve Poisson's equation with Neumann boundary (Eq. 8) through the
- * cosine/sine series of Eqs. 9-12.  fftpl_step runs Algorithm 1's loop with a
- * Nesterov step in place of the conjugate-gradient solver and the parameter
- * control of Section IV-A.
+ * cosine/sine series of Eqs. 9-12.  fftpl_step runs Algorithm 1's loop with
+ * the parameter control of Section IV-A and either the paper's
+ * conjugate-gradient step or Nesterov's method (fftpl_options.optimizer);
+ * LSE wirelength and the Helmholtz smoothing of Eq. 4 are model options.
  *
  * Conventions (they define the results; the oracle used by the tests states
  * the same):
@@ -132,6 +133,17 @@ enum {
  * softmax(p/g) - softmax(-p/g). */
 enum { FFTPL_WL_WA = 0, FFTPL_WL_LSE = 1 };
 
+/* Placement-loop step (fftpl_step).  FFTPL_OPT_NESTEROV: Nesterov's method
+ * with the step alpha_k = |v_k - v_{k-1}| / |g_k - g_{k-1}| kept in the
+ * interval [0.01 alpha_max, alpha_max] of Section IV-A.  FFTPL_OPT_CG: the
+ * nonlinear conjugate-gradient step of Algorithm 1 (Polak-Ribiere+
+ * direction d, restarted to -g when not a descent direction; the step a is
+ * the farthest cell move, x + a d / |d|_inf, chosen in the same interval by
+ * one quadratic fit through f(x), the slope and a trial evaluation at
+ * alpha_max; then alpha_max = max(alpha_max_0, 2 a)).  One CG iteration
+ * costs two evaluations. */
+enum { FFTPL_OPT_NESTEROV = 0, FFTPL_OPT_CG = 1 };
+
 typedef struct {
     double target_density;  /* rho_t (Section III-B, Section V: 1.0) */
     int32_t solve_path;     /* FFTPL_SOLVE_* */
@@ -149,7 +161,7 @@ typedef struct {
     int32_t use_graphs;     /* 1: replay captured CUDA graphs for repeated
                                calls with the same buffers */
     int32_t wirelength;     /* FFTPL_WL_WA (default) or FFTPL_WL_LSE */
-    int32_t reserved0;
+    int32_t optimizer;      /* FFTPL_OPT_NESTEROV (default) or FFTPL_OPT_CG */
     double helmholtz_eps;   /* 0: the Poisson equation of Eq. 8 (the (0,0)
                                mode dropped); > 0: the Helmholtz smoothing of
                                Eq. 4, laplacian psi - eps psi = -rho: every
@@ -276,12 +288,15 @@ fftpl_status fftpl_bin_ranges(fftpl_t h, const float* x, const float* y, int32_t
 /* ------------------------------------------------------ placement loop */
 
 /* Starts a placement run at (x0, y0) (device, m_mov): u = v = clamp(x0),
- * Nesterov a = 1, lambda, gamma and alpha_max from the options. */
+ * Nesterov a = 1 / no CG direction yet, lambda, gamma and alpha_max from the
+ * options. */
 fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0);
 
-/* Runs up to iters iterations of the loop (Algorithm 1 with the Nesterov
- * step; Section IV-A control).  recs: host array of iters records (may be
- * NULL).  *ran: iterations done (host).  Synchronises at the end only. */
+/* Runs up to iters iterations of the loop (Algorithm 1 with the step of
+ * fftpl_options.optimizer; Section IV-A control).  recs: host array of iters
+ * records (may be NULL).  *ran: iterations done (host).  Synchronises at the
+ * end, and with stop_on_tau also every 16 iterations to stop enqueuing once
+ * the device has met the stop test. */
 fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32_t* ran);
 
 /* Copies the current major iterate u to device arrays x, y (m_mov). */

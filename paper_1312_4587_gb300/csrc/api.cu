@@ -164,6 +164,8 @@ fftpl_status validate(Ctx& c, const fftpl_region* R, int n, const fftpl_cells* c
         if (!(opt->dw_ref > 0.0)) return set_err(c, FFTPL_EINVAL, "dw_ref must be > 0");
         if (opt->wirelength != FFTPL_WL_WA && opt->wirelength != FFTPL_WL_LSE)
             return set_err(c, FFTPL_EINVAL, "unknown wirelength model");
+        if (opt->optimizer != FFTPL_OPT_NESTEROV && opt->optimizer != FFTPL_OPT_CG)
+            return set_err(c, FFTPL_EINVAL, "unknown optimizer");
         if (!(opt->helmholtz_eps >= 0.0) || !isfinite(opt->helmholtz_eps))
             return set_err(c, FFTPL_EINVAL, "helmholtz_eps must be finite and >= 0");
     }
@@ -328,6 +330,7 @@ void fftpl_default_options(fftpl_options* o) {
     o->stop_on_tau = 0;
     o->use_graphs = 0;
     o->wirelength = FFTPL_WL_WA;
+    o->optimizer = FFTPL_OPT_NESTEROV;
     o->helmholtz_eps = 0.0;
 }
 
@@ -921,7 +924,10 @@ fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
 }
 
 extern "C++" {
-fftpl_status fftpl::loop_enqueue(Ctx& c) {
+// One evaluation of the loop at the positions in c.v (gamma from the
+// control scalars): zero the sums, density chain, WA branch, join; with
+// `cells` also the per-cell gradients and lambda_k.
+static fftpl_status loop_eval(Ctx& c, bool cells) {
     cudaStream_t s = c.stream;
     size_t nn = (size_t)c.n * c.n;
     const float* vx = c.v;
@@ -945,12 +951,32 @@ fftpl_status fftpl::loop_enqueue(Ctx& c) {
     CK(cudaEventRecord(c.ev_join, c.side));
     TRY(enqueue_solve(c, s));
     CK(cudaStreamWaitEvent(s, c.ev_join, 0));
-    { Stage st(c, 5, s); CK(launch_loop_cells(c, s)); }
-    {
-        Stage st(c, 6, s);
-        CK(launch_loop_g(c, s));
-        CK(launch_loop_update(c, s));
+    if (cells) {
+        Stage st(c, 5, s);
+        CK(launch_loop_cells(c, s));
     }
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl::loop_enqueue(Ctx& c) {
+    cudaStream_t s = c.stream;
+    TRY(loop_eval(c, true));
+    if (c.opt.optimizer == FFTPL_OPT_CG) {
+        {
+            Stage st(c, 6, s);
+            CK(launch_cg_g(c, s));
+            CK(launch_cg_dir(c, s));
+            CK(launch_cg_trial(c, s));
+        }
+        TRY(loop_eval(c, false));   // f at the trial point
+        Stage st(c, 6, s);
+        CK(launch_cg_alpha(c, s));
+        CK(launch_cg_update(c, s));
+        return FFTPL_OK;
+    }
+    Stage st(c, 6, s);
+    CK(launch_loop_g(c, s));
+    CK(launch_loop_update(c, s));
     return FFTPL_OK;
 }
 
@@ -981,7 +1007,20 @@ fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32
     CK(cudaMemcpyAsync(&k0, c.ctrl + C_K, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
     TRY(loop_records(c, iters, k0));
-    for (int it = 0; it < iters; ++it) TRY(loop_enqueue(c));
+    // with the stop test on, enqueue in chunks and look at the device's
+    // stop flag between them, so that a run that stops early does not keep
+    // its remaining iterations' kernels in the queue
+    constexpr int kChunk = 16;
+    for (int it = 0; it < iters; it += kChunk) {
+        for (int j = it; j < std::min(iters, it + kChunk); ++j) TRY(loop_enqueue(c));
+        if (c.opt.stop_on_tau && it + kChunk < iters) {
+            double done = 0.0;
+            CK(cudaMemcpyAsync(&done, c.ctrl + C_DONE, sizeof(double), cudaMemcpyDeviceToHost,
+                               c.stream));
+            CK(cudaStreamSynchronize(c.stream));
+            if (done != 0.0) break;
+        }
+    }
     double k1 = 0.0;
     CK(cudaMemcpyAsync(&k1, c.ctrl + C_K, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));

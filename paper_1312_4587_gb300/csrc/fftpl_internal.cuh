@@ -46,6 +46,8 @@ enum {
     ACC_DG2,        // ||g_k - g_{k-1}||^2
     ACC_GINF,       // ||g_k||_inf (as ordered bits of a non-negative double)
     ACC_STEPMAX,    // max |u_{k+1} - v_k|
+    ACC_GD,         // g_k . d_k (conjugate-gradient loop)
+    ACC_DINF,       // ||d_k||_inf (conjugate-gradient loop)
     ACC_COUNT
 };
 
@@ -498,6 +500,12 @@ cudaError_t launch_loop_g(Ctx& c, cudaStream_t s);
 cudaError_t launch_loop_update(Ctx& c, cudaStream_t s);
 cudaError_t launch_place_init(Ctx& c, const float* x0, const float* y0, cudaStream_t s);
 cudaError_t launch_gamma0(Ctx& c, cudaStream_t s);
+// conjugate-gradient loop (k_step.cu)
+cudaError_t launch_cg_g(Ctx& c, cudaStream_t s);
+cudaError_t launch_cg_dir(Ctx& c, cudaStream_t s);
+cudaError_t launch_cg_trial(Ctx& c, cudaStream_t s);
+cudaError_t launch_cg_alpha(Ctx& c, cudaStream_t s);
+cudaError_t launch_cg_update(Ctx& c, cudaStream_t s);
 
 }  // namespace fftpl
 

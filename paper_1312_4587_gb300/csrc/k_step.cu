@@ -1,7 +1,7 @@
 // Placement loop kernels: the per-cell gradient with the lambda update, the
 // combined gradient g = grad W~ + lambda grad N with the step-size sums, and
-// the Nesterov position update (Algorithm 1 with Nesterov's method in place of
-// the conjugate-gradient solver; control of Section IV-A in loop_ctrl.cuh).
+// the position update, either Nesterov's method or Algorithm 1's
+// conjugate-gradient step (control of Section IV-A in loop_ctrl.cuh).
 //
 // Vectors hold x coordinates in [0, m) and y coordinates in [m, 2m).
 #include "loop_ctrl.cuh"
@@ -99,6 +99,101 @@ k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
     if (last_cta(b.counters + 2) && threadIdx.x == 0) ctrl_record(b.ctrl, b.acc, b.recs);
 }
 
+// ------------------------------------------------ conjugate-gradient loop
+// The direction d_k lives in the Nesterov loop's vprev buffer (unused here);
+// u holds x_k and v the point being evaluated (x_k, then the trial point).
+
+// g = gW + lambda gN; sums |g|^2 and g . g_prev, max |g|; last CTA: beta,
+// f_k and the values recorded for iteration k.
+__global__ void __launch_bounds__(kCellThreads) k_cg_g(int m2, LoopBufs b) {
+    if (b.ctrl[C_DONE] != 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float lam = (float)b.ctrl[C_LAMBDA];
+    const bool first = b.ctrl[C_K] == 0.0;
+    float sq = 0.0f, gp = 0.0f, gi = 0.0f;
+    if (i < m2) {
+        float gg = fmaf(lam, b.gN[i], b.gW[i]);
+        b.g[i] = gg;
+        sq = gg * gg;
+        gp = first ? 0.0f : gg * b.gprev[i];
+        gi = fabsf(gg);
+    }
+    reduce2(sq, gp, b.acc, ACC_DG2, ACC_DV2, b.dr);
+    block_max(gi, b.acc, ACC_GINF);
+    if (last_cta(b.counters + 3) && threadIdx.x == 0) ctrl_cg_g(b.ctrl, b.acc);
+}
+
+// d = -g + beta d; sum g . d and max |d|; last CTA: restart test, |d|_inf
+// and the slope.
+__global__ void __launch_bounds__(kCellThreads) k_cg_dir(int m2, LoopBufs b) {
+    if (b.ctrl[C_DONE] != 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float beta = (float)b.ctrl[C_BETA];
+    const bool first = b.ctrl[C_K] == 0.0;
+    float gd = 0.0f, da = 0.0f;
+    if (i < m2) {
+        float gi = b.g[i];
+        float dn = first ? -gi : fmaf(beta, b.vprev[i], -gi);
+        b.vprev[i] = dn;
+        gd = gi * dn;
+        da = fabsf(dn);
+    }
+    reduce2(gd, 0.0f, b.acc, ACC_GD, -1, b.dr);
+    block_max(da, b.acc, ACC_DINF);
+    if (last_cta(b.counters + 4) && threadIdx.x == 0) ctrl_cg_dir(b.ctrl, b.acc);
+}
+
+// per coordinate i < 2m: the direction (d, or -g after a restart) and the
+// clamp bounds of the cell inside the region
+__device__ __forceinline__ void cg_coord(int i, int m, const Grid& gr, float x1, float y1,
+                                         const LoopBufs& b, float& dir, float& lo, float& hi) {
+    const bool isx = i < m;
+    const int c = isx ? i : i - m;
+    const float half = __fmul_rn(0.5f, isx ? b.w[c] : b.h[c]);
+    lo = __fadd_rn(isx ? gr.x0 : gr.y0, half);
+    hi = __fsub_rn(isx ? x1 : y1, half);
+    dir = b.ctrl[C_RESTART] != 0.0 ? -b.g[i] : b.vprev[i];
+}
+
+// trial point v = clamp(u + a_max dir / |d|_inf)
+__global__ void __launch_bounds__(kCellThreads)
+k_cg_trial(int m, Grid gr, float x1, float y1, LoopBufs b) {
+    if (b.ctrl[C_DONE] != 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * m) return;
+    const double dinf = b.ctrl[C_DINF];
+    const float scale = dinf > 0.0 ? (float)(b.ctrl[C_ALPHA_MAX] / dinf) : 0.0f;
+    float dir, lo, hi;
+    cg_coord(i, m, gr, x1, y1, b, dir, lo, hi);
+    b.v[i] = fminf(hi, fmaxf(lo, fmaf(scale, dir, b.u[i])));
+}
+
+// the step from the trial evaluation (one thread)
+__global__ void k_cg_alpha(double* ctrl, const double* acc) {
+    if (ctrl[C_DONE] != 0.0) return;
+    ctrl_cg_alpha(ctrl, acc);
+}
+
+// u = v = clamp(u + a_k dir / |d|_inf); d = dir; g_prev = g.  Last CTA:
+// record and advance.
+__global__ void __launch_bounds__(kCellThreads)
+k_cg_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
+    if (b.ctrl[C_DONE] != 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 2 * m) {
+        const double dinf = b.ctrl[C_DINF];
+        const float scale = dinf > 0.0 ? (float)(b.ctrl[C_ALPHA] / dinf) : 0.0f;
+        float dir, lo, hi;
+        cg_coord(i, m, gr, x1, y1, b, dir, lo, hi);
+        const float un = fminf(hi, fmaxf(lo, fmaf(scale, dir, b.u[i])));
+        b.u[i] = un;
+        b.v[i] = un;
+        b.vprev[i] = dir;
+        b.gprev[i] = b.g[i];
+    }
+    if (last_cta(b.counters + 5) && threadIdx.x == 0) ctrl_record_cg(b.ctrl, b.recs);
+}
+
 // u = v = clamp(x0, y0); previous vectors zeroed.
 __global__ void k_place_init(int m, Grid gr, float x1, float y1, const float* __restrict__ x0,
                              const float* __restrict__ y0, LoopBufs b) {
@@ -164,6 +259,38 @@ cudaError_t launch_loop_update(Ctx& c, cudaStream_t s) {
 cudaError_t launch_place_init(Ctx& c, const float* x0, const float* y0, cudaStream_t s) {
     k_place_init<<<nblk(2LL * c.m_mov, 256), 256, 0, s>>>(c.m_mov, c.grid, (float)c.x1,
                                                          (float)c.y1, x0, y0, loop_bufs(c));
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_g(Ctx& c, cudaStream_t s) {
+    k_cg_g<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_dir(Ctx& c, cudaStream_t s) {
+    k_cg_dir<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_trial(Ctx& c, cudaStream_t s) {
+    k_cg_trial<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
+        c.m_mov, c.grid, (float)c.x1, (float)c.y1, loop_bufs(c));
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_alpha(Ctx& c, cudaStream_t s) {
+    k_cg_alpha<<<1, 1, 0, s>>>(c.ctrl, c.acc);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(Ctx& c, cudaStream_t s) {
+    k_cg_update<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
+        c.m_mov, c.grid, (float)c.x1, (float)c.y1, loop_bufs(c));
     c.launches++;
     return cudaGetLastError();
 }

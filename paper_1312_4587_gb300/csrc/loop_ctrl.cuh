@@ -13,6 +13,9 @@ enum {
     C_LAMBDA = 0, C_GAMMA, C_ALPHA, C_ALPHA_MAX, C_A, C_BETA, C_HP_PREV, C_K, C_DONE, C_A_NEXT,
     C_ALPHA_MAX0, C_DW_REF, C_GAMMA_FIXED, C_LAMBDA0_OPT, C_STOP_ON_TAU, C_TAU_STOP, C_WB,
     C_HALF_AB, C_MOV_AREA, C_REC_CAP, C_REC_BASE,
+    // conjugate-gradient loop: |g_{k-1}|^2, f_k, slope along d/|d|_inf,
+    // |d|_inf, restart flag, and the values recorded for iteration k
+    C_GG_PREV, C_FK, C_SLOPE, C_DINF, C_RESTART, C_W_K, C_HP_K, C_N_K, C_TAU_K,
     C_COUNT
 };
 constexpr int kRecFields = 8;
@@ -114,6 +117,77 @@ __device__ __forceinline__ void ctrl_record(double* ctrl, const double* acc, dou
     }
     ctrl[C_A] = ctrl[C_A_NEXT];
     ctrl[C_ALPHA_MAX] = fmax(ctrl[C_ALPHA_MAX0], 2.0 * step_max);
+    if (ctrl[C_GAMMA_FIXED] <= 0.0) ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
+    ctrl[C_K] = (double)(k + 1);
+    if (ctrl[C_STOP_ON_TAU] != 0.0 && tau <= ctrl[C_TAU_STOP]) ctrl[C_DONE] = 1.0;
+}
+
+// ------------------------------------------------ conjugate-gradient loop
+// Algorithm 1's CGsolver with the search interval [0.01 a_max, a_max] of
+// Section IV-A: Polak-Ribiere+ directions, the step measured as the farthest
+// cell move (direction scaled by 1/|d|_inf), one quadratic-fit line search
+// from f_k, the slope and one trial evaluation at a_max.
+
+// After g_k: beta_k (PR+), f_k and the values recorded for iteration k.
+__device__ __forceinline__ void ctrl_cg_g(double* ctrl, const double* acc) {
+    int k = (int)ctrl[C_K];
+    double gg = acc_sum(acc, ACC_DG2), ggp = acc_sum(acc, ACC_DV2);
+    double prev = ctrl[C_GG_PREV];
+    ctrl[C_BETA] = (k > 0 && prev > 0.0) ? fmax(0.0, (gg - ggp) / prev) : 0.0;
+    ctrl[C_GG_PREV] = gg;
+    double W = acc_sum(acc, ACC_W), N = acc_sum(acc, ACC_N) * ctrl[C_HALF_AB];
+    ctrl[C_FK] = W + ctrl[C_LAMBDA] * N;
+    ctrl[C_W_K] = W;
+    ctrl[C_HP_K] = acc_sum(acc, ACC_HPWL);
+    ctrl[C_N_K] = N;
+    ctrl[C_TAU_K] = acc_sum(acc, ACC_TAU) / ctrl[C_MOV_AREA];
+}
+
+// After d_k: restart to -g_k unless g_k . d_k < 0; |d|_inf and the slope.
+__device__ __forceinline__ void ctrl_cg_dir(double* ctrl, const double* acc) {
+    double gd = acc_sum(acc, ACC_GD), dinf = acc_max(acc, ACC_DINF);
+    bool restart = !(gd < 0.0);
+    if (restart) {
+        dinf = acc_max(acc, ACC_GINF);
+        gd = -ctrl[C_GG_PREV];
+    }
+    ctrl[C_RESTART] = restart ? 1.0 : 0.0;
+    ctrl[C_DINF] = dinf;
+    ctrl[C_SLOPE] = dinf > 0.0 ? gd / dinf : 0.0;
+}
+
+// After the trial evaluation at a_max: the step a_k from the parabola
+// through f_k (slope s) and f_t, kept in [0.01 a_max, a_max].
+__device__ __forceinline__ void ctrl_cg_alpha(double* ctrl, const double* acc) {
+    double amax = ctrl[C_ALPHA_MAX], alpha = 0.0;
+    if (ctrl[C_DINF] > 0.0) {
+        double ft = acc_sum(acc, ACC_W) + ctrl[C_LAMBDA] * acc_sum(acc, ACC_N) * ctrl[C_HALF_AB];
+        double s = ctrl[C_SLOPE];
+        double c = (ft - ctrl[C_FK] - s * amax) / (amax * amax);
+        double as = c > 0.0 ? -s / (2.0 * c) : amax;
+        alpha = fmin(amax, fmax(0.01 * amax, as));
+    }
+    ctrl[C_ALPHA] = alpha;
+}
+
+// After the position update: record iteration k, then a_max_{k+1} =
+// max(a_max_0, 2 a_k), gamma_{k+1}, k+1 and the stop test.
+__device__ __forceinline__ void ctrl_record_cg(double* ctrl, double* recs) {
+    int k = (int)ctrl[C_K];
+    double tau = ctrl[C_TAU_K], alpha = ctrl[C_ALPHA];
+    int slot = k - (int)ctrl[C_REC_BASE];
+    if (slot >= 0 && slot < (int)ctrl[C_REC_CAP]) {
+        double* r = recs + (size_t)slot * kRecFields;
+        r[0] = ctrl[C_W_K];
+        r[1] = ctrl[C_HP_K];
+        r[2] = ctrl[C_N_K];
+        r[3] = tau;
+        r[4] = ctrl[C_LAMBDA];
+        r[5] = ctrl[C_GAMMA];
+        r[6] = alpha;
+        r[7] = alpha;
+    }
+    ctrl[C_ALPHA_MAX] = fmax(ctrl[C_ALPHA_MAX0], 2.0 * alpha);
     if (ctrl[C_GAMMA_FIXED] <= 0.0) ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
     ctrl[C_K] = (double)(k + 1);
     if (ctrl[C_STOP_ON_TAU] != 0.0 && tau <= ctrl[C_TAU_STOP]) ctrl[C_DONE] = 1.0;

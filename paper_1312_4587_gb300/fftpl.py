@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "FFTPL_OK", 1: "FFTPL_EINVAL", 2: "FFTPL_ENOMEM", 3: "FFTPL_E
 FFTPL_SOLVE_FFT, FFTPL_SOLVE_TC_BF16X3 = 0, 1
 FFTPL_TC_MIN_N = 128
 FFTPL_WL_WA, FFTPL_WL_LSE = 0, 1
+FFTPL_OPT_NESTEROV, FFTPL_OPT_CG = 0, 1
 FFTPL_NUM_STAGES = 8
 STAGES = ["scatter", "rows_fwd", "cols", "rows_inv", "wa", "cells", "step", "reserved"]
 
@@ -61,7 +62,7 @@ class fftpl_options(C.Structure):
                 ("gamma_fixed", C.c_double), ("dw_ref", C.c_double),
                 ("alpha_max0_bins", C.c_double), ("tau_stop", C.c_double),
                 ("stop_on_tau", C.c_int32), ("use_graphs", C.c_int32),
-                ("wirelength", C.c_int32), ("reserved0", C.c_int32),
+                ("wirelength", C.c_int32), ("optimizer", C.c_int32),
                 ("helmholtz_eps", C.c_double), ("reserved", C.c_int32 * 2)]
 
 
