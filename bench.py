@@ -346,6 +346,38 @@ def run_optimizers(args, x_inst):
     return out
 
 
+def run_fillers(args, inst, flush, stream):
+    """The same step on the instance extended by the filler rule's cells
+    (Section III-B): the cost of the extra pin-less movable cells."""
+    import torch
+
+    import synth
+    from paper_1312_4587_gb300 import fftpl as F
+    cnt, fw, fh = F.fftpl_fillers(inst.region, inst.w, inst.h, inst.m_mov, inst.fix_x,
+                                  inst.fix_y, inst.target_density)
+    ext = synth.with_fillers(inst, cnt, fw, fh)
+    x = torch.from_numpy(ext.x).cuda()
+    y = torch.from_numpy(ext.y).cuda()
+    g = [torch.empty_like(x) for _ in range(4)]
+    prob = F.Problem(ext, use_graphs=0 if args.no_graphs else 1)
+    for _ in range(max(3, args.warmup)):
+        F.fftpl_eval(prob.h, x, y, ext.gamma, *g, sync=False)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        F.fftpl_eval(prob.h, x, y, ext.gamma, *g, sync=False)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    F.fftpl_check(prob.h)
+    prob.close()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    return {"fillers": cnt, "filler_size": [fw, fh], "cells": ext.m_mov,
+            "value": round(1000.0 / ms, 2), "unit": UNIT, "ms_per_step": round(ms, 5)}
+
+
 def cpu_baseline_sample(inst):
     """The oracle as it stands, one evaluation of the same instance."""
     import oracle
@@ -467,6 +499,7 @@ def run_ours(args, ws, rank, local):
         line["optimizers"] = run_optimizers(args, inst)
     if not args.no_variants:
         line["variants"] = run_variants(args, inst, x, y, g, flush, stream)
+        line["variants"]["fillers"] = run_fillers(args, inst, flush, stream)
     if not args.no_tc_path and n >= F.FFTPL_TC_MIN_N:
         line["tc_path"] = run_tc_path(args, inst, x, y, g, flush, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -285,6 +285,21 @@ fftpl_status fftpl_fields_q(fftpl_t h, const int64_t** movable_area_q);
 fftpl_status fftpl_bin_ranges(fftpl_t h, const float* x, const float* y, int32_t* ranges,
                               int64_t* pairs);
 
+/* Filler cells (Section III-B: disconnected movable cells that take up the
+ * free area).  The paper gives no count or size; this library's rule: the
+ * fillers' total area is target_density times the free area of the region
+ * (its area minus the fixed cells' overlap with it) minus the movable area;
+ * each filler has the mean movable width and height (float32); *count is
+ * that area over one filler's, rounded down, 0 when the movable cells
+ * already fill it.  Host only (no device work, no handle): the caller
+ * appends the fillers as pin-less movable cells (any start positions) to the
+ * cells it passes to fftpl_create.  Dark nodes (non-placeable rectangles)
+ * are fixed cells.  cells: as for fftpl_create (host arrays).  FFTPL_EINVAL
+ * for null arguments or sizes that are not finite and > 0. */
+fftpl_status fftpl_fillers(const fftpl_region* region, const fftpl_cells* cells,
+                           double target_density, int64_t* count, float* filler_w,
+                           float* filler_h);
+
 /* ------------------------------------------------------ placement loop */
 
 /* Starts a placement run at (x0, y0) (device, m_mov): u = v = clamp(x0),

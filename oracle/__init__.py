@@ -357,3 +357,19 @@ def _loop(fn, inst, iters, lambda0=0.0, gamma_fixed=None, dw_ref=3.5e5, alpha_ma
     rows = [dict(W=r.W, hpwl=r.hpwl, N=r.N, tau=r.tau, lam=r.lambda_, gamma=r.gamma,
                  alpha=r.alpha, step_max=r.step_max) for r in recs[:ran]]
     return x, y, rows, int(ran)
+
+
+def fillers(region, w, h, m_mov, fix_x=None, fix_y=None, target_density=1.0):
+    """Filler rule (Section III-B reading): (count, filler width, height)."""
+    w, h = _f32(w), _f32(h)
+    k = w.shape[0] - m_mov
+    fx = _f32(fix_x) if k else None
+    fy = _f32(fix_y) if k else None
+    fw = w[m_mov:] if k else None
+    fh = h[m_mov:] if k else None
+    cnt = C.c_int64(0); a = C.c_float(0.0); b = C.c_float(0.0)
+    R = _region(region)
+    lib().orc_fillers(C.byref(R), C.c_int(m_mov), _ptr(w), _ptr(h), C.c_int(k), _ptr(fx), _ptr(fy),
+                      _ptr(fw), _ptr(fh), C.c_double(target_density), C.byref(cnt), C.byref(a),
+                      C.byref(b))
+    return int(cnt.value), float(a.value), float(b.value)

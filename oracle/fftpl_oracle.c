@@ -937,3 +937,36 @@ int orc_cg(const orc_region* R, int n, double rho_t,
     free(xf); free(yf);
     return k;
 }
+
+/* Filler cells (Section III-B: disconnected movable cells that take up the
+ * free area the movable cells leave).  The paper gives no count or size;
+ * the reading: the fillers' total area is rho_t times the free area of the
+ * region (its area minus the fixed cells' overlap with it) minus the movable
+ * area, each filler has the mean movable width and height, and the count is
+ * that area over one filler's, rounded down (0 if the movable cells already
+ * fill rho_t of the free area).  Sizes are returned in float32, as the
+ * library stores them. */
+void orc_fillers(const orc_region* R, int m_mov, const float* w, const float* h,
+                 int m_fix, const float* fx, const float* fy, const float* fw, const float* fh,
+                 double rho_t, int64_t* count, float* filler_w, float* filler_h) {
+    double area = (R->x1 - R->x0) * (R->y1 - R->y0), fixed = 0.0, mov = 0.0, sw = 0.0, sh = 0.0;
+    for (int f = 0; f < m_fix; ++f) {
+        double ox = dmin(R->x1, (double)fx[f] + 0.5 * fw[f]) - dmax(R->x0, (double)fx[f] - 0.5 * fw[f]);
+        double oy = dmin(R->y1, (double)fy[f] + 0.5 * fh[f]) - dmax(R->y0, (double)fy[f] - 0.5 * fh[f]);
+        if (ox > 0.0 && oy > 0.0) fixed += ox * oy;
+    }
+    for (int i = 0; i < m_mov; ++i) {
+        mov += (double)w[i] * (double)h[i];
+        sw += w[i];
+        sh += h[i];
+    }
+    *count = 0;
+    *filler_w = 0.0f;
+    *filler_h = 0.0f;
+    if (m_mov <= 0) return;
+    float mw = (float)(sw / m_mov), mh = (float)(sh / m_mov);
+    double fill = rho_t * (area - fixed) - mov;
+    *filler_w = mw;
+    *filler_h = mh;
+    if (fill > 0.0) *count = (int64_t)floor(fill / ((double)mw * (double)mh));
+}

@@ -334,6 +334,48 @@ void fftpl_default_options(fftpl_options* o) {
     o->helmholtz_eps = 0.0;
 }
 
+fftpl_status fftpl_fillers(const fftpl_region* R, const fftpl_cells* cells,
+                           double target_density, int64_t* count, float* filler_w,
+                           float* filler_h) {
+    if (!R || !cells || !count || !filler_w || !filler_h || cells->m_mov < 0 ||
+        cells->m_fix < 0 || (cells->m_mov + cells->m_fix > 0 && (!cells->w || !cells->h)) ||
+        (cells->m_fix > 0 && (!cells->fix_x || !cells->fix_y)) ||
+        !(target_density > 0.0) || !std::isfinite(target_density)) {
+        set_global_error("fftpl_fillers: null or invalid argument");
+        return FFTPL_EINVAL;
+    }
+    const int m = cells->m_mov, k = cells->m_fix;
+    for (int i = 0; i < m + k; ++i)
+        if (!finite_pos(cells->w[i]) || !finite_pos(cells->h[i])) {
+            set_global_error("fftpl_fillers: cell sizes must be finite and > 0");
+            return FFTPL_EINVAL;
+        }
+    double area = (R->x1 - R->x0) * (R->y1 - R->y0), fixed = 0.0, mov = 0.0, sw = 0.0, sh = 0.0;
+    for (int f = 0; f < k; ++f) {
+        const double hw = 0.5 * cells->w[m + f], hh = 0.5 * cells->h[m + f];
+        const double ox = std::min(R->x1, (double)cells->fix_x[f] + hw) -
+                          std::max(R->x0, (double)cells->fix_x[f] - hw);
+        const double oy = std::min(R->y1, (double)cells->fix_y[f] + hh) -
+                          std::max(R->y0, (double)cells->fix_y[f] - hh);
+        if (ox > 0.0 && oy > 0.0) fixed += ox * oy;
+    }
+    for (int i = 0; i < m; ++i) {
+        mov += (double)cells->w[i] * (double)cells->h[i];
+        sw += cells->w[i];
+        sh += cells->h[i];
+    }
+    *count = 0;
+    *filler_w = 0.0f;
+    *filler_h = 0.0f;
+    if (m <= 0) return FFTPL_OK;
+    const float mw = (float)(sw / m), mh = (float)(sh / m);
+    const double fill = target_density * (area - fixed) - mov;
+    *filler_w = mw;
+    *filler_h = mh;
+    if (fill > 0.0) *count = (int64_t)std::floor(fill / ((double)mw * (double)mh));
+    return FFTPL_OK;
+}
+
 void fftpl_debug_fail_alloc_after(int32_t k) { g_fail_after.store(k > 0 ? k : 0); }
 
 fftpl_status fftpl_debug_tc_gemm(const void* a_hi, const void* a_lo, const void* b_hi,

@@ -156,6 +156,7 @@ def lib():
             "fftpl_stage_times": (S, [_H, _P, _P, C.c_int32]),
             "fftpl_launch_count": (C.c_int64, [_H]),
             "fftpl_debug_fail_alloc_after": (None, [C.c_int32]),
+            "fftpl_fillers": (S, [_P, _P, C.c_double, _P, _P, _P]),
             "fftpl_debug_tc_gemm": (S, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P,
                                         C.c_int32, C.c_int32, _P, _P]),
             "fftpl_solve_noalloc": (S, [_P, C.c_int32, C.c_double, C.c_double, _P, _P, _P, _P, _P]),
@@ -486,6 +487,21 @@ def fftpl_server_report(s):
 
 def fftpl_server_set_clock(s, now_s):
     _check(lib().fftpl_server_set_clock(s, C.c_double(float(now_s))), None)
+
+
+def fftpl_fillers(region, w, h, m_mov, fix_x=None, fix_y=None, target_density=1.0):
+    """Filler count and size for an instance (host arrays): (count, w, h)."""
+    w = np.ascontiguousarray(w, np.float32)
+    h = np.ascontiguousarray(h, np.float32)
+    m_fix = int(w.shape[0]) - int(m_mov)
+    fx = np.ascontiguousarray(fix_x if fix_x is not None else np.zeros(0), np.float32)
+    fy = np.ascontiguousarray(fix_y if fix_y is not None else np.zeros(0), np.float32)
+    R = fftpl_region(*[float(v) for v in region])
+    cells = fftpl_cells(int(m_mov), m_fix, _hptr(w, 0), _hptr(h, 0), _hptr(fx, 0), _hptr(fy, 0))
+    cnt = C.c_int64(0); a = C.c_float(0.0); b = C.c_float(0.0)
+    _check(lib().fftpl_fillers(C.byref(R), C.byref(cells), C.c_double(target_density),
+                               C.byref(cnt), C.byref(a), C.byref(b)), None)
+    return int(cnt.value), float(a.value), float(b.value)
 
 
 def fftpl_debug_fail_alloc_after(k):

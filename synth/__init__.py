@@ -324,3 +324,29 @@ def random_cells(rng: np.random.Generator, m: int, region, wmax: float = 6.0,
     w = rng.uniform(0.05, wmax, size=m).astype(np.float32)
     h = rng.uniform(0.05, hmax, size=m).astype(np.float32)
     return x, y, w, h
+
+
+def with_fillers(inst: Instance, count: int, filler_w: float, filler_h: float,
+                 seed: int | None = None) -> Instance:
+    """A copy of inst with `count` pin-less movable cells of size
+    filler_w x filler_h appended after the movable cells, at seeded uniform
+    positions inside the region (the count and size come from the caller).
+    Fixed-cell pin indices shift by count."""
+    rng = np.random.default_rng(1312 + 7919 if seed is None else seed)
+    x0, y0, x1, y1 = inst.region
+    m = inst.m_mov
+    fw = np.full(count, filler_w, np.float32)
+    fh = np.full(count, filler_h, np.float32)
+    fxs = rng.uniform(x0 + 0.5 * filler_w, x1 - 0.5 * filler_w, count).astype(np.float32)
+    fys = rng.uniform(y0 + 0.5 * filler_h, y1 - 0.5 * filler_h, count).astype(np.float32)
+    pc = inst.pin_cell.astype(np.int64)
+    pc = np.where(pc >= m, pc + count, pc).astype(np.int32)
+    return Instance(name=inst.name + "+fillers", region=inst.region, n=inst.n,
+                    target_density=inst.target_density, gamma=inst.gamma,
+                    m_mov=m + count, m_fix=inst.m_fix,
+                    w=np.concatenate([inst.w[:m], fw, inst.w[m:]]),
+                    h=np.concatenate([inst.h[:m], fh, inst.h[m:]]),
+                    fix_x=inst.fix_x, fix_y=inst.fix_y, net_ptr=inst.net_ptr, pin_cell=pc,
+                    pin_dx=inst.pin_dx, pin_dy=inst.pin_dy,
+                    x=np.concatenate([inst.x, fxs]), y=np.concatenate([inst.y, fys]),
+                    seed=inst.seed, extra=dict(inst.extra, fillers=count))
