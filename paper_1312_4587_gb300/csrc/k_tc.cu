@@ -33,9 +33,14 @@
 namespace fftpl {
 namespace tc {
 
+// k-step of 64 bf16 (one 128-byte swizzle row), a 3-stage ring of 192 KiB,
+// one CTA per SM.  (BK = 32 runs two 96 KiB CTAs per SM with the 64-byte
+// swizzle: measured no faster at 2048^3 and slower at 4096^3.)
 constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int kSwz = BK * 2;                   // swizzle span in bytes (64 or 128)
+constexpr int kMinBlocks = BK == 32 ? 2 : 1;   // CTAs per SM the launch bounds ask for
 constexpr int kStages = 3;
-constexpr int kTileBytes = BM * BK * 2;        // 16 KiB of bf16
+constexpr int kTileBytes = BM * BK * 2;        // bf16 tile of one operand half
 constexpr int kStageBytes = 4 * kTileBytes;    // A hi, A lo, B hi, B lo
 constexpr int kThreads = 128;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;
@@ -112,15 +117,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand in 128-byte swizzled
-// atoms of 8 rows x 128 bytes, atoms 1024 bytes apart.
+// Shared-memory matrix descriptor: K-major operand in swizzled atoms of
+// 8 rows x kSwz bytes, atoms 8 kSwz bytes apart (layout 2: 128-byte
+// swizzle, 4: 64-byte swizzle).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
     d |= (uint64_t)1 << 16;                         // leading byte offset (unused here)
-    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+    d |= (uint64_t)((8 * kSwz) >> 4) << 32;         // stride byte offset
     d |= (uint64_t)1 << 46;                         // descriptor version
-    d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+    d |= (uint64_t)(kSwz == 128 ? 2 : 4) << 61;     // swizzle mode
     return d;
 }
 
@@ -168,7 +174,7 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
 
 // ------------------------------------------------------------------ kernel
 template <int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
 k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
           const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
           int K, int ntn, int nsplit, EpiArgs ep) {
@@ -416,8 +422,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D bf16 tensor [rows][cols] (cols contiguous) read in 128-row x 64-column
-// boxes with the 128-byte swizzle.
+// 2-D bf16 tensor [rows][cols] (cols contiguous) read in 128-row x BK-column
+// boxes with the kSwz-byte swizzle.
 bool make_map(CUtensorMap* map, const void* base, int rows, int cols) {
     auto fn = encode_fn();
     if (!fn) return false;
@@ -426,7 +432,8 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int cols) {
     cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    tc::kSwz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
