@@ -218,7 +218,8 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
     constexpr int NP = padded(N);
     extern __shared__ float2 sm[];
     const int y0 = blockIdx.x * ROWS;
-    dfloat tau = df_zero(), charge = df_zero();
+    // per-thread sums of at most 8 n / 256 non-negative terms in float32
+    float tau = 0.0f, charge = 0.0f;
     // ROWS*N values, 4 per thread and iteration (float4 loads), unrolled so
     // that many loads are in flight
     constexpr int V4 = ROWS * N / 4;
@@ -246,12 +247,12 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
         float* row = reinterpret_cast<float*>(sm + (r >> 1) * NP);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            tau = df_add(tau, fmaxf(0.0f, d4[t] - (cap - m4[t])));
-            charge = df_add(charge, d4[t] + m4[t]);
+            tau += fmaxf(0.0f, d4[t] - (cap - m4[t]));
+            charge += d4[t] + m4[t];
             row[2 * pidx(mk_pos(x + t, N)) + (r & 1)] = (d4[t] + m4[t]) * inv_ab;
         }
     }
-    reduce2(df_val(tau), df_val(charge), acc, ACC_TAU, ACC_CHARGE, dr);
+    reduce2(tau, charge, acc, ACC_TAU, ACC_CHARGE, dr);
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, false);
     // split the packed spectra and apply the post-twiddle:
@@ -379,13 +380,15 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
                 float a0 = eu * ev * invn2 * B[rr][0];
                 // Poisson: (0,0) mode dropped; Helmholtz (eps > 0): divisor
                 // w^2 + eps and the (0,0) mode kept
+                // the divisor is at least (pi/L)^2 > 0 (or eps): the fast
+                // divide (2 ulp) stays far inside the transform's bound
                 float psi0 = (u == 0 && v == 0 && !(eps > 0.0f))
                                  ? 0.0f
-                                 : a0 / (wu * wu + wv * wv + eps);
+                                 : __fdividef(a0, wu * wu + wv * wv + eps);
                 float psin = 0.0f;
                 if (has_n) {
                     float an = eu * 2.0f * invn2 * B[rr][1];
-                    psin = an / (wu * wu + wvn * wvn + eps);
+                    psin = __fdividef(an, wu * wu + wvn * wvn + eps);
                     energy = df_add(energy, B[rr][1] * psin);
                 }
                 energy = df_add(energy, B[rr][0] * psi0);
