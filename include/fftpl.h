@@ -304,7 +304,7 @@ fftpl_status fftpl_fillers(const fftpl_region* region, const fftpl_cells* cells,
 
 /* Starts a placement run at (x0, y0) (device, m_mov): u = v = clamp(x0),
  * Nesterov a = 1 / no CG direction yet, lambda, gamma and alpha_max from the
- * options. */
+ * options.  FFTPL_EINVAL when the instance has no movable cells. */
 fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0);
 
 /* Runs up to iters iterations of the loop (Algorithm 1 with the step of

@@ -469,7 +469,8 @@ double orc_overflow(int n, double Ab, double rho_t, const double* mov_area,
         double cap = rho_t * (Ab - (fix_area ? fix_area[b] : 0.0));
         s += dmax(0.0, mov_area[b] - cap);
     }
-    return s / total_mov_area;
+    /* no movable cells: nothing can overflow (the ratio is read as 0) */
+    return total_mov_area > 0.0 ? s / total_mov_area : 0.0;
 }
 
 /* ------------------------------------------------------------------------ */

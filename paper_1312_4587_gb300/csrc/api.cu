@@ -923,7 +923,8 @@ fftpl_status fftpl_bin_ranges(fftpl_t h, const float* x, const float* y, int32_t
 fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
     if (!h) return FFTPL_EINVAL;
     Ctx& c = *h;
-    if (c.m_mov > 0 && (!x0 || !y0)) return set_err(c, FFTPL_EINVAL, "null positions");
+    if (c.m_mov <= 0) return set_err(c, FFTPL_EINVAL, "no movable cells to place");
+    if (!x0 || !y0) return set_err(c, FFTPL_EINVAL, "null positions");
     size_t m2 = 2 * (size_t)c.m_mov;
     if (!c.u) {
         TRY(dalloc(c, &c.u, m2));

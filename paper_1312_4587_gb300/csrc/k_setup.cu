@@ -117,7 +117,8 @@ cudaError_t launch_label_rounds(int m, int E, const int* np, const int* pc, int*
                                 int* dist, int* netlab, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     k_lp_init<<<nb(m), 256, 0, s>>>(m, kSeedStride, lab, dist);
-    for (int r = 0; r < kLabelRounds; ++r) {
+    // no nets: every cell keeps its seed label (or none) at distance 0 / unset
+    for (int r = 0; r < (E > 0 ? kLabelRounds : 0); ++r) {
         k_lp_net<<<nb(E), 256, 0, s>>>(E, np, pc, m, kRankMaxDegree, lab, netlab);
         cudaError_t e = cudaMemcpyAsync(next, lab, (size_t)m * sizeof(int), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
