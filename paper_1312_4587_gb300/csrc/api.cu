@@ -585,6 +585,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     c.stream = (cudaStream_t)stream;
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
     if (!c.stream) {
         // a blocking stream of our own: ordered with the legacy default
         // stream (implicit synchronisation) yet capturable into graphs

@@ -375,6 +375,7 @@ struct Ctx {
     // pins re-laid into degree slabs (see k_wire.cu): slot base + 32 k + lane
     int4* slabs = nullptr;      // {base slot, degree, net count, 0}
     int nslabs = 0;
+    int num_sms = 1;            // of the handle's device
     int64_t slab_slots = 0;
     int32_t *pin_cell = nullptr, *pin_slot = nullptr, *cell_pin_ptr = nullptr;
     float *pin_dx = nullptr, *pin_dy = nullptr;
@@ -463,6 +464,8 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                            const double* gamma_dev, const double* done, bool interleave,
                            cudaStream_t s);
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s);
+// 1 when the WA kernel runs slab pairs per warp (large instances)
+int wa_pairs(const Ctx& c);
 
 // create-time netlist layout (k_setup.cu): label rounds for the internal
 // cell numbers (seeds every kSeedStride cells, kLabelRounds rounds, nets of

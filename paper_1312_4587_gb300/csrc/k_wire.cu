@@ -253,12 +253,14 @@ __device__ __forceinline__ void wa_slab(const WaIo& io, const int4& sl, int lane
     }
 }
 
-// One warp per pair of consecutive slabs (2w, 2w+1).  When both have the
-// same degree 2..4 (most nets) each lane runs its two nets with their loads
-// in flight together; otherwise the slabs go one after the other.
+// pairs != 0: one warp per pair of consecutive slabs (2w, 2w+1); when both
+// have the same degree 2..4 (most nets) each lane runs its two nets with
+// their loads in flight together, otherwise the slabs go one after the
+// other.  pairs == 0: one warp per slab (small instances, where the GPU has
+// room for a warp per slab and latency matters more).
 template <bool CSR, bool LSE>
 __global__ void __launch_bounds__(kWaThreads, 4)
-k_wa(int nslabs, const int4* __restrict__ slabs, WaIo io, float gamma,
+k_wa(int nslabs, int pairs, const int4* __restrict__ slabs, WaIo io, float gamma,
      const double* __restrict__ gamma_dev, double* __restrict__ acc,
      const double* __restrict__ done, DetRed dr) {
     if (done && *done != 0.0) return;
@@ -269,9 +271,15 @@ k_wa(int nslabs, const int4* __restrict__ slabs, WaIo io, float gamma,
     // exp(t / g) = exp2(t * log2(e) / g)
     const float l2g = (float)(1.4426950408889634 / (double)gamma);
     const int4 zero = make_int4(0, 0, 0, 0);
+    float wsum = 0.0f, hsum = 0.0f;
+    if (!pairs) {
+        const int4 sl = warp < nslabs ? slabs[warp] : zero;
+        wa_slab<CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum);
+        reduce2(wsum, hsum, acc, ACC_W, ACC_HPWL, dr);
+        return;
+    }
     const int4 sa = 2 * warp < nslabs ? slabs[2 * warp] : zero;
     const int4 sb = 2 * warp + 1 < nslabs ? slabs[2 * warp + 1] : zero;
-    float wsum = 0.0f, hsum = 0.0f;
     if (sa.y == sb.y && sa.y >= 2 && sa.y <= 4) {
         const bool la = lane < sa.z, lb = lane < sb.z;
         switch (sa.y) {
@@ -364,6 +372,12 @@ k_split(int m, const int* __restrict__ rank, const float2* __restrict__ gW2,
 
 static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }
 
+// Slab pairs per warp once a warp per slab would fill the GPU about twice
+// over (4 CTAs of 8 warps per SM); below that, one slab per warp.
+int wa_pairs(const Ctx& c) {
+    return c.nslabs >= 2LL * c.num_sms * 4 * (kWaThreads / 32) ? 1 : 0;
+}
+
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                            const double* gamma_dev, const double* done, bool interleave,
                            cudaStream_t s) {
@@ -376,11 +390,12 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
     const WaIo io{c.pin_cell, c.pin_dx, c.pin_dy, c.pos2, c.pxy,
                   c.opt.deterministic ? nullptr : c.gW2, c.pin_slot, c.gpin};
     const int wpb = kWaThreads / 32;
-    int nb = nblk((c.nslabs + 1) / 2, wpb);   // one warp per pair of slabs
+    const int pairs = wa_pairs(c);
+    int nb = nblk(pairs ? (c.nslabs + 1) / 2 : c.nslabs, wpb);
     const bool lse = c.opt.wirelength == FFTPL_WL_LSE;
     auto go = [&](auto kern) {
-        kern<<<nb, kWaThreads, 0, s>>>(c.nslabs, c.slabs, io, gamma, gamma_dev, c.acc, done,
-                                       det_red(c, 1));
+        kern<<<nb, kWaThreads, 0, s>>>(c.nslabs, pairs, c.slabs, io, gamma, gamma_dev, c.acc,
+                                       done, det_red(c, 1));
     };
     if (c.opt.deterministic) {
         if (lse) go(k_wa<true, true>);
