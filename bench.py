@@ -55,12 +55,12 @@ STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "ce
 # source it was taken from is unchanged: key = first 16 hex digits of the
 # SHA-256 of the kernel file followed by fftpl_internal.cuh.
 STAGE_TRAFFIC = {
-    "scatter": ("k_density.cu", "13027c5984583aff", 41772032 + 256),
-    "rows_fwd": ("k_spectral.cu", "3ecd272d697f20ea", 33655808 + 1280),
-    "cols": ("k_spectral.cu", "3ecd272d697f20ea", 17454592 + 588288),
-    "rows_inv": ("k_spectral.cu", "3ecd272d697f20ea", 33650432 + 2417408),
-    "wa": ("k_wire.cu", "8b57baf50d9e5db5", 28479232 + 2088960 + 138113280 + 22430208),
-    "cells": ("k_wire.cu", "8b57baf50d9e5db5", 75812608 + 15020544),
+    "scatter": ("k_density.cu", "9456c81802a6adda", 50687232 + 824320),
+    "rows_fwd": ("k_spectral.cu", "e88bb1bf4172a223", 33650176 + 1024),
+    "cols": ("k_spectral.cu", "e88bb1bf4172a223", 17544448 + 669184),
+    "rows_inv": ("k_spectral.cu", "e88bb1bf4172a223", 33645056 + 2180608),
+    "wa": ("k_wire.cu", "549a2ada1712c5eb", 137156608 + 19534848),
+    "cells": ("k_wire.cu", "549a2ada1712c5eb", 76274176 + 12669184),
 }
 
 
