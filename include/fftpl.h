@@ -260,8 +260,14 @@ fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma,
                         float* gNx, float* gNy, float* gWx, float* gWy,
                         fftpl_eval_report* rep);
 
-/* fftpl_eval on HOST buffers: copies x, y to the device, evaluates, copies
- * the four gradients back and synchronises.  Pinned host memory is fastest. */
+/* fftpl_eval on HOST buffers (m_mov floats each; gradient outputs may be
+ * NULL), synchronising before it returns.  When all six are pinned
+ * (page-locked, device-mapped) host memory the kernels read x, y and write
+ * the gradients over the host link themselves, overlapping the transfers
+ * with the computation (the scatter reads the positions once and keeps a
+ * device copy for the later kernels); otherwise the call copies x, y in,
+ * evaluates and copies the gradients out.  Results are the same either way
+ * (bit-identical in deterministic mode). */
 fftpl_status fftpl_eval_host(fftpl_t h, const float* x_host, const float* y_host, float gamma,
                              float* gNx_host, float* gNy_host, float* gWx_host,
                              float* gWy_host, fftpl_eval_report* rep);

@@ -230,8 +230,12 @@ cudaError_t launch_tau(Ctx& c, cudaStream_t s) {
 enum { EV_DENSITY = 1, EV_WA = 2, EV_ADJOINT = 4, EV_NO_GATHER = 8 };
 
 // Enqueues one evaluation; gradients must be non-null device arrays.
+// stage (2 m_mov floats, or null): x, y may be pinned host memory; the
+// scatter reads them once and leaves a device copy there for the later
+// kernels.
 fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, int what,
-                          float* gNx, float* gNy, float* gWx, float* gWy) {
+                          float* gNx, float* gNy, float* gWx, float* gWy,
+                          float* stage = nullptr) {
     cudaStream_t s = c.stream;
     size_t nn = (size_t)c.n * c.n;
     CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
@@ -257,7 +261,7 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
             Stage st(c, 0, s);
             if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
             else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
-            CK(launch_scatter_mov(c, x, y, pos_from_scatter, s));
+            CK(launch_scatter_mov(c, x, y, pos_from_scatter, stage, s));
         }
         if (pos_from_scatter) TRY(wa_branch(false));
         TRY(enqueue_solve(c, s));
@@ -266,9 +270,12 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
     if (!(what & EV_NO_GATHER)) {
         Stage st(c, 5, s);
         if (dens && wa && !(what & EV_ADJOINT)) {
-            CK(launch_cells(c, x, y, gNx, gNy, gWx, gWy, s));
+            CK(launch_cells(c, stage ? stage : x, stage ? stage + c.m_mov : y, gNx, gNy, gWx,
+                            gWy, s));
         } else {
-            if (dens) CK(launch_gather(c, x, y, gNx, gNy, (what & EV_ADJOINT) != 0, s));
+            if (dens)
+                CK(launch_gather(c, stage ? stage : x, stage ? stage + c.m_mov : y, gNx, gNy,
+                                 (what & EV_ADJOINT) != 0, s));
             if (wa) CK(launch_pin_sum(c, gWx, gWy, s));
         }
     }
@@ -791,18 +798,13 @@ fftpl_status fftpl_wa(fftpl_t h, const float* x, const float* y, float gamma, do
     return FFTPL_OK;
 }
 
-fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma, float* gNx,
-                        float* gNy, float* gWx, float* gWy, fftpl_eval_report* rep) {
-    if (!h || (h->m_mov > 0 && (!x || !y))) return h ? set_err(*h, FFTPL_EINVAL, "null positions") : FFTPL_EINVAL;
-    Ctx& c = *h;
-    if (!(gamma > 0.0f) || !isfinite(gamma)) return set_err(c, FFTPL_EINVAL, "gamma must be > 0");
-    gNx = gNx ? gNx : scratch(c, 0);
-    gNy = gNy ? gNy : scratch(c, 1);
-    gWx = gWx ? gWx : scratch(c, 2);
-    gWy = gWy ? gWy : scratch(c, 3);
+// One full evaluation through the captured graph when use_graphs is set
+// (the graph is keyed by the buffers, gamma and the staging buffer).
+static fftpl_status eval_impl(Ctx& c, const float* x, const float* y, float gamma, float* gNx,
+                              float* gNy, float* gWx, float* gWy, float* stage) {
     if (c.opt.use_graphs && !c.profiling) {
         float gk = gamma;
-        const void* key[7] = {x, y, gNx, gNy, gWx, gWy, nullptr};
+        const void* key[8] = {x, y, gNx, gNy, gWx, gWy, nullptr, stage};
         memcpy(&key[6], &gk, sizeof(float));
         if (!c.eval_graph || memcmp(key, c.graph_key, sizeof(key)) != 0) {
             if (c.eval_graph) {
@@ -812,7 +814,8 @@ fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma, 
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
             int64_t before = c.launches;
-            fftpl_status st = enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy);
+            fftpl_status st =
+                enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy, stage);
             cudaError_t ee = cudaStreamEndCapture(c.stream, &g);
             if (st != FFTPL_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -831,11 +834,35 @@ fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma, 
         c.fields_valid = true;
         c.rho_valid = false;
         c.split_valid = false;
-    } else {
-        TRY(enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy));
+        return FFTPL_OK;
     }
+    return enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy, stage);
+}
+
+fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma, float* gNx,
+                        float* gNy, float* gWx, float* gWy, fftpl_eval_report* rep) {
+    if (!h || (h->m_mov > 0 && (!x || !y))) return h ? set_err(*h, FFTPL_EINVAL, "null positions") : FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (!(gamma > 0.0f) || !isfinite(gamma)) return set_err(c, FFTPL_EINVAL, "gamma must be > 0");
+    gNx = gNx ? gNx : scratch(c, 0);
+    gNy = gNy ? gNy : scratch(c, 1);
+    gWx = gWx ? gWx : scratch(c, 2);
+    gWy = gWy ? gWy : scratch(c, 3);
+    TRY(eval_impl(c, x, y, gamma, gNx, gNy, gWx, gWy, nullptr));
     if (rep) TRY(read_report(c, rep));
     return FFTPL_OK;
+}
+
+// Device address of pinned (page-locked, mapped) host memory, or null for
+// any other pointer (pageable host memory is not handed to kernels).
+static void* mapped_host(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 fftpl_status fftpl_eval_host(fftpl_t h, const float* x_host, const float* y_host, float gamma,
@@ -844,6 +871,7 @@ fftpl_status fftpl_eval_host(fftpl_t h, const float* x_host, const float* y_host
     if (!h) return FFTPL_EINVAL;
     Ctx& c = *h;
     if (c.m_mov > 0 && (!x_host || !y_host)) return set_err(c, FFTPL_EINVAL, "null positions");
+    if (!(gamma > 0.0f) || !isfinite(gamma)) return set_err(c, FFTPL_EINVAL, "gamma must be > 0");
     size_t m = (size_t)c.m_mov;
     if (!c.hx) {
         TRY(dalloc(c, &c.hx, 2 * m));
@@ -851,9 +879,22 @@ fftpl_status fftpl_eval_host(fftpl_t h, const float* x_host, const float* y_host
         c.hy = c.hx + m;
     }
     cudaStream_t s = c.stream;
+    // all six buffers pinned: the kernels read the positions and write the
+    // gradients over the host link themselves (the scatter reads x, y once
+    // and stages a device copy; the cell kernel writes the gradients), so the
+    // transfers overlap the computation instead of preceding and following it
+    void* xd = mapped_host(x_host);
+    void* yd = mapped_host(y_host);
+    void* gd[4] = {mapped_host(gNx_host), mapped_host(gNy_host), mapped_host(gWx_host),
+                   mapped_host(gWy_host)};
+    if (m > 0 && xd && yd && gd[0] && gd[1] && gd[2] && gd[3]) {
+        TRY(eval_impl(c, (const float*)xd, (const float*)yd, gamma, (float*)gd[0], (float*)gd[1],
+                      (float*)gd[2], (float*)gd[3], c.hx));
+        return read_report(c, rep);
+    }
     CK(cudaMemcpyAsync(c.hx, x_host, m * sizeof(float), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.hy, y_host, m * sizeof(float), cudaMemcpyHostToDevice, s));
-    TRY(fftpl_eval(h, c.hx, c.hy, gamma, c.hg, c.hg + m, c.hg + 2 * m, c.hg + 3 * m, nullptr));
+    TRY(eval_impl(c, c.hx, c.hy, gamma, c.hg, c.hg + m, c.hg + 2 * m, c.hg + 3 * m, nullptr));
     float* outs[4] = {gNx_host, gNy_host, gWx_host, gWy_host};
     for (int k = 0; k < 4; ++k)
         if (outs[k])
@@ -958,7 +999,7 @@ fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
         CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
         if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
         else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
-        CK(launch_scatter_mov(c, c.v, c.v + c.m_mov, false, s));
+        CK(launch_scatter_mov(c, c.v, c.v + c.m_mov, false, nullptr, s));
         CK(launch_tau(c, s));
         CK(launch_gamma0(c, s));
     }
@@ -981,7 +1022,7 @@ static fftpl_status loop_eval(Ctx& c, bool cells) {
         Stage st(c, 0, s);
         if (c.opt.deterministic) CK(cudaMemsetAsync(c.Dq, 0, nn * sizeof(long long), s));
         else CK(cudaMemsetAsync(c.D, 0, nn * sizeof(float), s));
-        CK(launch_scatter_mov(c, vx, vy, true, s));
+        CK(launch_scatter_mov(c, vx, vy, true, nullptr, s));
     }
     // the WA branch forks after the scatter, which wrote its positions
     CK(cudaEventRecord(c.ev_fork, s));

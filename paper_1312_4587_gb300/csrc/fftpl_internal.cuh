@@ -410,7 +410,7 @@ struct Ctx {
 
     // captured CUDA graph of fftpl_eval for one set of buffers
     cudaGraphExec_t eval_graph = nullptr;
-    const void* graph_key[7] = {};
+    const void* graph_key[8] = {};
     int64_t graph_nkernels = 0;
     // profiling ring of (stage, begin, end) event records
     std::vector<cudaEvent_t> prof_ev;
@@ -445,9 +445,10 @@ void prepare_spectral(int logn);
 cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* w,
                            const float* h, int m, float* D, long long* Dq, cudaStream_t s);
 // movable cells into the handle's D / Dq; write_pos: also the interleaved
-// centres pos2 (by internal cell number) for the WA kernel
+// centres pos2 (by internal cell number) for the WA kernel; stage (2 m_mov
+// floats or null): also a device copy of (x, y)
 cudaError_t launch_scatter_mov(Ctx& c, const float* x, const float* y, bool write_pos,
-                               cudaStream_t s);
+                               float* stage, cudaStream_t s);
 cudaError_t launch_bin_ranges(Ctx& c, const float* x, const float* y, int32_t* ranges,
                               cudaStream_t s);
 cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s);

@@ -19,16 +19,23 @@ namespace fftpl {
 // product), scaled by 2^32 (exact) and rounded to the nearest integer (ties to
 // even); int64 atomics make the bin sums independent of order.
 // pos, if given, receives the interleaved centre at the cell's internal
-// number for the WA kernel (so that it needs no pass of its own).
+// number for the WA kernel (so that it needs no pass of its own); stage, if
+// given, a device copy of (x, y) for the later kernels (x, y may then be
+// pinned host memory read over the host link once).
 template <bool QUANT>
 __global__ void __launch_bounds__(kCellThreads)
 k_scatter(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
           const float* __restrict__ w, const float* __restrict__ h, const int* __restrict__ rank,
-          float2* __restrict__ pos, float* __restrict__ D, unsigned long long* __restrict__ Dq) {
+          float2* __restrict__ pos, float* __restrict__ stage, float* __restrict__ D,
+          unsigned long long* __restrict__ Dq) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const float xi = x[i], yi = y[i];
     if (pos) pos[rank[i]] = make_float2(xi, yi);
+    if (stage) {
+        stage[i] = xi;
+        stage[m + i] = yi;
+    }
     Span s = cell_span(g, xi, yi, w[i], h[i]);
     if (s.ilo > s.ihi || s.jlo > s.jhi) return;
     const AxisOv ax = axis_ov(g.x0, g.wb, s.ilo, s.ihi, s.xl, s.xh);
@@ -153,28 +160,28 @@ cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* 
     int nb = blocks_for(m, kCellThreads);
     if (Dq)
         k_scatter<true><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, nullptr, nullptr,
-                                                   nullptr,
+                                                   nullptr, nullptr,
                                                    reinterpret_cast<unsigned long long*>(Dq));
     else
-        k_scatter<false><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, nullptr, nullptr, D,
-                                                    nullptr);
+        k_scatter<false><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, w, h, nullptr, nullptr,
+                                                    nullptr, D, nullptr);
     c.launches++;
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_mov(Ctx& c, const float* x, const float* y, bool write_pos,
-                               cudaStream_t s) {
+                               float* stage, cudaStream_t s) {
     const int m = c.m_mov;
     if (m <= 0) return cudaSuccess;
     float2* pos = write_pos ? c.pos2 : nullptr;
     int nb = blocks_for(m, kCellThreads);
     if (c.opt.deterministic)
         k_scatter<true><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, c.w, c.h, c.cell_rank, pos,
-                                                   nullptr,
+                                                   stage, nullptr,
                                                    reinterpret_cast<unsigned long long*>(c.Dq));
     else
         k_scatter<false><<<nb, kCellThreads, 0, s>>>(c.grid, m, x, y, c.w, c.h, c.cell_rank, pos,
-                                                    c.D, nullptr);
+                                                    stage, c.D, nullptr);
     c.launches++;
     return cudaGetLastError();
 }

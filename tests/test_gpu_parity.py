@@ -253,8 +253,15 @@ def test_graphs_and_host_path(F):
         assert n_launch >= 3 * 5
         hx = torch.from_numpy(inst.x).pin_memory(); hy = torch.from_numpy(inst.y).pin_memory()
         hg = [torch.empty(inst.m_mov, dtype=torch.float32).pin_memory() for _ in range(4)]
+        # pinned buffers: the kernels read and write host memory directly
         rep_h = F.fftpl_eval_host(p.h, hx, hy, inst.gamma, *hg)
         assert all(np.array_equal(a.numpy(), b) for a, b in zip(hg, outs[0][1]))
+        # pageable buffers: copied in and out; the same results
+        px = np.array(inst.x); py = np.array(inst.y)
+        pg = [np.empty(inst.m_mov, np.float32) for _ in range(4)]
+        rep_p = F.fftpl_eval_host(p.h, px, py, inst.gamma, *pg)
+        assert all(np.array_equal(a, b) for a, b in zip(pg, outs[0][1]))
+        assert rep_p["N"] == rep_h["N"] and rep_p["W"] == rep_h["W"]
     got = {"rep": rep_h, "gNx": hg[0].numpy(), "gNy": hg[1].numpy(), "gWx": hg[2].numpy(),
            "gWy": hg[3].numpy(), "rho": ref["rho"], "psi": ref["psi"], "ex": ref["ex"], "ey": ref["ey"]}
     check_eval(got, ref)
