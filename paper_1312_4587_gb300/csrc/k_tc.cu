@@ -12,7 +12,8 @@
 // (Eqs. 10-12 at the bin centres; the energy N = 1/2 A_b sum B Psi is
 // reduced in the G2 epilogue.)  Operands are float32 values split into two
 // bf16 halves, x = hi + lo; each product accumulates hi*hi + hi*lo + lo*hi in
-// float32 in tensor memory (the lo*lo term, 2^-16 relative, is dropped).
+// float32 in tensor memory (the lo*lo term, 2^-16 relative, is dropped), in
+// four chains over consecutive quarters of K summed in the epilogue.
 //
 // Kernel: one CTA per 128 x 128 output tile, 4 warps.  Warp 0 (one thread)
 // loads 128 x 64 operand tiles with TMA (128-byte swizzle) into a 3-stage
@@ -45,6 +46,14 @@ constexpr int kStageBytes = 4 * kTileBytes;    // A hi, A lo, B hi, B lo
 constexpr int kThreads = 128;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;
 constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait
+// Accumulators per tile: the k-tiles are cut into kAcc consecutive chunks,
+// each accumulated in its own 128-column region of tensor memory and the
+// chunks summed in float32 in the epilogue.  The error of the tensor cores'
+// float32 accumulation grows with the chain length: one chain over K = 4096
+// left psi 3.7e-4 (relative L2) from the transform path at n = 4096, four
+// chains of K/4 stay within 2e-4.  kAcc * BN = 512 columns is all of an SM's
+// tensor memory, which the one CTA per SM owns.
+constexpr int kAcc = 4;
 
 enum Epi { EPI_F32 = 0, EPI_SPLIT = 1, EPI_SPECTRAL = 2, EPI_PSI_EX = 3, EPI_EY = 4 };
 
@@ -190,6 +199,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     // one 1-D grid of tiles, column tiles fastest (CTAs in flight share A rows)
     const int m0 = (blockIdx.x / ntn) * BM, n0 = (blockIdx.x % ntn) * BN;
     const int ktiles = K / BK;
+    const int nacc = ktiles < kAcc ? ktiles : kAcc;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -204,7 +214,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(BN));
+                     "r"(kAcc * BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     __syncthreads();
@@ -238,8 +248,16 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
         for (int kt = (issued > kStages ? issued - kStages : 0); kt < issued; ++kt)
             mbar_wait(&full_bar[kt % kStages], (uint32_t)(kt / kStages) & 1u, kWaitNs);
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
+        // MMA issuer; chunk c holds k-tiles [ceil(c K' / nacc), ceil((c+1) K' / nacc))
+        int chunk = 0, next_start = (ktiles + nacc - 1) / nacc;
+        const uint64_t d_ring = smem_desc(smem_u32(smem));
         for (int kt = 0; kt < ktiles; ++kt) {
+            bool first = kt == 0;
+            if (kt == next_start) {
+                ++chunk;
+                first = true;
+                next_start = ((chunk + 1) * ktiles + nacc - 1) / nacc;
+            }
             const int s = kt % kStages;
             const uint32_t ph = (uint32_t)(kt / kStages) & 1u;
             if (!mbar_wait(&full_bar[s], ph, kWaitNs)) {
@@ -248,18 +266,24 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_hi = smem_u32(smem + (size_t)s * kStageBytes);
-            const uint32_t a_lo = a_hi + kTileBytes;
-            const uint32_t b_hi = a_hi + 2 * kTileBytes;
-            const uint32_t b_lo = a_hi + 3 * kTileBytes;
+            // descriptors of this stage: the start-address field (bits 0-13,
+            // address >> 4) of the ring's base descriptor advanced by the
+            // stage, operand and k offsets (the whole ring lies below 256 KiB,
+            // so the field cannot carry into the next one)
+            const uint64_t ds = d_ring + (uint64_t)((s * kStageBytes) >> 4);
+            const uint32_t d = tmem + (uint32_t)(chunk * BN);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t off = kk * 32;   // 16 bf16 along K inside the swizzle atom
-                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-                mma_bf16(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), acc);
+                // 16 bf16 along K inside the swizzle atom: 32 bytes
+                const uint64_t a_hi = ds + (uint64_t)((kk * 32) >> 4);
+                const uint64_t a_lo = a_hi + (uint64_t)(kTileBytes >> 4);
+                const uint64_t b_hi = a_hi + (uint64_t)((2 * kTileBytes) >> 4);
+                const uint64_t b_lo = a_hi + (uint64_t)((3 * kTileBytes) >> 4);
+                const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+                mma_bf16(d, a_hi, b_hi, acc);
                 if (nsplit == 3) {
-                    mma_bf16(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), 1u);
-                    mma_bf16(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), 1u);
+                    mma_bf16(d, a_hi, b_lo, 1u);
+                    mma_bf16(d, a_lo, b_hi, 1u);
                 }
             }
             mma_commit(&empty_bar[s]);
@@ -278,8 +302,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     if (store) {
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+            float v[32], t[32];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32);
+            tmem_ld32(ta, v);
+            // chunks summed in a fixed order
+            for (int a = 1; a < nacc; ++a) {
+                tmem_ld32(ta + (uint32_t)(a * BN), t);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] += t[j];
+            }
             const int col0 = n0 + c * 32;
             if (EPI == EPI_F32) {
                 float4* dst = reinterpret_cast<float4*>(ep.f32 + (size_t)row * ep.ld + col0);
@@ -339,7 +370,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * BN));
 }
 
 // Tables: C[u][x], the stacked [Ct; Sx] (Ct[x][u] = C[u][x]) and Sy[y][v],

@@ -57,7 +57,7 @@ def run_gemm(F, ah, al, bh, bl, nsplit=3, no_loads=0, fill=0.0):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 192), (384, 256, 512),
-                                   (128, 256, 1024)])
+                                   (128, 128, 320), (128, 256, 1024)])
 def test_gemm_integer_exact(F, M, N, K):
     """Small integers: every partial sum is an integer below 2^24, exact in
     float32, so the tensor-core result equals the FP64 product bit for bit."""
@@ -213,3 +213,30 @@ def test_tc_in_the_loop(F):
     for k in ("hpwl", "N", "tau"):
         ra = np.array([r[k] for r in a]); rb = np.array([r[k] for r in b])
         assert np.allclose(ra, rb, rtol=1e-3, atol=1e-6), k
+
+
+def test_tc_largest_grid_matches_fft_path(F):
+    """n = 4096 (the largest grid, 600 MB of bf16 operands): 20000 random
+    cells of a few bins each; the two solve paths agree within the
+    tensor-core bound, and the energy is positive."""
+    import synth as S
+    rng = np.random.default_rng(4096)
+    m = 20000
+    L = 2048.0
+    x, y, w, h = S.random_cells(rng, m, (0.0, 0.0, L, L), wmax=3.0, hmax=3.0)
+    inst = S.make_instance("tiny")
+    inst.n = 4096
+    inst.region = (0.0, 0.0, L, L)
+    inst.m_mov = m
+    inst.m_fix = 0
+    inst.w, inst.h, inst.x, inst.y = w, h, x, y
+    inst.fix_x = np.zeros(0, np.float32); inst.fix_y = np.zeros(0, np.float32)
+    inst.net_ptr = np.array([0, 2], np.int32); inst.pin_cell = np.array([0, 1], np.int32)
+    inst.pin_dx = np.zeros(2, np.float32); inst.pin_dy = np.zeros(2, np.float32)
+    t = gpu_eval(F, inst, solve_path=F.FFTPL_SOLVE_TC_BF16X3)
+    f = gpu_eval(F, inst, solve_path=F.FFTPL_SOLVE_FFT)
+    for k in ("psi", "ex", "ey"):
+        assert rel(t[k], f[k]) < TOL_TC, k
+    assert rel(np.concatenate([t["gNx"], t["gNy"]]), np.concatenate([f["gNx"], f["gNy"]])) < TOL_TC
+    assert t["rep"]["N"] == pytest.approx(f["rep"]["N"], rel=TOL_TC)
+    assert t["rep"]["N"] > 0
