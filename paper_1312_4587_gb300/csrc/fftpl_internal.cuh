@@ -236,6 +236,19 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// *p += (a, b) as one relaxed, device-scope 8-byte vector reduction with no
+// return value (the same operation as atomicAdd on a float2, which is issued
+// as a returning atomic and so holds its destination registers until the
+// answer comes back).
+__device__ __forceinline__ void red_add_f2(float2* p, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
+// *p += v as a relaxed, device-scope reduction with no return value.
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
 // Sums of non-negative per-thread values a and b over each warp (a float32
 // tree: relative error at most 5 units in the last place for non-negative
 // terms); lane 0 adds each nonzero warp total in FP64 to the stripe of
@@ -247,8 +260,8 @@ __device__ __forceinline__ void block_acc2(float a, float b, double* acc, int qa
     if ((threadIdx.x & 31) == 0) {
         unsigned gw = (blockIdx.x * ((blockDim.x + 31) >> 5)) + (threadIdx.x >> 5);
         double* st = acc + (gw & (kAccStripes - 1)) * kAccStride;
-        if (qa >= 0 && a != 0.0f) atomicAdd(st + qa, (double)a);
-        if (qb >= 0 && b != 0.0f) atomicAdd(st + qb, (double)b);
+        if (qa >= 0 && a != 0.0f) red_add_f64(st + qa, (double)a);
+        if (qb >= 0 && b != 0.0f) red_add_f64(st + qb, (double)b);
     }
 }
 

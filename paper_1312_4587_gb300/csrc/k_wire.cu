@@ -68,7 +68,8 @@ template <int D, bool CSR, bool LSE>
 __device__ __forceinline__ void wa_core(const float (&rx)[D], const float (&ry)[D], int base,
                                         const WaIo& io, float l2g, float inv_g, float& wsum,
                                         float& hsum) {
-    float ex_p[D], ex_m[D], ey_p[D], ey_m[D];
+    // the exponentials are recomputed in the gradient loop (the same
+    // operations, so the same values) rather than held in 4 D registers
     float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -79,10 +80,10 @@ __device__ __forceinline__ void wa_core(const float (&rx)[D], const float (&ry)[
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         float tpx = rx[k] - Mx, tmx = rx[k] - mx, tpy = ry[k] - My, tmy = ry[k] - my;
-        ex_p[k] = exp2f(tpx * l2g); ex_m[k] = exp2f(-tmx * l2g);
-        ey_p[k] = exp2f(tpy * l2g); ey_m[k] = exp2f(-tmy * l2g);
-        Spx += ex_p[k]; Tpx = fmaf(tpx, ex_p[k], Tpx); Smx += ex_m[k]; Tmx = fmaf(tmx, ex_m[k], Tmx);
-        Spy += ey_p[k]; Tpy = fmaf(tpy, ey_p[k], Tpy); Smy += ey_m[k]; Tmy = fmaf(tmy, ey_m[k], Tmy);
+        const float apx = exp2f(tpx * l2g), amx = exp2f(-tmx * l2g);
+        const float apy = exp2f(tpy * l2g), amy = exp2f(-tmy * l2g);
+        Spx += apx; Tpx = fmaf(tpx, apx, Tpx); Smx += amx; Tmx = fmaf(tmx, amx, Tmx);
+        Spy += apy; Tpy = fmaf(tpy, apy, Tpy); Smy += amy; Tmy = fmaf(tmy, amy, Tmy);
     }
     // every S is in [1, d] (its largest term is exp(0) = 1): the fast
     // reciprocal (2 ulp) is accurate over that whole range
@@ -100,14 +101,15 @@ __device__ __forceinline__ void wa_core(const float (&rx)[D], const float (&ry)[
                                                   (logf(Spy) + logf(Smy)));
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            float gxj = ex_p[k] * isx - ex_m[k] * imx;
-            float gyj = ey_p[k] * isy - ey_m[k] * imy;
+            float tpx = rx[k] - Mx, tmx = rx[k] - mx, tpy = ry[k] - My, tmy = ry[k] - my;
+            float gxj = exp2f(tpx * l2g) * isx - exp2f(-tmx * l2g) * imx;
+            float gyj = exp2f(tpy * l2g) * isy - exp2f(-tmy * l2g) * imy;
             if (CSR) {
                 int sl = io.pin_slot[base + 32 * k];
                 if (sl >= 0) io.gpin[sl] = make_float2(gxj, gyj);
             } else {
                 int c = io.pin_cell[base + 32 * k];
-                if (c >= 0) atomicAdd(io.gW + c, make_float2(gxj, gyj));
+                if (c >= 0) red_add_f2(io.gW + c, gxj, gyj);
             }
         }
         return;
@@ -122,14 +124,14 @@ __device__ __forceinline__ void wa_core(const float (&rx)[D], const float (&ry)[
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         float tpx = rx[k] - Mx, tmx = rx[k] - mx, tpy = ry[k] - My, tmy = ry[k] - my;
-        float gxj = ex_p[k] * fmaf(tpx, P1x, P0x) - ex_m[k] * fmaf(-tmx, Q1x, Q0x);
-        float gyj = ey_p[k] * fmaf(tpy, P1y, P0y) - ey_m[k] * fmaf(-tmy, Q1y, Q0y);
+        float gxj = exp2f(tpx * l2g) * fmaf(tpx, P1x, P0x) - exp2f(-tmx * l2g) * fmaf(-tmx, Q1x, Q0x);
+        float gyj = exp2f(tpy * l2g) * fmaf(tpy, P1y, P0y) - exp2f(-tmy * l2g) * fmaf(-tmy, Q1y, Q0y);
         if (CSR) {
             int sl = io.pin_slot[base + 32 * k];
             if (sl >= 0) io.gpin[sl] = make_float2(gxj, gyj);
         } else {
             int c = io.pin_cell[base + 32 * k];
-            if (c >= 0) atomicAdd(io.gW + c, make_float2(gxj, gyj));
+            if (c >= 0) red_add_f2(io.gW + c, gxj, gyj);
         }
     }
 }
@@ -232,7 +234,7 @@ __device__ __forceinline__ void wa_net_any(const WaIo& io, int base, int d, floa
             if (q >= 0) io.gpin[q] = make_float2(gxj, gyj);
         } else {
             int c = io.pin_cell[sl];
-            if (c >= 0) atomicAdd(io.gW + c, make_float2(gxj, gyj));
+            if (c >= 0) red_add_f2(io.gW + c, gxj, gyj);
         }
     }
 }
