@@ -508,6 +508,17 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
         int d = np[e + 1] - np[e], j = seen[d]++;
         net_slot[e] = slabs[(size_t)(first_slab[d] + j / 32)].x + (j % 32);
     }
+    // the slabs of degree kBigMin..kBigMax first (k_wa_big), the others
+    // after them in the same order (k_wa); the slot layout is unchanged
+    auto is_big = [](const int4& sl) { return sl.y >= kBigMin && sl.y <= kBigMax; };
+    std::stable_partition(slabs.begin(), slabs.end(), is_big);
+    c.nbig = 0;
+    c.big_dmax = 0;
+    for (const int4& sl : slabs)
+        if (is_big(sl)) {
+            c.nbig++;
+            c.big_dmax = std::max(c.big_dmax, sl.y);
+        }
     // cell-ordered slots (by internal cell number) for the deterministic
     // reduction
     std::vector<int32_t> cslot;
@@ -651,13 +662,16 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     CK(cudaMemcpyAsync(c.tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.ph, ph.data(), (n + 1) * sizeof(float2), cudaMemcpyHostToDevice, s));
     TRY(build_slabs(c, nets, pins));
+    CK(prepare_wa(c));
     if (c.opt.deterministic) {
         // capacity in blocks of every kernel that reduces on each stream
         long long cap0 = std::max<long long>((long long)n / 4, (2LL * c.m_mov + kCellThreads - 1) / kCellThreads);
         if (c.opt.solve_path == FFTPL_SOLVE_TC_BF16X3)
             cap0 = std::max<long long>(cap0, std::max<long long>((long long)n * n / 1024,
                                                                  (long long)(n / 128) * (n / 128)));
-        long long cap1 = ((long long)c.nslabs + kWaThreads / 32 - 1) / (kWaThreads / 32);
+        long long cap1 = std::max<long long>(
+            ((long long)(c.nslabs - c.nbig) + kWaThreads / 32 - 1) / (kWaThreads / 32),
+            ((long long)c.nbig + kBigWarps - 1) / kBigWarps);
         c.det_cap[0] = (int)std::max<long long>(cap0, 1);
         c.det_cap[1] = (int)std::max<long long>(cap1, 1);
         TRY(dalloc(c, &c.det_part, 2 * ((size_t)c.det_cap[0] + c.det_cap[1])));

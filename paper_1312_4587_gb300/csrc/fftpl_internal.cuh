@@ -31,6 +31,11 @@ constexpr int kSpecThreads = 256;   // threads of the transform kernels
 constexpr int kSpecBuffers = 4;     // complex length-n buffers per CTA
 constexpr int kCellThreads = 256;
 constexpr int kWaThreads = 256;
+// Slabs of degree kBigMin..kBigMax go to the shared-memory WA kernel
+// (k_wa_big, kBigWarps warps per block); the rest to k_wa.
+constexpr int kBigMin = 7;
+constexpr int kBigMax = 64;
+constexpr int kBigWarps = 2;
 constexpr int kWaPinCap = 2048;     // pins staged in shared memory per WA CTA
 
 // accumulator slots (FP64 sums written by the kernels)
@@ -280,8 +285,11 @@ struct DetRed {
     int cap;            // capacity in blocks
 };
 
+// add: the deterministic total is added to acc[q] instead of stored there
+// (for a second kernel on the same stream that reduces into the same
+// quantities after the first).
 __device__ __forceinline__ void reduce2(float a, float b, double* acc, int qa, int qb,
-                                        const DetRed& dr) {
+                                        const DetRed& dr, bool add = false) {
     if (!dr.part) {
         block_acc2(a, b, acc, qa, qb);
         return;
@@ -324,8 +332,8 @@ __device__ __forceinline__ void reduce2(float a, float b, double* acc, int qa, i
     if (threadIdx.x == 0) {
         double fa = 0.0, fb = 0.0;
         for (int k = 0; k < nw; ++k) { fa += s_a[k]; fb += s_b[k]; }
-        if (qa >= 0) acc[qa] = fa;
-        if (qb >= 0) acc[qb] = fb;
+        if (qa >= 0) acc[qa] = add ? acc[qa] + fa : fa;
+        if (qb >= 0) acc[qb] = add ? acc[qb] + fb : fb;
         __threadfence();
     }
 }
@@ -388,6 +396,8 @@ struct Ctx {
     // pins re-laid into degree slabs (see k_wire.cu): slot base + 32 k + lane
     int4* slabs = nullptr;      // {base slot, degree, net count, 0}
     int nslabs = 0;
+    int nbig = 0;               // the first nbig slabs: degree kBigMin..kBigMax (k_wa_big)
+    int big_dmax = 0;           // their largest degree
     int num_sms = 1;            // of the handle's device
     int64_t slab_slots = 0;
     int32_t *pin_cell = nullptr, *pin_slot = nullptr, *cell_pin_ptr = nullptr;
@@ -455,6 +465,8 @@ void set_global_error(const std::string& msg);
 // ------------------------------------------------------------ launchers
 // (each returns the CUDA error of the launch)
 void prepare_spectral(int logn);
+// shared-memory opt-in of the WA kernels for this handle (create time)
+cudaError_t prepare_wa(const Ctx& c);
 cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* w,
                            const float* h, int m, float* D, long long* Dq, cudaStream_t s);
 // movable cells into the handle's D / Dq; write_pos: also the interleaved

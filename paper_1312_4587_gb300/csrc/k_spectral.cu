@@ -205,8 +205,13 @@ __device__ __forceinline__ float2 pack_inv(float c1u, float c1nu, float c2u, flo
 
 // -------------------------------------------------------- pass 1: rows
 // CTA: 8 rows of rho (2 per complex buffer).  Writes T1[u][y0..y0+7].
+// At most 96 registers below n = 4096 (it needs no more): two blocks leave
+// room on the SM for a block of the concurrent WA kernel (measured 2 %
+// faster steps than with 128).  At n = 4096 the four buffers (139 KB) allow
+// one block per SM in every pass, which may then use all its registers
+// instead of spilling.
 template <int LOGN, bool QUANT>
-__global__ void __launch_bounds__(kSpecThreads, 2)
+__global__ void __maxnreg__(LOGN >= 12 ? 255 : 96)
 k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
            const float* __restrict__ M, float inv_ab, float cap, float* __restrict__ T1,
            const float2* __restrict__ tw, const float2* __restrict__ ph, double* __restrict__ acc,
@@ -315,7 +320,7 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
 // w_v Psi, via reversed coefficients).  Each complex IFFT carries the same
 // quantity for two rows (P with P, R with R), so both parts share a scale.
 template <int LOGN>
-__global__ void __launch_bounds__(kSpecThreads, 2)
+__global__ void __launch_bounds__(kSpecThreads, LOGN >= 12 ? 1 : 2)
 k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__ RT,
        const float2* __restrict__ tw, const float2* __restrict__ ph, float pi_lx, float pi_ly,
        float eps, double* __restrict__ acc, DetRed dr) {
@@ -445,7 +450,7 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
 // memory.  Round B: E_x (sine sum of w_u P) for two rows per IFFT, written
 // with E_y as the interleaved field map E2[y][x] = (E_x, E_y).
 template <int LOGN>
-__global__ void __launch_bounds__(kSpecThreads, 2)
+__global__ void __launch_bounds__(kSpecThreads, LOGN >= 12 ? 1 : 2)
 k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __restrict__ psi,
            float2* __restrict__ E2, const float2* __restrict__ tw, const float2* __restrict__ ph,
            float pi_lx) {

@@ -296,6 +296,144 @@ k_wa(int nslabs, int pairs, const int4* __restrict__ slabs, WaIo io, float gamma
     reduce2(wsum, hsum, acc, ACC_W, ACC_HPWL, dr);
 }
 
+// ------------------------------------------------ slabs of degree 7..64
+// One warp per slab.  The slab's pin records (32 d words per field, the
+// warp's own lanes' slots) are copied into the warp's share of shared memory
+// with asynchronous 4-byte copies, all of them in flight at once; the
+// cell-centre gathers then go out kGather at a time and the pin coordinates
+// replace the offsets in shared memory, where the exponential sums and the
+// gradients read them.  So a slab costs about three memory latencies
+// whatever its degree, where the register path's loop over d pins would pay
+// one per few pins.  The per-net arithmetic is that of wa_net_any, pin by
+// pin in the same order.
+constexpr int kGather = 8;
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <bool CSR, bool LSE>
+__device__ __forceinline__ void wa_net_big(const WaIo& io, int d, const int* sc, float* sx,
+                                           float* sy, const int* sq, int lane, float l2g,
+                                           float inv_g, float& wsum, float& hsum) {
+    float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
+    for (int k0 = 0; k0 < d; k0 += kGather) {
+        float2 g[kGather];
+#pragma unroll
+        for (int t = 0; t < kGather; ++t) {
+            g[t] = make_float2(0.0f, 0.0f);
+            if (k0 + t < d) {
+                const int c = sc[32 * (k0 + t) + lane];
+                if (c >= 0) g[t] = __ldg(io.pos + c);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kGather; ++t) {
+            if (k0 + t < d) {
+                const int i = 32 * (k0 + t) + lane;
+                const float px = __fadd_rn(g[t].x, sx[i]), py = __fadd_rn(g[t].y, sy[i]);
+                sx[i] = px;
+                sy[i] = py;
+                Mx = fmaxf(Mx, px); mx = fminf(mx, px);
+                My = fmaxf(My, py); my = fminf(my, py);
+            }
+        }
+    }
+    float Spx = 0, Tpx = 0, Smx = 0, Tmx = 0, Spy = 0, Tpy = 0, Smy = 0, Tmy = 0;
+#pragma unroll 4
+    for (int k = 0; k < d; ++k) {
+        const int i = 32 * k + lane;
+        float tpx = sx[i] - Mx, tmx = sx[i] - mx, tpy = sy[i] - My, tmy = sy[i] - my;
+        float apx = exp2f(tpx * l2g), amx = exp2f(-tmx * l2g);
+        float apy = exp2f(tpy * l2g), amy = exp2f(-tmy * l2g);
+        Spx += apx; Tpx = fmaf(tpx, apx, Tpx); Smx += amx; Tmx = fmaf(tmx, amx, Tmx);
+        Spy += apy; Tpy = fmaf(tpy, apy, Tpy); Smy += amy; Tmy = fmaf(tmy, amy, Tmy);
+    }
+    const float isx = __fdividef(1.0f, Spx), imx = __fdividef(1.0f, Smx);
+    const float isy = __fdividef(1.0f, Spy), imy = __fdividef(1.0f, Smy);
+    const float Wpx = Tpx * isx, Wmx = Tmx * imx, Wpy = Tpy * isy, Wmy = Tmy * imy;
+    const float span = (Mx - mx) + (My - my);
+    hsum += span;
+    if (LSE)
+        wsum += span + __fdividef(1.0f, inv_g) * ((logf(Spx) + logf(Smx)) +
+                                                  (logf(Spy) + logf(Smy)));
+    else
+        wsum += span + ((Wpx - Wmx) + (Wpy - Wmy));
+    const float P0x = isx * fmaf(-Wpx, inv_g, 1.0f), P1x = isx * inv_g;
+    const float Q0x = imx * fmaf(Wmx, inv_g, 1.0f), Q1x = imx * inv_g;
+    const float P0y = isy * fmaf(-Wpy, inv_g, 1.0f), P1y = isy * inv_g;
+    const float Q0y = imy * fmaf(Wmy, inv_g, 1.0f), Q1y = imy * inv_g;
+#pragma unroll 4
+    for (int k = 0; k < d; ++k) {
+        const int i = 32 * k + lane;
+        float tpx = sx[i] - Mx, tmx = sx[i] - mx, tpy = sy[i] - My, tmy = sy[i] - my;
+        float gxj, gyj;
+        if (LSE) {
+            gxj = exp2f(tpx * l2g) * isx - exp2f(-tmx * l2g) * imx;
+            gyj = exp2f(tpy * l2g) * isy - exp2f(-tmy * l2g) * imy;
+        } else {
+            gxj = exp2f(tpx * l2g) * fmaf(tpx, P1x, P0x) - exp2f(-tmx * l2g) * fmaf(-tmx, Q1x, Q0x);
+            gyj = exp2f(tpy * l2g) * fmaf(tpy, P1y, P0y) - exp2f(-tmy * l2g) * fmaf(-tmy, Q1y, Q0y);
+        }
+        if (CSR) {
+            const int q = sq[i];
+            if (q >= 0) io.gpin[q] = make_float2(gxj, gyj);
+        } else {
+            const int c = sc[i];
+            if (c >= 0) red_add_f2(io.gW + c, gxj, gyj);
+        }
+    }
+}
+
+// Shared memory of one warp of k_wa_big: (3 or, with the deterministic
+// slots, 4) fields x 32 lanes x dmax words.
+__host__ __device__ inline size_t big_warp_words(bool csr, int dmax) {
+    return (csr ? 4 : 3) * 32 * (size_t)dmax;
+}
+
+template <bool CSR, bool LSE>
+__global__ void __launch_bounds__(kBigWarps * 32)
+k_wa_big(int nbig, int dmax, const int4* __restrict__ slabs, WaIo io, float gamma,
+         const double* __restrict__ gamma_dev, double* __restrict__ acc,
+         const double* __restrict__ done, DetRed dr) {
+    extern __shared__ __align__(16) int wa_sm[];
+    if (done && *done != 0.0) return;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * kBigWarps + wib;
+    if (gamma_dev) gamma = (float)*gamma_dev;
+    const float inv_g = 1.0f / gamma;
+    const float l2g = (float)(1.4426950408889634 / (double)gamma);
+    float wsum = 0.0f, hsum = 0.0f;
+    if (warp < nbig) {
+        const int4 sl = slabs[warp];
+        const int d = sl.y, w32 = 32 * dmax;
+        int* sc = wa_sm + (size_t)wib * big_warp_words(CSR, dmax);
+        float* sx = reinterpret_cast<float*>(sc + w32);
+        float* sy = reinterpret_cast<float*>(sc + 2 * w32);
+        int* sq = sc + 3 * w32;   // deterministic mode only
+        // every lane copies (and later reads) only its own slots; the slab
+        // has all 32 lanes' slots (padding: cell -1, offsets 0)
+        for (int k = 0; k < d; ++k) {
+            const int slot = sl.x + 32 * k + lane, i = 32 * k + lane;
+            cp_async4(sc + i, io.pin_cell + slot);
+            cp_async4(sx + i, io.pin_dx + slot);
+            cp_async4(sy + i, io.pin_dy + slot);
+            if (CSR) cp_async4(sq + i, io.pin_slot + slot);
+        }
+        cp_async_wait_all();
+        if (lane < sl.z) wa_net_big<CSR, LSE>(io, d, sc, sx, sy, sq, lane, l2g, inv_g, wsum, hsum);
+    }
+    // after k_wa on the same stream: add to its totals
+    reduce2(wsum, hsum, acc, ACC_W, ACC_HPWL, dr, true);
+}
+
 // Per-cell kernel: density gradient by the field gather (q.E of Eq. 7),
 // wirelength gradient by summing the cell's pin gradients (CSR mode) or
 // reading the atomically accumulated sums, and the L1 norms of both.
@@ -377,7 +515,24 @@ static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }
 // Slab pairs per warp once a warp per slab would fill the GPU about twice
 // over (4 CTAs of 8 warps per SM); below that, one slab per warp.
 int wa_pairs(const Ctx& c) {
-    return c.nslabs >= 2LL * c.num_sms * 4 * (kWaThreads / 32) ? 1 : 0;
+    return (c.nslabs - c.nbig) >= 2LL * c.num_sms * 4 * (kWaThreads / 32) ? 1 : 0;
+}
+
+cudaError_t prepare_wa(const Ctx& c) {
+    if (c.nbig <= 0) return cudaSuccess;
+    // the opt-in is per kernel, not per handle: always the largest any
+    // handle can ask for, so that no later handle lowers it under another
+    const int bytes = (int)(kBigWarps * big_warp_words(true, kBigMax) * 4);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess) e = r;
+    };
+    set((const void*)k_wa_big<false, false>);
+    set((const void*)k_wa_big<false, true>);
+    set((const void*)k_wa_big<true, false>);
+    set((const void*)k_wa_big<true, true>);
+    return e;
 }
 
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
@@ -391,22 +546,44 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
     }
     const WaIo io{c.pin_cell, c.pin_dx, c.pin_dy, c.pos2, c.pxy,
                   c.opt.deterministic ? nullptr : c.gW2, c.pin_slot, c.gpin};
-    const int wpb = kWaThreads / 32;
-    const int pairs = wa_pairs(c);
-    int nb = nblk(pairs ? (c.nslabs + 1) / 2 : c.nslabs, wpb);
     const bool lse = c.opt.wirelength == FFTPL_WL_LSE;
-    auto go = [&](auto kern) {
-        kern<<<nb, kWaThreads, 0, s>>>(c.nslabs, pairs, c.slabs, io, gamma, gamma_dev, c.acc,
-                                       done, det_red(c, 1));
-    };
-    if (c.opt.deterministic) {
-        if (lse) go(k_wa<true, true>);
-        else go(k_wa<true, false>);
-    } else {
-        if (lse) go(k_wa<false, true>);
-        else go(k_wa<false, false>);
+    const bool det = c.opt.deterministic != 0;
+    // k_wa: the slabs after the first nbig (degree 2..6 and above kBigMax);
+    // it stores the deterministic totals, k_wa_big (next, same stream) adds
+    const int nsmall = c.nslabs - c.nbig;
+    if (nsmall > 0) {
+        const int wpb = kWaThreads / 32;
+        const int pairs = wa_pairs(c);
+        const int nb = std::max(1, nblk(pairs ? (nsmall + 1) / 2 : nsmall, wpb));
+        auto go = [&](auto kern) {
+            kern<<<nb, kWaThreads, 0, s>>>(nsmall, pairs, c.slabs + c.nbig, io, gamma, gamma_dev,
+                                           c.acc, done, det_red(c, 1));
+        };
+        if (det) {
+            if (lse) go(k_wa<true, true>);
+            else go(k_wa<true, false>);
+        } else {
+            if (lse) go(k_wa<false, true>);
+            else go(k_wa<false, false>);
+        }
+        c.launches++;
     }
-    c.launches++;
+    if (c.nbig > 0) {
+        const size_t smem = kBigWarps * big_warp_words(det, c.big_dmax) * 4;
+        const int nb = nblk(c.nbig, kBigWarps);
+        auto go = [&](auto kern) {
+            kern<<<nb, kBigWarps * 32, smem, s>>>(c.nbig, c.big_dmax, c.slabs, io, gamma,
+                                                  gamma_dev, c.acc, done, det_red(c, 1));
+        };
+        if (det) {
+            if (lse) go(k_wa_big<true, true>);
+            else go(k_wa_big<true, false>);
+        } else {
+            if (lse) go(k_wa_big<false, true>);
+            else go(k_wa_big<false, false>);
+        }
+        c.launches++;
+    }
     return cudaGetLastError();
 }
 
