@@ -551,7 +551,12 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     TRY(dalloc(c, &c.pin_cell, ns));
     TRY(dalloc(c, &c.pin_dx, ns));
     TRY(dalloc(c, &c.pin_dy, ns));
-    TRY(dalloc(c, &c.pxy, ns));
+    // pxy: scratch of the runtime-degree WA body, which only the slabs above
+    // kBigMax use; slots go out heaviest first, so theirs are [0, hi_slots)
+    int64_t hi_slots = 0;
+    for (const int4& sl : slabs)
+        if (sl.y > kBigMax) hi_slots += 32LL * sl.y;
+    TRY(dalloc(c, &c.pxy, (size_t)std::max<int64_t>(hi_slots, 1)));
     if (c.opt.deterministic) TRY(dalloc(c, &c.pin_slot, ns));
     if (!slabs.empty())
         CK(cudaMemcpyAsync(c.slabs, slabs.data(), slabs.size() * sizeof(int4),

@@ -405,7 +405,8 @@ struct Ctx {
     float2* gpin = nullptr;
     float2* gW2 = nullptr;      // interleaved wirelength gradient accumulator (m_mov),
                                 // by internal number
-    float2* pxy = nullptr;      // pin coordinates in slab order (slab_slots)
+    float2* pxy = nullptr;      // pin coordinates by slot, for the slabs of degree
+                                // above kBigMax (their slots come first)
     float2* pos2 = nullptr;     // interleaved cell centres (m_mov), by internal number
     int32_t* cell_rank = nullptr;  // internal number of each movable cell (m_mov)
     // deterministic reductions: region 0 for the main stream, 1 for WA

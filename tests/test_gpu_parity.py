@@ -173,6 +173,57 @@ def test_wa_alone(F):
                    np.concatenate([ref["gcx"], ref["gcy"]])) < TOL_MAP
 
 
+def degree_instance(seed=11):
+    """Nets of every degree at the boundaries of the WA kernel's bodies (2..6
+    in registers, 7..64 in the shared-memory kernel, above 64 the
+    runtime-degree path), 70 nets of each (several slabs, one ragged), with
+    pins on fixed cells and non-zero offsets."""
+    rng = np.random.default_rng(seed)
+    base = synth.make_instance("tiny")
+    m, nf = base.m_mov, 5
+    L = base.region[2]
+    base.m_fix = nf
+    base.fix_x = rng.uniform(0.1 * L, 0.9 * L, nf).astype(np.float32)
+    base.fix_y = rng.uniform(0.1 * L, 0.9 * L, nf).astype(np.float32)
+    base.w = np.concatenate([base.w[:m], np.full(nf, 2.0, np.float32)])
+    base.h = np.concatenate([base.h[:m], np.full(nf, 2.0, np.float32)])
+    net_ptr, pc = [0], []
+    for d in [2, 3, 5, 6, 7, 8, 33, 63, 64, 65, 100, 300]:
+        for _ in range(70):
+            cells = rng.choice(m + nf, d, replace=False)
+            pc += list(cells); net_ptr.append(len(pc))
+    pc = np.array(pc, np.int32)
+    base.net_ptr = np.array(net_ptr, np.int32)
+    base.pin_cell = pc
+    base.pin_dx = rng.uniform(-0.4, 0.4, pc.size).astype(np.float32)
+    base.pin_dy = rng.uniform(-0.4, 0.4, pc.size).astype(np.float32)
+    return base
+
+
+@pytest.mark.parametrize("det", [0, 1])
+@pytest.mark.parametrize("model", ["wa", "lse"])
+def test_wa_degree_boundaries(F, det, model):
+    import torch
+    inst = degree_instance()
+    wl = oracle.WL_WA if model == "wa" else oracle.WL_LSE
+    ref = oracle.wa(inst.net_ptr, inst.pin_cell, inst.pin_dx, inst.pin_dy, inst.m_mov,
+                    inst.x, inst.y, inst.gamma, inst.fix_x, inst.fix_y, model=wl)
+    opts = dict(deterministic=det, wirelength=F.FFTPL_WL_WA if model == "wa" else F.FFTPL_WL_LSE)
+    with F.Problem(inst, **opts) as p:
+        gx = torch.empty(inst.m_mov, device="cuda"); gy = torch.empty_like(gx)
+        W = F.fftpl_wa(p.h, cuda(inst.x), cuda(inst.y), inst.gamma, gx, gy)
+        rep = F.fftpl_report(p.h)
+        # the full evaluation takes the same kernels beside the density chain
+        g = [torch.empty_like(gx) for _ in range(4)]
+        rep2 = F.fftpl_eval(p.h, cuda(inst.x), cuda(inst.y), inst.gamma, *g)
+    assert abs(W - ref["W"]) / ref["W"] < 1e-6
+    assert abs(rep["hpwl"] - ref["hpwl"]) / ref["hpwl"] < 1e-6
+    want = np.concatenate([ref["gcx"], ref["gcy"]])
+    assert rel(np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()]), want) < TOL_MAP
+    assert abs(rep2["W"] - ref["W"]) / ref["W"] < 1e-6
+    assert rel(np.concatenate([g[2].cpu().numpy(), g[3].cpu().numpy()]), want) < TOL_MAP
+
+
 def test_adjoint_parity(F):
     import torch
     inst = synth.make_instance("medium")
