@@ -5,6 +5,8 @@
 //   main stream: zero sums, zero D, scatter -> rows_fwd -> cols -> rows_inv
 //   side stream: (zero gW) -> WA                       (forked, concurrent)
 //   main stream: join -> cells (gather + pin sums + norms)
+// (with host outputs the WA branch writes grad W~ itself and the main
+// stream ends with the field gather before the join)
 // and, when use_graphs is set, is replayed from a captured CUDA graph.
 #include <math.h>
 #include <string.h>
@@ -227,7 +229,8 @@ cudaError_t launch_tau(Ctx& c, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- evaluation
-enum { EV_DENSITY = 1, EV_WA = 2, EV_ADJOINT = 4, EV_NO_GATHER = 8 };
+// EV_HOST: the gradient arrays are pinned host memory written over the link
+enum { EV_DENSITY = 1, EV_WA = 2, EV_ADJOINT = 4, EV_NO_GATHER = 8, EV_HOST = 16 };
 
 // Enqueues one evaluation; gradients must be non-null device arrays.
 // stage (2 m_mov floats, or null): x, y may be pinned host memory; the
@@ -240,9 +243,16 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
     size_t nn = (size_t)c.n * c.n;
     CK(cudaMemsetAsync(c.acc, 0, kAccDoubles * sizeof(double), s));
     bool dens = (what & EV_DENSITY) != 0, wa = (what & EV_WA) != 0;
+    const bool grads = !(what & EV_NO_GATHER);
     // with both branches the scatter also writes the WA kernel's positions,
-    // and the WA branch forks after it
+    // and the WA branch forks after it.  Device outputs: after the join one
+    // cell kernel writes both gradients (measured 18 % faster than a
+    // separate WA gradient pass beside the chain).  Host outputs (and the
+    // other combinations): the WA branch ends with its own gradient pass, so
+    // that its writes over the host link overlap the density chain (5 %
+    // faster end to end).
     const bool pos_from_scatter = dens && wa;
+    const bool fused = dens && wa && grads && !(what & (EV_ADJOINT | EV_HOST));
     auto wa_branch = [&](bool interleave) -> fftpl_status {
         CK(cudaEventRecord(c.ev_fork, s));
         CK(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
@@ -251,6 +261,7 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
             if (!c.opt.deterministic)
                 CK(cudaMemsetAsync(c.gW2, 0, (size_t)c.m_mov * sizeof(float2), c.side));
             CK(launch_wa_impl(c, x, y, gamma, nullptr, nullptr, interleave, c.side));
+            if (grads && !fused) CK(launch_pin_sum(c, gWx, gWy, c.side));
         }
         CK(cudaEventRecord(c.ev_join, c.side));
         return FFTPL_OK;
@@ -266,18 +277,18 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
         if (pos_from_scatter) TRY(wa_branch(false));
         TRY(enqueue_solve(c, s));
     }
-    if (wa) CK(cudaStreamWaitEvent(s, c.ev_join, 0));
-    if (!(what & EV_NO_GATHER)) {
+    const float* xs = stage ? stage : x;
+    const float* ys = stage ? stage + c.m_mov : y;
+    if (fused) {
+        CK(cudaStreamWaitEvent(s, c.ev_join, 0));
         Stage st(c, 5, s);
-        if (dens && wa && !(what & EV_ADJOINT)) {
-            CK(launch_cells(c, stage ? stage : x, stage ? stage + c.m_mov : y, gNx, gNy, gWx,
-                            gWy, s));
-        } else {
-            if (dens)
-                CK(launch_gather(c, stage ? stage : x, stage ? stage + c.m_mov : y, gNx, gNy,
-                                 (what & EV_ADJOINT) != 0, s));
-            if (wa) CK(launch_pin_sum(c, gWx, gWy, s));
+        CK(launch_cells(c, xs, ys, gNx, gNy, gWx, gWy, s));
+    } else {
+        if (dens && grads) {
+            Stage st(c, 5, s);
+            CK(launch_gather(c, xs, ys, gNx, gNy, (what & EV_ADJOINT) != 0, s));
         }
+        if (wa) CK(cudaStreamWaitEvent(s, c.ev_join, 0));
     }
     c.rho_valid = false;
     c.split_valid = false;
@@ -677,6 +688,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
         long long cap1 = std::max<long long>(
             ((long long)(c.nslabs - c.nbig) + kWaThreads / 32 - 1) / (kWaThreads / 32),
             ((long long)c.nbig + kBigWarps - 1) / kBigWarps);
+        cap1 = std::max<long long>(cap1, ((long long)c.m_mov + kCellThreads - 1) / kCellThreads);
         c.det_cap[0] = (int)std::max<long long>(cap0, 1);
         c.det_cap[1] = (int)std::max<long long>(cap1, 1);
         TRY(dalloc(c, &c.det_part, 2 * ((size_t)c.det_cap[0] + c.det_cap[1])));
@@ -821,6 +833,8 @@ fftpl_status fftpl_wa(fftpl_t h, const float* x, const float* y, float gamma, do
 // (the graph is keyed by the buffers, gamma and the staging buffer).
 static fftpl_status eval_impl(Ctx& c, const float* x, const float* y, float gamma, float* gNx,
                               float* gNy, float* gWx, float* gWy, float* stage) {
+    // a staging buffer means x, y and the gradients are pinned host memory
+    const int what = EV_DENSITY | EV_WA | (stage ? EV_HOST : 0);
     if (c.opt.use_graphs && !c.profiling) {
         float gk = gamma;
         const void* key[8] = {x, y, gNx, gNy, gWx, gWy, nullptr, stage};
@@ -833,8 +847,7 @@ static fftpl_status eval_impl(Ctx& c, const float* x, const float* y, float gamm
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
             int64_t before = c.launches;
-            fftpl_status st =
-                enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy, stage);
+            fftpl_status st = enqueue_eval(c, x, y, gamma, what, gNx, gNy, gWx, gWy, stage);
             cudaError_t ee = cudaStreamEndCapture(c.stream, &g);
             if (st != FFTPL_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -855,7 +868,7 @@ static fftpl_status eval_impl(Ctx& c, const float* x, const float* y, float gamm
         c.split_valid = false;
         return FFTPL_OK;
     }
-    return enqueue_eval(c, x, y, gamma, EV_DENSITY | EV_WA, gNx, gNy, gWx, gWy, stage);
+    return enqueue_eval(c, x, y, gamma, what, gNx, gNy, gWx, gWy, stage);
 }
 
 fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma, float* gNx,

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kCellThreads)
 k_gather(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
          const float* __restrict__ w, const float* __restrict__ h, const float* __restrict__ fx,
          const float2* __restrict__ E2, float* __restrict__ gx, float* __restrict__ gy,
-         double* __restrict__ acc) {
+         double* __restrict__ acc, DetRed dr) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float sx = 0.0f, sy = 0.0f;
     if (i < m) {
@@ -123,7 +123,7 @@ k_gather(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y
         gx[i] = sx;
         gy[i] = sy;
     }
-    block_acc1(fabsf(sx) + fabsf(sy), acc, ACC_GN_L1);
+    reduce2(fabsf(sx) + fabsf(sy), 0.0f, acc, ACC_GN_L1, -1, dr);
 }
 
 // rho = (D + M) / A_b (formed on demand for fftpl_fields).
@@ -201,10 +201,10 @@ cudaError_t launch_gather(Ctx& c, const float* x, const float* y, float* gx, flo
     int nb = blocks_for(c.m_mov, kCellThreads);
     if (adjoint)
         k_gather<true><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, c.psi, nullptr,
-                                                  gx, gy, c.acc);
+                                                  gx, gy, c.acc, det_red(c, 0));
     else
         k_gather<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, x, y, c.w, c.h, nullptr, c.E2,
-                                                   gx, gy, c.acc);
+                                                   gx, gy, c.acc, det_red(c, 0));
     c.launches++;
     return cudaGetLastError();
 }

@@ -479,7 +479,7 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
 __global__ void __launch_bounds__(kCellThreads)
 k_pin_sum(int m, const int* __restrict__ rank, const int* __restrict__ cell_pin_ptr,
           const float2* __restrict__ gpin, float* __restrict__ gx, float* __restrict__ gy,
-          double* __restrict__ acc) {
+          double* __restrict__ acc, DetRed dr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float wx = 0.0f, wy = 0.0f;
     if (i < m) {
@@ -492,13 +492,13 @@ k_pin_sum(int m, const int* __restrict__ rank, const int* __restrict__ cell_pin_
         gx[i] = wx;
         gy[i] = wy;
     }
-    block_acc1(fabsf(wx) + fabsf(wy), acc, ACC_GW_L1);
+    reduce2(fabsf(wx) + fabsf(wy), 0.0f, acc, ACC_GW_L1, -1, dr);
 }
 
 // Splits the interleaved atomic accumulator into gx, gy and adds ||g||_1.
 __global__ void __launch_bounds__(kCellThreads)
 k_split(int m, const int* __restrict__ rank, const float2* __restrict__ gW2,
-        float* __restrict__ gx, float* __restrict__ gy, double* __restrict__ acc) {
+        float* __restrict__ gx, float* __restrict__ gy, double* __restrict__ acc, DetRed dr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float v = 0.0f;
     if (i < m) {
@@ -507,7 +507,7 @@ k_split(int m, const int* __restrict__ rank, const float2* __restrict__ gW2,
         gy[i] = g.y;
         v = fabsf(g.x) + fabsf(g.y);
     }
-    block_acc1(v, acc, ACC_GW_L1);
+    reduce2(v, 0.0f, acc, ACC_GW_L1, -1, dr);
 }
 
 static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }
@@ -593,12 +593,13 @@ cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, cudaS
 
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s) {
     if (c.m_mov <= 0) return cudaSuccess;
+    // region 1: this pass follows the WA kernels on their stream
     if (c.opt.deterministic)
         k_pin_sum<<<nblk(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
-            c.m_mov, c.cell_rank, c.cell_pin_ptr, c.gpin, gx, gy, c.acc);
+            c.m_mov, c.cell_rank, c.cell_pin_ptr, c.gpin, gx, gy, c.acc, det_red(c, 1));
     else
-        k_split<<<nblk(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(c.m_mov, c.cell_rank,
-                                                                    c.gW2, gx, gy, c.acc);
+        k_split<<<nblk(c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
+            c.m_mov, c.cell_rank, c.gW2, gx, gy, c.acc, det_red(c, 1));
     c.launches++;
     return cudaGetLastError();
 }
