@@ -51,16 +51,18 @@ STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "ce
 
 # DRAM traffic per stage launch on the 2.2M-cell instance, dram__bytes_read.sum
 # + dram__bytes_write.sum of the stage's kernels from one ncu --set full
-# capture (profiles/eval_precision_kernels.md), valid only while the kernel
+# capture of this script (its summary is kept under profiles/), valid only
+# while the kernel
 # source it was taken from is unchanged: key = first 16 hex digits of the
 # SHA-256 of the kernel file followed by fftpl_internal.cuh.
 STAGE_TRAFFIC = {
-    "scatter": ("k_density.cu", "9456c81802a6adda", 50687232 + 824320),
-    "rows_fwd": ("k_spectral.cu", "e88bb1bf4172a223", 33650176 + 1024),
-    "cols": ("k_spectral.cu", "e88bb1bf4172a223", 17544448 + 669184),
-    "rows_inv": ("k_spectral.cu", "e88bb1bf4172a223", 33645056 + 2180608),
-    "wa": ("k_wire.cu", "549a2ada1712c5eb", 137156608 + 19534848),
-    "cells": ("k_wire.cu", "549a2ada1712c5eb", 76274176 + 12669184),
+    "scatter": ("k_density.cu", "c99b39f6e1ec279f", 50680576 + 631808),
+    "rows_fwd": ("k_spectral.cu", "a2431570c7720e47", 33652992 + 256),
+    "cols": ("k_spectral.cu", "a2431570c7720e47", 17423104 + 751872),
+    "rows_inv": ("k_spectral.cu", "a2431570c7720e47", 33645824 + 2244608),
+    # k_wa and k_wa_big
+    "wa": ("k_wire.cu", "f680768acafcc601", 103064832 + 3850240 + 65444352 + 514048),
+    "cells": ("k_wire.cu", "f680768acafcc601", 76414720 + 14316800),
 }
 
 
