@@ -168,6 +168,16 @@ def barrier(ws):
         dist.barrier()
 
 
+def run_config(inst, args, ws):
+    """The workload of a bench line (the same for both arms)."""
+    m, n = inst.m_mov, inst.n
+    E, P = inst.E, inst.P
+    return {"workload": f"{inst.name}: {m} cells, {E} nets, {P} pins, {inst.m_fix} macros, "
+                        f"{n}x{n} bins", "solve_path": "fft", "graphs": not args.no_graphs,
+            "l2": "flushed before each timed step (256 MiB write)",
+            "parallelism": f"replicas x{ws}"}
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -192,10 +202,9 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "precision: 2.2M cells, 2.3M nets, 150 macros, 2048x2048 bins",
-                   "sample": "one full FP64 oracle evaluation per step"},
+        "config": run_config(inst, args, ws),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "one full evaluation of the 2.2M-cell / 2048^2 instance per step"},
+                         "sample": "one full FP64 oracle evaluation of the same instance per step"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -480,10 +489,7 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{inst.name}: {m} cells, {E} nets, {P} pins, {inst.m_fix} macros, "
-                               f"{n}x{n} bins", "solve_path": "fft", "graphs": not args.no_graphs,
-                   "l2": "flushed before each timed step (256 MiB write)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": run_config(inst, args, ws),
         "gpu_launches": int(launches),
         "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * m,
                 "d2h_bytes_per_step": 16 * m + 64},
