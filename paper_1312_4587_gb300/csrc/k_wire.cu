@@ -450,13 +450,9 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float nx = 0.0f, ny = 0.0f, wx = 0.0f, wy = 0.0f;
     if (i < m) {
-        Span s = cell_span(g, x[i], y[i], w[i], h[i]);
-        float2 e = gather_span(g, s, E2);
-        nx = -e.x;
-        ny = -e.y;
-        gNx[i] = nx;
-        gNy[i] = ny;
+        // the wirelength gradient's loads go out before the field gather's
         const int r = rank[i];
+        Span s = cell_span(g, x[i], y[i], w[i], h[i]);
         if (CSR) {
             int q0 = cell_pin_ptr[r], q1 = cell_pin_ptr[r + 1];
             for (int q = q0; q < q1; ++q) {
@@ -469,6 +465,11 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
             wx = v.x;
             wy = v.y;
         }
+        float2 e = gather_span(g, s, E2);
+        nx = -e.x;
+        ny = -e.y;
+        gNx[i] = nx;
+        gNy[i] = ny;
         gWx[i] = wx;
         gWy[i] = wy;
     }
