@@ -611,6 +611,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     c.grid.hb = (float)c.hb;
     c.grid.inv_wb = (float)(1.0 / c.wb);
     c.grid.inv_hb = (float)(1.0 / c.hb);
+    c.grid.guard = (float)((n + 1) * ldexp(1.0, -20));
     c.mov_area = 0.0;
     for (int i = 0; i < c.m_mov; ++i) c.mov_area += (double)cells->w[i] * (double)cells->h[i];
     for (int e = 0; e < c.E; ++e)

@@ -69,9 +69,11 @@ enum { ERR_TIMEOUT = 1, ERR_BOUNDS = 2 };
 
 // Bin grid along both axes.  Edges e_k = x0 + k * wb are exact in float32
 // (checked at create), so comparisons against them decide indices exactly.
+// guard: see last_edge (1 = always take the exact comparisons).
 struct Grid {
     int n;
     float x0, y0, wb, hb, inv_wb, inv_hb;
+    float guard = 1.0f;
 };
 
 __device__ __forceinline__ float edge_at(float lo, float step, int k) {
@@ -79,12 +81,20 @@ __device__ __forceinline__ float edge_at(float lo, float step, int k) {
 }
 
 // Largest k in [-1, n] with e_k <= t (strict: e_k < t).  The float estimate
-// floor((t - x0) / w_b) is within one of the answer (its relative error is a
+// q = (t - x0) * (1/w_b) is within one of the answer (its relative error is a
 // few 2^-24 and the quotient is at most n + 1 after clamping), so one
 // comparison against the exact edges in each direction settles the index.
+// Fast path: where 0 <= floor(q) < n and q lies at least `guard` bins from
+// both neighbouring integers, floor(q) is the answer without comparisons:
+// the edges are exact and q differs from (t - x0) / w_b by at most
+// n 2^-22 bins there, below guard = (n + 1) 2^-20 (q - floor(q) is exact).
 template <bool STRICT>
-__device__ __forceinline__ int last_edge(float lo, float step, float inv, int n, float t) {
-    float kf = floorf(__fmul_rn(__fsub_rn(t, lo), inv));
+__device__ __forceinline__ int last_edge(float lo, float step, float inv, float guard, int n,
+                                         float t) {
+    const float q = __fmul_rn(__fsub_rn(t, lo), inv);
+    float kf = floorf(q);
+    const float fr = q - kf;
+    if (kf >= 0.0f && kf < (float)n && fr >= guard && fr <= 1.0f - guard) return (int)kf;
     int k;
     if (!(kf >= -1.0f)) k = -1;          // also catches NaN
     else if (kf > (float)n) k = n;
@@ -112,10 +122,10 @@ __device__ __forceinline__ Span cell_span(const Grid& g, float x, float y, float
     s.xh = __fadd_rn(x, hw);
     s.yl = __fsub_rn(y, hh);
     s.yh = __fadd_rn(y, hh);
-    s.ilo = max(last_edge<false>(g.x0, g.wb, g.inv_wb, g.n, s.xl), 0);
-    s.ihi = min(last_edge<true>(g.x0, g.wb, g.inv_wb, g.n, s.xh), g.n - 1);
-    s.jlo = max(last_edge<false>(g.y0, g.hb, g.inv_hb, g.n, s.yl), 0);
-    s.jhi = min(last_edge<true>(g.y0, g.hb, g.inv_hb, g.n, s.yh), g.n - 1);
+    s.ilo = max(last_edge<false>(g.x0, g.wb, g.inv_wb, g.guard, g.n, s.xl), 0);
+    s.ihi = min(last_edge<true>(g.x0, g.wb, g.inv_wb, g.guard, g.n, s.xh), g.n - 1);
+    s.jlo = max(last_edge<false>(g.y0, g.hb, g.inv_hb, g.guard, g.n, s.yl), 0);
+    s.jhi = min(last_edge<true>(g.y0, g.hb, g.inv_hb, g.guard, g.n, s.yh), g.n - 1);
     return s;
 }
 

@@ -100,10 +100,10 @@ k_gather(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y
             sy = -e.y;
         } else if (s.ilo <= s.ihi && s.jlo <= s.jhi) {
             int n = g.n;
-            int kl = last_edge<false>(g.x0, g.wb, g.inv_wb, n, s.xl);
-            int kr = last_edge<false>(g.x0, g.wb, g.inv_wb, n, s.xh);
-            int jl = last_edge<false>(g.y0, g.hb, g.inv_hb, n, s.yl);
-            int jr = last_edge<false>(g.y0, g.hb, g.inv_hb, n, s.yh);
+            int kl = last_edge<false>(g.x0, g.wb, g.inv_wb, g.guard, n, s.xl);
+            int kr = last_edge<false>(g.x0, g.wb, g.inv_wb, g.guard, n, s.xh);
+            int jl = last_edge<false>(g.y0, g.hb, g.inv_hb, g.guard, n, s.yl);
+            int jr = last_edge<false>(g.y0, g.hb, g.inv_hb, g.guard, n, s.yh);
             bool kr_in = kr >= 0 && kr < n, kl_in = kl >= 0 && kl < n;
             bool jr_in = jr >= 0 && jr < n, jl_in = jl >= 0 && jl < n;
             for (int j = s.jlo; j <= s.jhi; ++j) {
