@@ -40,24 +40,30 @@ k_scatter(Grid g, int m, const float* __restrict__ x, const float* __restrict__ 
     if (s.ilo > s.ihi || s.jlo > s.jhi) return;
     const AxisOv ax = axis_ov(g.x0, g.wb, s.ilo, s.ihi, s.xl, s.xh);
     const AxisOv ay = axis_ov(g.y0, g.hb, s.jlo, s.jhi, s.yl, s.yh);
-    for (int j = s.jlo; j <= s.jhi; ++j) {
-        float oy = ov_at(ay, j);
-        if (QUANT) {
+    if (QUANT) {
+        for (int j = s.jlo; j <= s.jhi; ++j) {
+            float oy = ov_at(ay, j);
             for (int k = s.ilo; k <= s.ihi; ++k) {
                 float a = __fmul_rn(ov_at(ax, k), oy);
                 long long q = __float2ll_rn(__fmul_rn(a, 4294967296.0f));
                 atomicAdd(Dq + (size_t)j * g.n + k, (unsigned long long)q);
             }
-        } else {
-            float* row = D + (size_t)j * g.n;
-            for (int q = s.ilo >> 2; q <= (s.ihi >> 2); ++q) {
-                float v[4];
+        }
+    } else {
+        // quads outer, rows inner: a quad's four x overlaps serve every row
+        for (int q = s.ilo >> 2; q <= (s.ihi >> 2); ++q) {
+            float ox[4];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    int k = 4 * q + t;
-                    v[t] = (k >= s.ilo && k <= s.ihi) ? __fmul_rn(ov_at(ax, k), oy) : 0.0f;
-                }
-                atomicAdd(reinterpret_cast<float4*>(row + 4 * q), make_float4(v[0], v[1], v[2], v[3]));
+            for (int t = 0; t < 4; ++t) {
+                int k = 4 * q + t;
+                ox[t] = (k >= s.ilo && k <= s.ihi) ? ov_at(ax, k) : 0.0f;
+            }
+            float* col = D + 4 * q;
+            for (int j = s.jlo; j <= s.jhi; ++j) {
+                const float oy = ov_at(ay, j);
+                atomicAdd(reinterpret_cast<float4*>(col + (size_t)j * g.n),
+                          make_float4(__fmul_rn(ox[0], oy), __fmul_rn(ox[1], oy),
+                                      __fmul_rn(ox[2], oy), __fmul_rn(ox[3], oy)));
             }
         }
     }
