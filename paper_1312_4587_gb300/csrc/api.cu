@@ -94,6 +94,7 @@ void free_ctx(fftpl_ctx* c) {
     if (!c) return;
     if (c->stream || c->side) cudaDeviceSynchronize();
     if (c->eval_graph) cudaGraphExecDestroy(c->eval_graph);
+    if (c->loop_graph) cudaGraphExecDestroy(c->loop_graph);
     for (void* p : c->dev_allocs) cudaFree(p);
     tc_free(*c);
     if (c->acc_host) cudaFreeHost(c->acc_host);
@@ -1098,6 +1099,39 @@ fftpl_status fftpl::loop_enqueue(Ctx& c) {
     return FFTPL_OK;
 }
 
+// One loop iteration: replayed from a graph captured on first use when
+// use_graphs is set (every other input of the iteration lives on the device:
+// the control scalars, positions and the record counter).
+static fftpl_status loop_iter(Ctx& c) {
+    if (!c.opt.use_graphs || c.profiling) return loop_enqueue(c);
+    const void* key[3] = {c.recs, c.gN, c.gW};
+    if (!c.loop_graph || memcmp(key, c.loop_key, sizeof(key)) != 0) {
+        if (c.loop_graph) {
+            cudaGraphExecDestroy(c.loop_graph);
+            c.loop_graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        int64_t before = c.launches;
+        fftpl_status st = loop_enqueue(c);
+        cudaError_t ee = cudaStreamEndCapture(c.stream, &g);
+        if (st != FFTPL_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        CK(ee);
+        cudaError_t ie = cudaGraphInstantiate(&c.loop_graph, g, 0);
+        cudaGraphDestroy(g);
+        CK(ie);
+        memcpy(c.loop_key, key, sizeof(key));
+        c.loop_graph_nkernels = c.launches - before;
+        c.launches = before;  // counted at replay
+    }
+    CK(cudaGraphLaunch(c.loop_graph, c.stream));
+    c.launches += c.loop_graph_nkernels;
+    return FFTPL_OK;
+}
+
 fftpl_status fftpl::loop_records(Ctx& c, int cap, double base_k) {
     if (c.recs_cap < std::max(cap, 1)) {
         if (c.recs) {
@@ -1130,7 +1164,7 @@ fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32
     // its remaining iterations' kernels in the queue
     constexpr int kChunk = 16;
     for (int it = 0; it < iters; it += kChunk) {
-        for (int j = it; j < std::min(iters, it + kChunk); ++j) TRY(loop_enqueue(c));
+        for (int j = it; j < std::min(iters, it + kChunk); ++j) TRY(loop_iter(c));
         if (c.opt.stop_on_tau && it + kChunk < iters) {
             double done = 0.0;
             CK(cudaMemcpyAsync(&done, c.ctrl + C_DONE, sizeof(double), cudaMemcpyDeviceToHost,

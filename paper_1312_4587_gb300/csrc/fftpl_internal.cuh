@@ -444,6 +444,11 @@ struct Ctx {
 
     // captured CUDA graph of fftpl_eval for one set of buffers
     cudaGraphExec_t eval_graph = nullptr;
+    // captured CUDA graph of one placement-loop iteration (fftpl_step), keyed
+    // by the buffers its kernels take that can be reallocated
+    cudaGraphExec_t loop_graph = nullptr;
+    const void* loop_key[3] = {};
+    int64_t loop_graph_nkernels = 0;
     const void* graph_key[8] = {};
     int64_t graph_nkernels = 0;
     // profiling ring of (stage, begin, end) event records

@@ -26,13 +26,9 @@ k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float nx = 0.0f, ny = 0.0f, wx = 0.0f, wy = 0.0f;
     if (i < m) {
-        Span s = cell_span(gr, b.v[i], b.v[m + i], b.w[i], b.h[i]);
-        float2 e = gather_span(gr, s, E2);
-        nx = -e.x;
-        ny = -e.y;
-        b.gN[i] = nx;
-        b.gN[m + i] = ny;
+        // the wirelength gradient's loads go out before the field gather's
         const int r = rank[i];
+        Span s = cell_span(gr, b.v[i], b.v[m + i], b.w[i], b.h[i]);
         if (CSR) {
             for (int q = cell_pin_ptr[r]; q < cell_pin_ptr[r + 1]; ++q) {
                 float2 p = gpin[q];
@@ -44,6 +40,11 @@ k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
             wx = v.x;
             wy = v.y;
         }
+        float2 e = gather_span(gr, s, E2);
+        nx = -e.x;
+        ny = -e.y;
+        b.gN[i] = nx;
+        b.gN[m + i] = ny;
         b.gW[i] = wx;
         b.gW[m + i] = wy;
     }

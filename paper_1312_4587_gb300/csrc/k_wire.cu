@@ -437,8 +437,10 @@ k_wa_big(int nbig, int dmax, const int4* __restrict__ slabs, WaIo io, float gamm
 // Per-cell kernel: density gradient by the field gather (q.E of Eq. 7),
 // wirelength gradient by summing the cell's pin gradients (CSR mode) or
 // reading the atomically accumulated sums, and the L1 norms of both.
+// (6 blocks per SM: at most 40 registers, 48 warps to hide the gathers'
+// latency; it runs alone after the join)
 template <bool CSR>
-__global__ void __launch_bounds__(kCellThreads)
+__global__ void __launch_bounds__(kCellThreads, 6)
 k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
         const float* __restrict__ w, const float* __restrict__ h, const float2* __restrict__ E2,
         float* __restrict__ gNx, float* __restrict__ gNy,
