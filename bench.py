@@ -56,13 +56,13 @@ STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "ce
 # source it was taken from is unchanged: key = first 16 hex digits of the
 # SHA-256 of the kernel file followed by fftpl_internal.cuh.
 STAGE_TRAFFIC = {
-    "scatter": ("k_density.cu", "c99b39f6e1ec279f", 50680576 + 631808),
-    "rows_fwd": ("k_spectral.cu", "a2431570c7720e47", 33652992 + 256),
-    "cols": ("k_spectral.cu", "a2431570c7720e47", 17423104 + 751872),
-    "rows_inv": ("k_spectral.cu", "a2431570c7720e47", 33645824 + 2244608),
+    "scatter": ("k_density.cu", "709f5bccb71b81ce", 50713600 + 689152),
+    "rows_fwd": ("k_spectral.cu", "f3dfd976954ee1ed", 33652992 + 256),
+    "cols": ("k_spectral.cu", "f3dfd976954ee1ed", 17456384 + 796672),
+    "rows_inv": ("k_spectral.cu", "f3dfd976954ee1ed", 33645056 + 2011136),
     # k_wa and k_wa_big
-    "wa": ("k_wire.cu", "f680768acafcc601", 103064832 + 3850240 + 65444352 + 514048),
-    "cells": ("k_wire.cu", "f680768acafcc601", 76414720 + 14316800),
+    "wa": ("k_wire.cu", "7721d1556b58b018", 103016960 + 3891200 + 65446656 + 471040),
+    "cells": ("k_wire.cu", "7721d1556b58b018", 76494592 + 14393600),
 }
 
 

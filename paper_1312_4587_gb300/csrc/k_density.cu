@@ -91,7 +91,7 @@ k_bin_ranges(Grid g, int m, const float* __restrict__ x, const float* __restrict
 // Field gather (ADJ = false) or exact edge-difference adjoint (ADJ = true,
 // field = psi in fx).  Writes gx, gy and adds ||g||_1 to *l1.
 template <bool ADJ>
-__global__ void __launch_bounds__(kCellThreads)
+__global__ void __launch_bounds__(kCellThreads, 6)
 k_gather(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
          const float* __restrict__ w, const float* __restrict__ h, const float* __restrict__ fx,
          const float2* __restrict__ E2, float* __restrict__ gx, float* __restrict__ gy,
