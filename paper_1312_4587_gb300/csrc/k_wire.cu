@@ -10,20 +10,24 @@
 // compared with the net's span.  Pin coordinate = fl32(cell centre + offset).
 //
 // The wirelength gradient of a pin goes to its cell with one 8-byte vector
-// atomic into an interleaved (x, y) accumulator, or, in deterministic mode,
-// to the pin's slot in a cell-ordered array that the cell kernel sums.
+// reduction (red, no return value) into an interleaved (x, y) accumulator,
+// or, in deterministic mode, to the pin's slot in a cell-ordered array that
+// the cell kernel sums.
 #include "fftpl_internal.cuh"
 
 namespace fftpl {
 
 // Nets are re-laid at create time into slabs of up to 32 nets of one degree
 // d (slab = {first pin slot, d, net count}); pin k of the slab's net j sits
-// at slot base + 32 k + j.  k_wa runs one warp per slab, one lane per net:
-// every lane walks the same d pins (no divergence), each pin-record read of
-// the warp is one contiguous access, and the cell-centre gathers of a slab
-// touch nearby lines (cells are numbered breadth-first over the nets).
-// Slabs of degree 2..6 (the bulk of the nets) run a body specialised for
-// their degree with the pins and exponentials held in registers.
+// at slot base + 32 k + j.  One warp per slab, one lane per net: every lane
+// walks the same d pins (no divergence), each pin-record read of the warp is
+// one contiguous access, and the cell-centre gathers of a slab touch nearby
+// lines (cells are numbered by regions of the netlist).  k_wa takes the
+// slabs of degree 2..6 (the bulk of the nets; a body specialised for the
+// degree, pin coordinates in registers, two slabs per warp for degree 2..4
+// on large instances) and those above kBigMax (runtime degree, coordinates
+// staged in pxy); k_wa_big the slabs of degree kBigMin..kBigMax (records
+// and coordinates in shared memory).
 
 // (x, y) -> interleaved positions at each cell's internal number, so that
 // one 8-byte load (one sector) fetches a pin's cell centre and the pins of a
