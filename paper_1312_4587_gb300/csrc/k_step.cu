@@ -16,9 +16,10 @@ struct LoopBufs {
     DetRed dr;
 };
 
-// gather + pin sums at v (like k_cells) and, in the last CTA, lambda_k.
+// gather + pin sums at v (like k_cells, 48 warps per SM) and, in the last
+// CTA, lambda_k.
 template <bool CSR>
-__global__ void __launch_bounds__(kCellThreads)
+__global__ void __launch_bounds__(kCellThreads, 6)
 k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
              const int* __restrict__ rank, const int* __restrict__ cell_pin_ptr,
              const float2* __restrict__ gpin, const float2* __restrict__ gW2) {
