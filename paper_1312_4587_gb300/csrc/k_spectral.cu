@@ -21,7 +21,11 @@
 // The inverse cosine sum y[x] = sum_u c[u] C(u,x) is the inverse of that map;
 // a sine sum is a cosine sum of the reversed coefficients times (-1)^x.
 // The FFTs are radix-4 Stockham (plus one radix-2 stage for odd log2 n) in
-// shared memory with twiddles from a float32 table computed in FP64.
+// shared memory with twiddles from a float32 table computed in FP64: a
+// radix-R butterfly loads W^(b st) for b = 1, 2, 4, 8 and forms the other
+// R - 1 - log2 R by products, at most three deep (about 3 ulp; each table
+// load costs more than the multiplies: 4 instead of 15 loads per radix-16
+// butterfly took the three passes from 124 to 114 us).
 #include "fftpl_internal.cuh"
 
 namespace fftpl {
@@ -142,15 +146,25 @@ __device__ __forceinline__ void stockham_stage(float2* __restrict__ buf, const f
             const float2* src = buf + f * NP;
             int st = (N / (R * Ns)) * k;   // twiddle index step: W_N^(r st)
             v[i][0] = src[pidx(j)];
+            if (Ns == 1) {
+                // first stage: every twiddle is exp(0) = 1
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                if (Ns == 1) {
-                    // first stage: every twiddle is exp(0) = 1
-                    v[i][r] = src[pidx(j + r * NR)];
-                } else {
-                    float2 w = tw[r * st];
-                    if (inv) w.y = -w.y;
-                    v[i][r] = cmul(src[pidx(j + r * NR)], w);
+                for (int r = 1; r < R; ++r) v[i][r] = src[pidx(j + r * NR)];
+            } else {
+                // W^(r st) for r < R from the table's W^(st), W^(2 st),
+                // W^(4 st), W^(8 st) by products (at most three deep)
+                float2 w[R];
+                w[0] = make_float2(1.0f, 0.0f);
+#pragma unroll
+                for (int b = 1; b < R; b <<= 1) w[b] = tw[b * st];
+#pragma unroll
+                for (int r = 3; r < R; ++r)
+                    if (r & (r - 1)) w[r] = cmul(w[r & (r - 1)], w[r & -r]);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 ww = w[r];
+                    if (inv) ww.y = -ww.y;
+                    v[i][r] = cmul(src[pidx(j + r * NR)], ww);
                 }
             }
             dst[i] = (f << 24) | ((j - k) * R + k);   // buffer and element index
