@@ -56,13 +56,13 @@ STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "ce
 # source it was taken from is unchanged: key = first 16 hex digits of the
 # SHA-256 of the kernel file followed by fftpl_internal.cuh.
 STAGE_TRAFFIC = {
-    "scatter": ("k_density.cu", "709f5bccb71b81ce", 50713600 + 689152),
-    "rows_fwd": ("k_spectral.cu", "f3dfd976954ee1ed", 33652992 + 256),
-    "cols": ("k_spectral.cu", "f3dfd976954ee1ed", 17456384 + 796672),
-    "rows_inv": ("k_spectral.cu", "f3dfd976954ee1ed", 33645056 + 2011136),
+    "scatter": ("k_density.cu", "709f5bccb71b81ce", 50708224 + 633344),
+    "rows_fwd": ("k_spectral.cu", "5e25095a26939b69", 33646592 + 0),
+    "cols": ("k_spectral.cu", "5e25095a26939b69", 17411072 + 545536),
+    "rows_inv": ("k_spectral.cu", "5e25095a26939b69", 33637120 + 2355200),
     # k_wa and k_wa_big
-    "wa": ("k_wire.cu", "7721d1556b58b018", 103016960 + 3891200 + 65446656 + 471040),
-    "cells": ("k_wire.cu", "7721d1556b58b018", 76494592 + 14393600),
+    "wa": ("k_wire.cu", "8c07f78e2007ca47", 103054848 + 3672576 + 65446144 + 566784),
+    "cells": ("k_wire.cu", "8c07f78e2007ca47", 76478464 + 14801664),
 }
 
 
