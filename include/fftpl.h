@@ -159,7 +159,8 @@ typedef struct {
     double tau_stop;        /* stop threshold for the overflow, 0.1 */
     int32_t stop_on_tau;    /* 1: fftpl_step stops when tau <= tau_stop */
     int32_t use_graphs;     /* 1: replay captured CUDA graphs for repeated
-                               calls with the same buffers */
+                               evaluations with the same buffers and for
+                               the iterations of fftpl_step */
     int32_t wirelength;     /* FFTPL_WL_WA (default) or FFTPL_WL_LSE */
     int32_t optimizer;      /* FFTPL_OPT_NESTEROV (default) or FFTPL_OPT_CG */
     double helmholtz_eps;   /* 0: the Poisson equation of Eq. 8 (the (0,0)
@@ -265,7 +266,8 @@ fftpl_status fftpl_eval(fftpl_t h, const float* x, const float* y, float gamma,
  * (page-locked, device-mapped) host memory the kernels read x, y and write
  * the gradients over the host link themselves, overlapping the transfers
  * with the computation (the scatter reads the positions once and keeps a
- * device copy for the later kernels); otherwise the call copies x, y in,
+ * device copy for the later kernels; the wirelength gradient is written
+ * while the transforms still run); otherwise the call copies x, y in,
  * evaluates and copies the gradients out.  Results are the same either way
  * (bit-identical in deterministic mode). */
 fftpl_status fftpl_eval_host(fftpl_t h, const float* x_host, const float* y_host, float gamma,
