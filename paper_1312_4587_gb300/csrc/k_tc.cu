@@ -503,6 +503,14 @@ struct TcPlan {
     int n = 0;
     __nv_bfloat16 *C[2], *CS[2], *Sy[2], *R[2], *A1[2], *P[2], *UX[2];
     CUtensorMap mC[2], mCS[2], mSy[2], mR[2], mA1[2], mP[2], mUX[2];
+    // G7 runs on its own stream beside G46 (both only read G35's output)
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~TcPlan() {
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (s2) cudaStreamDestroy(s2);
+    }
 };
 
 size_t tc_elems(int n) { return 18 * (size_t)n * n; }
@@ -531,6 +539,14 @@ cudaError_t tc_setup(Ctx& c, uint16_t* block, cudaStream_t s) {
              make_map(&p->mA1[h], p->A1[h], n, n) && make_map(&p->mP[h], p->P[h], n, n) &&
              make_map(&p->mUX[h], p->UX[h], 2 * n, n);
     }
+    if (!ok) {
+        delete p;
+        return cudaErrorInvalidValue;
+    }
+    if (ok)
+        ok = cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         delete p;
         return cudaErrorInvalidValue;
@@ -591,16 +607,25 @@ cudaError_t launch_tc(Ctx& c, int part, cudaStream_t s) {
         ep.lo = p.UX[1];
         e = gemm<tc::EPI_SPLIT>(p.mCS, p.mP, 2 * n, n, n, 3, ep, s);
         c.launches++;
-        if (e == cudaSuccess) {
-            ep.f32 = c.psi;
-            ep.E2 = c.E2;
-            e = gemm<tc::EPI_PSI_EX>(p.mCS, p.mUX, n, 2 * n, n, 3, ep, s);
-            c.launches++;
-        }
-        if (e == cudaSuccess) {
-            e = gemm<tc::EPI_EY>(p.mSy, p.mUX, n, n, n, 3, ep, s);
-            c.launches++;
-        }
+        if (e != cudaSuccess) return e;
+        // G46 (512 tiles at the launch's own stream) and G7 (256 tiles on
+        // s2) together: their 768 tiles fill about 5 waves of SMs instead of
+        // 4 + 2 one after the other; they write disjoint halves of E2
+        ep.f32 = c.psi;
+        ep.E2 = c.E2;
+        e = cudaEventRecord(p.fork, s);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamWaitEvent(p.s2, p.fork, 0);
+        if (e != cudaSuccess) return e;
+        e = gemm<tc::EPI_PSI_EX>(p.mCS, p.mUX, n, 2 * n, n, 3, ep, s);
+        c.launches++;
+        const cudaError_t e7 = gemm<tc::EPI_EY>(p.mSy, p.mUX, n, n, n, 3, ep, p.s2);
+        c.launches++;
+        // join in every case, so that a capture stays well formed
+        const cudaError_t ej = cudaEventRecord(p.join, p.s2);
+        const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(s, p.join, 0) : ej;
+        if (e == cudaSuccess) e = e7;
+        if (e == cudaSuccess) e = ew;
     }
     return e;
 }
