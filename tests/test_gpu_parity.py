@@ -146,6 +146,49 @@ def test_bin_ranges_bit_exact(F):
         assert got_pairs == pairs
 
 
+def test_bin_ranges_bit_exact_offset_4096(F):
+    """The largest grid on a region far from the origin (x0 = 10000,
+    w_b = 0.5): cell edges exactly on bin edges, one ulp either side of
+    them, 1e-4 bins from them, and at random; the bin ranges must match the
+    oracle bit for bit (the fast path of the bin search is only taken far
+    from every edge)."""
+    import torch
+    rng = np.random.default_rng(4097)
+    n, wb = 4096, 0.5
+    x0, y0 = 10000.0, -3000.0
+    region = (x0, y0, x0 + n * wb, y0 + n * wb)
+    m = 40000
+    w = rng.uniform(0.2, 3.0, m).astype(np.float32)
+    h = rng.uniform(0.2, 3.0, m).astype(np.float32)
+    k = rng.integers(-2, n + 3, m)
+    e = (np.float32(x0) + np.float32(wb) * k.astype(np.float32)).astype(np.float32)
+    kind = rng.integers(0, 5, m)
+    xl = np.where(kind == 0, e, np.where(kind == 1, np.nextafter(e, np.float32(np.inf)),
+                  np.where(kind == 2, np.nextafter(e, np.float32(-np.inf)),
+                           np.where(kind == 3, e + np.float32(1e-4 * wb),
+                                    np.float32(x0) + rng.uniform(-1, n * wb + 1, m).astype(np.float32)))))
+    x = (xl.astype(np.float32) + np.float32(0.5) * w).astype(np.float32)
+    ky = rng.integers(-2, n + 3, m)
+    ey = (np.float32(y0) + np.float32(wb) * ky.astype(np.float32)).astype(np.float32)
+    y = np.where(kind % 2 == 0, ey + np.float32(0.5) * h,
+                 np.float32(y0) + rng.uniform(-1, n * wb + 1, m).astype(np.float32)).astype(np.float32)
+    inst = synth.make_instance("tiny")
+    inst.n = n
+    inst.region = region
+    inst.m_mov, inst.m_fix = m, 0
+    inst.w, inst.h, inst.x, inst.y = w, h, x, y
+    inst.fix_x = np.zeros(0, np.float32); inst.fix_y = np.zeros(0, np.float32)
+    inst.net_ptr = np.array([0, 2], np.int32); inst.pin_cell = np.array([0, 1], np.int32)
+    inst.pin_dx = np.zeros(2, np.float32); inst.pin_dy = np.zeros(2, np.float32)
+    ref, pairs = oracle.bin_ranges(region, n, x, y, w, h)
+    with F.Problem(inst) as p:
+        rng_d = torch.zeros((m, 4), dtype=torch.int32, device="cuda")
+        got_pairs = F.fftpl_bin_ranges(p.h, cuda(x), cuda(y), rng_d)
+        got = rng_d.cpu().numpy()
+    assert np.array_equal(got, ref)
+    assert got_pairs == pairs
+
+
 def test_deterministic_map_bit_exact(F):
     import torch
     inst = synth.make_instance("precision_sub")
