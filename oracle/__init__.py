@@ -56,6 +56,16 @@ class IterRec(C.Structure):
                 ("alpha", C.c_double), ("step_max", C.c_double)]
 
 
+class PointOut(C.Structure):
+    _fields_ = [("W", C.c_double), ("hpwl", C.c_double), ("N", C.c_double),
+                ("tau", C.c_double), ("gN_l1", C.c_double), ("gW_l1", C.c_double)]
+
+
+# void f(void* ctx, const double* v, double gamma, double* gW, double* gN, PointOut* out)
+ObjectiveFn = C.CFUNCTYPE(None, C.c_void_p, C.POINTER(C.c_double), C.c_double,
+                          C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(PointOut))
+
+
 class LoopOpts(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("gamma_fixed", C.c_double),
                 ("dw_ref", C.c_double), ("alpha_max0_bins", C.c_double),
@@ -87,6 +97,9 @@ def lib():
             L.orc_nesterov_a.restype = C.c_double
             L.orc_nesterov_a.argtypes = [C.c_double]
             L.orc_nesterov.restype = C.c_int
+            L.orc_nesterov_run.restype = C.c_int
+            L.orc_nesterov_run.argtypes = [C.c_int, _P, _P, _P, C.c_double, ObjectiveFn,
+                                           C.c_void_p, C.POINTER(LoopOpts), C.c_int, _P]
             L.orc_cg.restype = C.c_int
             L.orc_num_threads.restype = C.c_int
             _lib = L
@@ -325,6 +338,37 @@ def nesterov(inst, iters, **kw):
     """Global placement loop (Algorithm 1 with a Nesterov step).  Returns
     (x, y, records[k] dicts, iterations run)."""
     return _loop("orc_nesterov", inst, iters, **kw)
+
+
+def nesterov_run(x0, lo, hi, wb, objective, iters, lambda0=0.0, gamma_fixed=1.0, dw_ref=3.5e5,
+                 alpha_max0_bins=0.044, stop_on_tau=False, tau_stop=0.1):
+    """The loop of orc_nesterov (Nesterov step, Section IV-A control) on an
+    objective given as a Python callable objective(v, gamma) -> dict with
+    gW, gN (arrays like v) and W, hpwl, N, tau, gN_l1, gW_l1 (gamma == 0 and
+    no gradients asked: only tau is read).  Returns (u, records, ran)."""
+    x = _f64(x0).copy()
+    lo, hi = _f64(lo), _f64(hi)
+    nv = x.shape[0]
+
+    def cb(ctx, v, gamma, gW, gN, out):
+        vv = np.ctypeslib.as_array(v, shape=(nv,)).copy()
+        r = objective(vv, float(gamma))
+        if gW:
+            np.ctypeslib.as_array(gW, shape=(nv,))[:] = r["gW"]
+            np.ctypeslib.as_array(gN, shape=(nv,))[:] = r["gN"]
+        o = out.contents
+        for k in ("W", "hpwl", "N", "tau", "gN_l1", "gW_l1"):
+            setattr(o, k, float(r.get(k, 0.0)))
+
+    fn = ObjectiveFn(cb)
+    opts = LoopOpts(float(lambda0), float(gamma_fixed), float(dw_ref), float(alpha_max0_bins),
+                    int(stop_on_tau), float(tau_stop), 0, 0.0)
+    recs = (IterRec * max(iters, 1))()
+    ran = lib().orc_nesterov_run(C.c_int(nv), _ptr(x), _ptr(lo), _ptr(hi), C.c_double(wb), fn,
+                                 None, C.byref(opts), C.c_int(iters), C.cast(recs, _P))
+    rows = [dict(W=r.W, hpwl=r.hpwl, N=r.N, tau=r.tau, lam=r.lambda_, gamma=r.gamma,
+                 alpha=r.alpha, step_max=r.step_max) for r in recs[:ran]]
+    return x, rows, int(ran)
 
 
 def cg(inst, iters, **kw):

@@ -705,32 +705,41 @@ typedef struct {
     double helmholtz_eps; /* 0 Poisson (Eq. 8), > 0 Helmholtz (Eq. 4) */
 } orc_loop_opts;
 
-/* Global placement loop (Algorithm 1 with the CG step replaced by Nesterov's
- * method).  Positions are kept in FP64 and rounded to float32 for each
- * evaluation.  x, y (m_mov) are updated in place with the final major
- * iterate u.  recs (iters entries) receive per-iteration metrics.  Returns the
- * number of iterations run.
+/* The objective as the loop sees it: at the point v (nvar doubles, all x
+ * then all y for a placement) and smoothing gamma, the wirelength gradient gW,
+ * the density gradient gN (nvar each) and the scalars of out.  With
+ * gW == NULL only out->tau is wanted (the gamma schedule's start). */
+typedef struct {
+    double W, hpwl, N, tau, gN_l1, gW_l1;
+} orc_point_out;
+
+typedef void (*orc_objective_fn)(void* ctx, const double* v, double gamma, double* gW,
+                                 double* gN, orc_point_out* out);
+
+/* Nesterov's method in place of the conjugate-gradient solver of Algorithm 1,
+ * with the parameter control of Section IV-A, on any objective f of the form
+ * W~ + lambda N given by its callback.  x (nvar) holds the start and receives
+ * the final major iterate u; lo, hi bound each variable (the projection Pi);
+ * wb is the bin width (alpha_max_0 = alpha_max0_bins wb and the gamma
+ * schedule).  recs (iters entries) receive per-iteration metrics.  Returns
+ * the number of iterations run.
  *
- * Iteration k, at the look-ahead point v_k:
+ * u_0 = v_0 = Pi(x), a_0 = 1.  Iteration k, at the look-ahead point v_k:
  *   g_k = grad W~(v_k; gamma_k) + lambda_k grad N(v_k)
+ *   lambda_0 = ||grad W~||_1 / ||grad N||_1 at v_0 unless given;
+ *   lambda_k = mu_k lambda_{k-1} (k >= 1), mu from dW = HPWL(v_k) - HPWL(v_{k-1})
  *   alpha_0 = alpha_max_0 / ||g_0||_inf,
  *   alpha_k = ||v_k - v_{k-1}||_2 / ||g_k - g_{k-1}||_2 (k >= 1),
  *   then alpha_k ||g_k||_inf is clamped to [0.01 alpha_max_k, alpha_max_k]
- *   u_{k+1} = clamp(v_k - alpha_k g_k)
+ *   u_{k+1} = Pi(v_k - alpha_k g_k)
  *   a_{k+1} = (1 + sqrt(1 + 4 a_k^2))/2, beta = (a_k - 1)/a_{k+1}
- *   v_{k+1} = clamp(u_{k+1} + beta (u_{k+1} - u_k))
+ *   v_{k+1} = Pi(u_{k+1} + beta (u_{k+1} - u_k))
  *   alpha_max_{k+1} = max(alpha_max_0, 2 max_i |u_{k+1} - v_k|)
- *   lambda_{k+1} = mu_k lambda_k with dW = HPWL(v_k) - HPWL(v_{k-1}) (k >= 1)
- *   gamma_{k+1} = gamma(tau_k) unless fixed.
- * clamp keeps each cell inside the region: [x0 + w/2, x1 - w/2]. */
-int orc_nesterov(const orc_region* R, int n, double rho_t,
-                 int m_mov, float* x, float* y, const float* w, const float* h,
-                 int m_fix, const float* fx, const float* fy, const float* fw, const float* fh,
-                 int E, const int32_t* net_ptr, const int32_t* pin_cell,
-                 const float* pdx, const float* pdy, const orc_loop_opts* o,
-                 int iters, orc_iter_rec* recs) {
-    size_t m2 = (size_t)2 * m_mov;
-    double wb = (R->x1 - R->x0) / n;
+ *   gamma_{k+1} = gamma(tau_k) unless fixed. */
+int orc_nesterov_run(int nvar, double* x, const double* lo, const double* hi, double wb,
+                     orc_objective_fn f, void* ctx, const orc_loop_opts* o, int iters,
+                     orc_iter_rec* recs) {
+    size_t m2 = (size_t)nvar;
     double* u = (double*)malloc(m2 * sizeof(double));
     double* v = (double*)malloc(m2 * sizeof(double));
     double* vp = (double*)malloc(m2 * sizeof(double));
@@ -738,39 +747,22 @@ int orc_nesterov(const orc_region* R, int n, double rho_t,
     double* gp = (double*)malloc(m2 * sizeof(double));
     double* gN = (double*)malloc(m2 * sizeof(double));
     double* gW = (double*)malloc(m2 * sizeof(double));
-    double* lo = (double*)malloc(m2 * sizeof(double));
-    double* hi = (double*)malloc(m2 * sizeof(double));
-    float* xf = (float*)malloc((size_t)m_mov * sizeof(float));
-    float* yf = (float*)malloc((size_t)m_mov * sizeof(float));
-    for (int i = 0; i < m_mov; ++i) {
-        lo[i] = R->x0 + 0.5 * w[i]; hi[i] = R->x1 - 0.5 * w[i];
-        lo[m_mov + i] = R->y0 + 0.5 * h[i]; hi[m_mov + i] = R->y1 - 0.5 * h[i];
-        u[i] = dmin(hi[i], dmax(lo[i], (double)x[i]));
-        u[m_mov + i] = dmin(hi[m_mov + i], dmax(lo[m_mov + i], (double)y[i]));
-        v[i] = u[i]; v[m_mov + i] = u[m_mov + i];
+    for (size_t i = 0; i < m2; ++i) {
+        u[i] = dmin(hi[i], dmax(lo[i], x[i]));
+        v[i] = u[i];
     }
     double a_k = 1.0, lambda = o->lambda0, alpha_max0 = o->alpha_max0_bins * wb;
     double alpha_max = alpha_max0, alpha = 0.0, hp_prev = 0.0;
     double gamma = o->gamma_fixed;
     int k;
     for (k = 0; k < iters; ++k) {
-        for (int i = 0; i < m_mov; ++i) { xf[i] = (float)v[i]; yf[i] = (float)v[m_mov + i]; }
-        orc_eval_out ev;
+        orc_point_out ev;
         if (k == 0 && gamma <= 0.0) {
-            /* schedule needs tau at the start: evaluate density once */
-            size_t nn = (size_t)n * n;
-            double* rho = (double*)malloc(nn * sizeof(double));
-            double* D = (double*)malloc(nn * sizeof(double));
-            double* F = (double*)malloc(nn * sizeof(double));
-            orc_density(R, n, rho_t, m_mov, xf, yf, w, h, m_fix, fx, fy, fw, fh, rho, D, F);
-            double q = 0.0;
-            for (int i = 0; i < m_mov; ++i) q += (double)w[i] * (double)h[i];
-            gamma = orc_gamma(orc_overflow(n, wb * ((R->y1 - R->y0) / n), rho_t, D, F, q), wb);
-            free(rho); free(D); free(F);
+            /* the schedule needs tau at the start */
+            f(ctx, v, 0.0, NULL, NULL, &ev);
+            gamma = orc_gamma(ev.tau, wb);
         }
-        orc_eval2(R, n, rho_t, m_mov, xf, yf, w, h, m_fix, fx, fy, fw, fh, E, net_ptr, pin_cell,
-                  pdx, pdy, gamma, o->wirelength, o->helmholtz_eps, gN, gN + m_mov, gW,
-                  gW + m_mov, NULL, NULL, NULL, NULL, &ev);
+        f(ctx, v, gamma, gW, gN, &ev);
         if (k == 0 && lambda <= 0.0) lambda = ev.gN_l1 > 0 ? ev.gW_l1 / ev.gN_l1 : 1.0;
         if (k >= 1) lambda *= orc_mu(ev.hpwl - hp_prev, o->dw_ref);
         hp_prev = ev.hpwl;
@@ -815,9 +807,85 @@ int orc_nesterov(const orc_region* R, int n, double rho_t,
         if (o->gamma_fixed <= 0.0) gamma = orc_gamma(ev.tau, wb);
         if (o->stop_on_tau && ev.tau <= o->tau_stop) { ++k; break; }
     }
+    for (size_t i = 0; i < m2; ++i) x[i] = u[i];
+    free(u); free(v); free(vp); free(g); free(gp); free(gN); free(gW);
+    return k;
+}
+
+/* A placement instance as the loop's objective: positions rounded to
+ * float32 for each evaluation (the library's inputs), then orc_eval2. */
+typedef struct {
+    const orc_region* R;
+    int n;
+    double rho_t;
+    int m_mov;
+    const float *w, *h;
+    int m_fix;
+    const float *fx, *fy, *fw, *fh;
+    int E;
+    const int32_t *net_ptr, *pin_cell;
+    const float *pdx, *pdy;
+    int wirelength;
+    double helmholtz_eps;
+    float *xf, *yf;
+} orc_place_ctx;
+
+static void place_objective(void* vctx, const double* v, double gamma, double* gW, double* gN,
+                            orc_point_out* out) {
+    orc_place_ctx* c = (orc_place_ctx*)vctx;
+    int m = c->m_mov;
+    for (int i = 0; i < m; ++i) { c->xf[i] = (float)v[i]; c->yf[i] = (float)v[m + i]; }
+    if (!gW) {
+        size_t nn = (size_t)c->n * c->n;
+        double* rho = (double*)malloc(nn * sizeof(double));
+        double* D = (double*)malloc(nn * sizeof(double));
+        double* F = (double*)malloc(nn * sizeof(double));
+        orc_density(c->R, c->n, c->rho_t, m, c->xf, c->yf, c->w, c->h, c->m_fix, c->fx, c->fy,
+                    c->fw, c->fh, rho, D, F);
+        double q = 0.0;
+        for (int i = 0; i < m; ++i) q += (double)c->w[i] * (double)c->h[i];
+        double Ab = ((c->R->x1 - c->R->x0) / c->n) * ((c->R->y1 - c->R->y0) / c->n);
+        out->tau = orc_overflow(c->n, Ab, c->rho_t, D, F, q);
+        free(rho); free(D); free(F);
+        return;
+    }
+    orc_eval_out ev;
+    orc_eval2(c->R, c->n, c->rho_t, m, c->xf, c->yf, c->w, c->h, c->m_fix, c->fx, c->fy, c->fw,
+              c->fh, c->E, c->net_ptr, c->pin_cell, c->pdx, c->pdy, gamma, c->wirelength,
+              c->helmholtz_eps, gN, gN + m, gW, gW + m, NULL, NULL, NULL, NULL, &ev);
+    out->W = ev.W; out->hpwl = ev.hpwl; out->N = ev.N; out->tau = ev.tau;
+    out->gN_l1 = ev.gN_l1; out->gW_l1 = ev.gW_l1;
+}
+
+/* Global placement loop (Algorithm 1 with the CG step replaced by Nesterov's
+ * method, orc_nesterov_run) on a placement instance.  Positions are kept in
+ * FP64 and rounded to float32 for each evaluation.  x, y (m_mov) are updated
+ * in place with the final major iterate u.  The projection keeps each cell
+ * inside the region: [x0 + w/2, x1 - w/2]. */
+int orc_nesterov(const orc_region* R, int n, double rho_t,
+                 int m_mov, float* x, float* y, const float* w, const float* h,
+                 int m_fix, const float* fx, const float* fy, const float* fw, const float* fh,
+                 int E, const int32_t* net_ptr, const int32_t* pin_cell,
+                 const float* pdx, const float* pdy, const orc_loop_opts* o,
+                 int iters, orc_iter_rec* recs) {
+    size_t m2 = (size_t)2 * m_mov;
+    double wb = (R->x1 - R->x0) / n;
+    double* u = (double*)malloc(m2 * sizeof(double));
+    double* lo = (double*)malloc(m2 * sizeof(double));
+    double* hi = (double*)malloc(m2 * sizeof(double));
+    orc_place_ctx c = {R, n, rho_t, m_mov, w, h, m_fix, fx, fy, fw, fh, E, net_ptr, pin_cell,
+                       pdx, pdy, o->wirelength, o->helmholtz_eps,
+                       (float*)malloc((size_t)m_mov * sizeof(float)),
+                       (float*)malloc((size_t)m_mov * sizeof(float))};
+    for (int i = 0; i < m_mov; ++i) {
+        lo[i] = R->x0 + 0.5 * w[i]; hi[i] = R->x1 - 0.5 * w[i];
+        lo[m_mov + i] = R->y0 + 0.5 * h[i]; hi[m_mov + i] = R->y1 - 0.5 * h[i];
+        u[i] = (double)x[i];
+        u[m_mov + i] = (double)y[i];
+    }
+    int k = orc_nesterov_run((int)m2, u, lo, hi, wb, place_objective, &c, o, iters, recs);
     for (int i = 0; i < m_mov; ++i) { x[i] = (float)u[i]; y[i] = (float)u[m_mov + i]; }
-    free(u); free(v); free(vp); free(g); free(gp); free(gN); free(gW); free(lo); free(hi);
-    free(xf); free(yf);
+    free(u); free(lo); free(hi); free(c.xf); free(c.yf);
     return k;
 }
 

@@ -196,3 +196,40 @@ def test_energy_decreases_when_spread(orc):
         _, psi, _, _ = orc.solve(r, L, L)
         Ns.append(orc.energy(r, psi, Ab))
     assert Ns[0] > Ns[1] > 0 and abs(Ns[2]) < 1e-9 * Ns[1]
+
+
+@pytest.mark.parametrize("n,Lx,Ly", [(8, 16.0, 16.0), (16, 20.0, 50.0), (32, 48.0, 24.0)])
+def test_potential_at_equals_full_field(orc, n, Lx, Ly):
+    """orc_potential_at (the pointwise series used to check large grids)
+    agrees with the full-map series at every bin of small grids, for random
+    coefficients with a nonzero (0,0) entry that both must ignore, in a
+    non-square region (w_u and w_v differ): a swapped sine/cosine or axis, a
+    kept (0,0) term or a wrong divisor would differ by O(1)."""
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal((n, n))
+    a[0, 0] = 5.0
+    psi, ex, ey = orc.potential_field(a, Lx, Ly)
+    ys, xs = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    p, qx, qy = orc.potential_at(a, Lx, Ly, xs.ravel(), ys.ravel())
+    scale = max(np.abs(psi).max(), np.abs(ex).max(), np.abs(ey).max())
+    for got, ref in ((p, psi), (qx, ex), (qy, ey)):
+        assert np.abs(got - ref.ravel()).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("p,q", [(3, 0), (0, 5), (7, 11), (255, 1)])
+def test_potential_at_single_mode_large_grid(orc, p, q):
+    """n = 256 with a single coefficient a[q][p] = 1: at sampled bins psi,
+    E_x and E_y equal the closed forms of Eqs. 11-12 for one mode."""
+    n, Lx, Ly = 256, 384.0, 192.0
+    a = np.zeros((n, n))
+    a[q, p] = 1.0
+    rng = np.random.default_rng(p * 1000 + q)
+    xs = rng.integers(0, n, 40); ys = rng.integers(0, n, 40)
+    psi, ex, ey = orc.potential_at(a, Lx, Ly, xs, ys)
+    wp, wq = np.pi * p / Lx, np.pi * q / Ly
+    d = wp * wp + wq * wq
+    cx, sx = basis(n, p)[xs], sbasis(n, p)[xs]
+    cy, sy = basis(n, q)[ys], sbasis(n, q)[ys]
+    np.testing.assert_allclose(psi, cx * cy / d, rtol=0, atol=1e-12 / d)
+    np.testing.assert_allclose(ex, wp / d * sx * cy, rtol=0, atol=1e-12 / d)
+    np.testing.assert_allclose(ey, wq / d * cx * sy, rtol=0, atol=1e-12 / d)
