@@ -396,15 +396,170 @@ def run_fillers(args, inst, flush, stream):
             "value": round(1000.0 / ms, 2), "unit": UNIT, "ms_per_step": round(ms, 5)}
 
 
-def cpu_baseline_sample(inst):
-    """The oracle as it stands, one evaluation of the same instance."""
+def step_stats(step_ms):
+    """Mean, median and 10th/90th percentiles of per-step CUDA-event times."""
+    import numpy as np
+    a = np.asarray(step_ms, np.float64)
+    return {"mean": round(float(a.mean()), 5), "median": round(float(np.median(a)), 5),
+            "p10": round(float(np.percentile(a, 10)), 5),
+            "p90": round(float(np.percentile(a, 90)), 5), "count": int(a.size)}
+
+
+# ------------------------------------------------------- fast CPU comparator
+def cpu_fft_eval(inst, cache):
+    """One objective-gradient evaluation in FP64 on the host with the
+    oracle's O(m) steps (exact overlaps, gather, WA) and the spectral solve
+    of Eqs. 9-12 by library FFTs (scipy.fft / pocketfft, all cores: DCT-II
+    forward, DCT-III and DST-III sums back) in place of the oracle's O(n^3)
+    cosine sums: the fast CPU comparator of the timing table."""
+    import numpy as np
+    import scipy.fft as sf
+
     import oracle
+    n, m = inst.n, inst.m_mov
+    x0, y0, x1, y1 = inst.region
+    Ab = ((x1 - x0) / n) * ((y1 - y0) / n)
+    if "div" not in cache:
+        u = np.arange(n)
+        wu, wv = np.pi * u / (x1 - x0), np.pi * u / (y1 - y0)
+        eps = np.where(u == 0, 1.0, 2.0)
+        W2 = wv[:, None] ** 2 + wu[None, :] ** 2
+        W2[0, 0] = np.inf
+        # a = eps_u eps_v / n^2 sum rho cos cos (Eq. 10); scipy's DCT-II carries 2 per axis
+        cache["div"] = (eps[:, None] * eps[None, :]) / (4.0 * n * n) / W2
+        cache["wu"], cache["wv"] = wu, wv
+    k = inst.m_fix
+    fx, fy = (inst.fix_x, inst.fix_y) if k else (None, None)
+    fw, fh = (inst.w[m:], inst.h[m:]) if k else (None, None)
+    rho, D, Fm = oracle.density(inst.region, n, inst.target_density, inst.x, inst.y,
+                                inst.w[:m], inst.h[:m], fx, fy, fw, fh)
+    psi_hat = sf.dctn(rho, type=2, workers=-1) * cache["div"]
+
+    def cos_sum(c, axis):        # sum_u c_u cos(pi u (2x+1) / 2n) along axis
+        c = c.copy()
+        sl = [slice(None)] * 2; sl[axis] = slice(1, None)
+        c[tuple(sl)] *= 0.5
+        return sf.dct(c, type=3, axis=axis, workers=-1)
+
+    def sin_sum(c, axis):        # sum_{u>=1} c_u sin(pi u (2x+1) / 2n) along axis
+        z = np.zeros_like(c)
+        src = [slice(None)] * 2; dst = [slice(None)] * 2
+        src[axis] = slice(1, None); dst[axis] = slice(0, n - 1)
+        z[tuple(dst)] = 0.5 * c[tuple(src)]
+        return sf.dst(z, type=3, axis=axis, workers=-1)
+
+    cy = cos_sum(psi_hat, 0)
+    psi = cos_sum(cy, 1)
+    ex = sin_sum(cy * cache["wu"][None, :], 1)
+    ey = cos_sum(sin_sum(psi_hat * cache["wv"][:, None], 0), 1)
+    gNx, gNy = oracle.gather(inst.region, n, inst.x, inst.y, inst.w[:m], inst.h[:m], ex, ey)
+    wa = oracle.wa(inst.net_ptr, inst.pin_cell, inst.pin_dx, inst.pin_dy, m, inst.x, inst.y,
+                   inst.gamma, fx, fy)
+    area = float(np.sum(inst.w[:m].astype(np.float64) * inst.h[:m].astype(np.float64)))
+    return {"N": oracle.energy(rho, psi, Ab), "W": wa["W"], "hpwl": wa["hpwl"],
+            "tau": oracle.overflow(D, Fm, Ab, inst.target_density, area),
+            "gNx": gNx, "gNy": gNy, "gWx": wa["gcx"], "gWy": wa["gcy"],
+            "psi": psi, "ex": ex, "ey": ey, "rho": rho}
+
+
+def cpu_baselines(inst):
+    """CPU timings beside the GPU line: the oracle on all host cores (the
+    main cpu_baseline), the FFT-based FP64 comparator on all cores, and the
+    oracle on one core (the paper's single-thread regime) on the 210K-cell
+    512 x 512 instance (a full 2048 x 2048 evaluation on one core would take
+    about a minute)."""
+    import oracle
+    import synth
     oracle.build()
+    out = []
+    cores = oracle.num_threads()
     t0 = time.perf_counter()
     oracle.eval_instance(inst)
     dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one full FP64 evaluation of the same instance ({dt:.1f} s)"}
+    out.append({"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"one full FP64 evaluation of the same instance ({dt:.1f} s)"})
+    cache = {}
+    cpu_fft_eval(inst, cache)
+    reps = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        cpu_fft_eval(inst, cache)
+        reps.append(time.perf_counter() - t0)
+    dt = statistics.median(reps)
+    out.append({"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle_with_scipy_fft",
+                "sample": f"median of 3 FP64 evaluations of the same instance, the oracle's "
+                          f"solve replaced by scipy FFTs ({dt:.2f} s each)"})
+    large = synth.make_instance("large")
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.eval_instance(large)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    out.append({"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"one FP64 oracle evaluation of the 210K-cell, 512 x 512 instance on one "
+                          f"core ({dt:.1f} s); a different workload from the GPU line"})
+    return out
+
+
+def run_errors(args):
+    """Relative L2 errors against the FP64 oracle on the 256 x 256 sub-problem
+    of the precision instance (34K cells): every output of one evaluation on
+    the transform and tensor-core solve paths, and the positions after 10
+    placement iterations run directly and served in a mix of jobs."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    from paper_1312_4587_gb300 import fftpl as F
+    from paper_1312_4587_gb300 import serve
+
+    def rel(a, b):
+        a = np.asarray(a, np.float64).ravel(); b = np.asarray(b, np.float64).ravel()
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    inst = synth.make_instance("precision_sub")
+    ref = oracle.eval_instance(inst, maps=True)
+    out = {"workload": f"{inst.name}: {inst.m_mov} cells, {inst.n}x{inst.n} bins",
+           "metric": "relative L2 vs FP64 oracle"}
+    for name, path in (("fft_fp32", F.FFTPL_SOLVE_FFT), ("tc_bf16x3", F.FFTPL_SOLVE_TC_BF16X3)):
+        with F.Problem(inst, solve_path=path) as p:
+            xd = torch.from_numpy(inst.x).cuda(); yd = torch.from_numpy(inst.y).cuda()
+            g = [torch.empty_like(xd) for _ in range(4)]
+            rep = F.fftpl_eval(p.h, xd, yd, inst.gamma, *g)
+            fl = F.fftpl_fields(p.h, inst.n)
+            gg = [t.cpu().numpy() for t in g]
+            out[name] = {
+                "rho": rel(fl["rho"].cpu().numpy(), ref["rho"]),
+                "psi": rel(fl["psi"].cpu().numpy(), ref["psi"]),
+                "ex": rel(fl["ex"].cpu().numpy(), ref["ex"]),
+                "ey": rel(fl["ey"].cpu().numpy(), ref["ey"]),
+                "gradN": rel(np.concatenate(gg[:2]), np.concatenate([ref["gNx"], ref["gNy"]])),
+                "gradW": rel(np.concatenate(gg[2:]), np.concatenate([ref["gWx"], ref["gWy"]])),
+                "N": abs(rep["N"] - ref["N"]) / abs(ref["N"]),
+                "W": abs(rep["W"] - ref["W"]) / abs(ref["W"]),
+            }
+    iters = 10
+    ox, oy, _, _ = oracle.nesterov(inst, iters, gamma_fixed=inst.gamma)
+    o = np.concatenate([ox, oy])
+    with F.Problem(inst, gamma_fixed=inst.gamma) as p:
+        x0 = torch.from_numpy(inst.x).cuda(); y0 = torch.from_numpy(inst.y).cuda()
+        F.fftpl_place_init(p.h, x0, y0)
+        F.fftpl_step(p.h, iters)
+        xx = torch.empty_like(x0); yy = torch.empty_like(y0)
+        F.fftpl_place_positions(p.h, xx, yy)
+        direct = np.concatenate([xx.cpu().numpy(), yy.cpu().numpy()])
+    with serve.Server(max_active=8) as s:
+        s.submit(synth.make_instance("medium"), iters + 15)
+        j = s.submit(inst, iters)
+        s.submit(synth.make_instance("large"), iters + 5)
+        s.drain()
+        _, sx, sy = s.job(j)
+    out["loop_positions_10_iters"] = {"direct_fp32": rel(direct, o),
+                                      "served_in_mix_fp32": rel(np.concatenate([sx, sy]), o)}
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -498,6 +653,7 @@ def run_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": run_config(inst, args, ws),
         "gpu_launches": int(launches),
+        "step_ms": step_stats(step_ms),
         "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * m,
                 "d2h_bytes_per_step": 16 * m + 64},
         "clocks": clk,
@@ -518,7 +674,11 @@ def run_ours(args, ws, rank, local):
     if not args.no_tc_path and n >= F.FFTPL_TC_MIN_N:
         line["tc_path"] = run_tc_path(args, inst, x, y, g, flush, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(inst)
+        cb = cpu_baselines(inst)
+        line["cpu_baseline"] = cb[0]
+        line["cpu_baselines"] = cb
+    if rank == 0 and ws == 1 and not args.no_errors:
+        line["errors"] = run_errors(args)
     if rank == 0 and ws == 1 and args.serving_jobs > 0:
         line["serving"] = run_serving(args)
     if rank == 0:
@@ -540,6 +700,8 @@ def main():
                     help="skip the Nesterov / CG convergence comparison")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the LSE / Helmholtz variant timings")
+    ap.add_argument("--no-errors", action="store_true",
+                    help="skip the per-result errors against the oracle")
     ap.add_argument("--no-tc-path", action="store_true",
                     help="skip the tensor-core solve path comparison")
     ap.add_argument("--serving-jobs", type=int, default=200,

@@ -428,11 +428,14 @@ fftpl_status fftpl_server_set_clock(fftpl_server_t s, double now_s);
  * is the same spectral solve as the density path, offered without a handle.
  *
  * rho: device, n*n float32 bin densities, row-major [y][x].  psi, ex, ey:
- * device outputs of the same layout (potential and field of Eqs. 11-12 for
- * a region of size Lx x Ly; the (0,0) mode of rho is dropped).  N: host,
+ * device outputs of the same layout: the potential psi and the field E_x,
+ * E_y of the Poisson solve for a region of size Lx x Ly (the mean of rho is
+ * dropped).  All four pointers must be 16-byte aligned (the kernels move
+ * rows in 16-byte vectors); a misaligned one returns FFTPL_EINVAL.  N: host,
  * may be NULL; if given, the call synchronises the stream and stores
- * 1/2 (Lx Ly / n^2) sum rho psi there.  n: power of two in [16,
- * FFTPL_NOALLOC_MAX_N]; larger n returns FFTPL_EINVAL.  stream: a
+ * 1/2 (Lx Ly / n^2) sum rho psi there, so N must be NULL while the stream
+ * is being captured (FFTPL_EINVAL otherwise).  n: power of two in [16,
+ * FFTPL_NOALLOC_MAX_N]; any other n returns FFTPL_EINVAL.  stream: a
  * cudaStream_t (NULL: legacy default stream).
  *
  * Memory: the intermediate transforms live in one fixed array in the

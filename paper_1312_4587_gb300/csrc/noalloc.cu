@@ -97,14 +97,28 @@ extern "C" fftpl_status fftpl_solve_noalloc(const float* rho, int32_t n, double 
         set_global_error("fftpl_solve_noalloc: null map pointer");
         return FFTPL_EINVAL;
     }
+    if ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(psi) |
+         reinterpret_cast<uintptr_t>(ex) | reinterpret_cast<uintptr_t>(ey)) & 15u) {
+        set_global_error("fftpl_solve_noalloc: rho, psi, ex and ey must be 16-byte aligned");
+        return FFTPL_EINVAL;
+    }
     if (!(Lx > 0.0) || !(Ly > 0.0) || !isfinite(Lx) || !isfinite(Ly)) {
         set_global_error("fftpl_solve_noalloc: region sizes must be finite and > 0");
         return FFTPL_EINVAL;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N) {
+        // N is read back with a synchronisation, which a capture cannot hold
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+        if (ce != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+            set_global_error("fftpl_solve_noalloc: N must be NULL while the stream is captured");
+            return FFTPL_EINVAL;
+        }
+    }
     unsigned char* base = nullptr;
     fftpl_status st = scratch_for_device(&base);
     if (st != FFTPL_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
 
     // A context on the stack pointing into the scratch array.  The row pass
     // forms (D + M) / A_b; with D = M = rho and 1/A_b = 0.5 that is rho

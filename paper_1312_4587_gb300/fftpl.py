@@ -403,9 +403,13 @@ def fftpl_launch_count(h):
 def fftpl_solve_noalloc(rho, n, Lx, Ly, psi, ex, ey, want_N=False, stream=None):
     """Allocation-free solve of a device density map rho ([n, n] float32 CUDA
     tensor) into caller-owned psi, ex, ey; returns N if want_N."""
+    import torch
+    for name, t in (("rho", rho), ("psi", psi), ("ex", ex), ("ey", ey)):
+        if t.dtype != torch.float32 or t.numel() < int(n) * int(n):
+            raise ValueError(f"fftpl_solve_noalloc: {name} must be float32 with at least "
+                             f"n*n = {int(n) * int(n)} elements")
     N = C.c_double(0.0)
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream().cuda_stream
     _check(lib().fftpl_solve_noalloc(_dptr(rho), C.c_int32(int(n)), C.c_double(Lx),
                                      C.c_double(Ly), _dptr(psi), _dptr(ex), _dptr(ey),

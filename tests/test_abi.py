@@ -147,3 +147,20 @@ def test_options_struct_layout(F):
     assert ctypes.sizeof(F.fftpl_options) == 88
     o = F.fftpl_default_options()
     assert o.wirelength == F.FFTPL_WL_WA and o.helmholtz_eps == 0.0
+
+
+def test_noalloc_validates_before_device_work(F):
+    """fftpl_solve_noalloc refuses bad sizes, misaligned maps and bad region
+    sizes on the host, before any CUDA call (fake device addresses are never
+    dereferenced)."""
+    lib = F.lib()
+    good, odd = 0x10000, 0x10004
+    def call(n, rho=good, Lx=1.0):
+        return lib.fftpl_solve_noalloc(ctypes.c_void_p(rho), n, Lx, 1.0, ctypes.c_void_p(good),
+                                       ctypes.c_void_p(good), ctypes.c_void_p(good), None, None)
+    for n in (8, 1000, 2048, 0, -64):
+        assert call(n) == F.FFTPL_EINVAL
+    assert call(64, rho=odd) == F.FFTPL_EINVAL
+    assert b"aligned" in lib.fftpl_last_error(None)
+    assert call(64, Lx=float("nan")) == F.FFTPL_EINVAL
+    assert call(64, rho=0) == F.FFTPL_EINVAL

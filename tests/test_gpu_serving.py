@@ -62,3 +62,27 @@ def test_stream_of_jobs_completes(S):
     assert st["completed"] == len(jobs) and st["failed"] == 0
     assert all(i["iters_done"] == 20 and i["hpwl"] > 0 for i in infos)
     assert st["iter_p99_ms"] >= st["iter_p50_ms"] > 0 and st["jobs_per_s"] > 0
+
+
+def test_job_in_a_mix_matches_oracle(S):
+    """A 10-iteration job served beside jobs of other sizes and grid sizes
+    (float atomics, not the deterministic mode) follows the oracle's loop
+    (Algorithm 1 with the Nesterov step) within the bounds of the direct
+    loop's parity test: positions within 1e-4 relative L2, the last
+    iteration's HPWL within 1e-4."""
+    import oracle
+    a = synth.make_instance("tiny")
+    ox, oy, orows, oran = oracle.nesterov(a, 10, gamma_fixed=a.gamma)
+    assert oran == 10
+    with S.Server(max_active=8) as s:
+        jb = s.submit(synth.make_instance("medium"), 25)
+        ja = s.submit(a, 10)
+        jc = s.submit(synth.make_instance("precision_sub"), 15)
+        s.drain()
+        info, xa, ya = s.job(ja)
+        assert s.stats()["completed"] == 3
+    assert info["iters_done"] == 10
+    g = np.concatenate([xa, ya]).astype(np.float64)
+    o = np.concatenate([ox, oy]).astype(np.float64)
+    assert np.linalg.norm(g - o) / np.linalg.norm(o) < 1e-4
+    assert abs(info["hpwl"] - orows[-1]["hpwl"]) <= 1e-4 * orows[-1]["hpwl"]

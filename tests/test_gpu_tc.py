@@ -182,11 +182,33 @@ def test_tc_deterministic_repeats_bitwise(F):
     assert a["rep"]["N"] == b["rep"]["N"]
 
 
+def oracle_samples(inst, count, seed):
+    """psi, E_x, E_y of the oracle's series (Eqs. 9-12, FP64) at sampled bins
+    of the instance's density map: (xs, ys, psi, ex, ey)."""
+    n, m = inst.n, inst.m_mov
+    fx = inst.fix_x if inst.m_fix else None
+    fy = inst.fix_y if inst.m_fix else None
+    fw = inst.w[m:] if inst.m_fix else None
+    fh = inst.h[m:] if inst.m_fix else None
+    rho, _, _ = oracle.density(inst.region, n, inst.target_density, inst.x, inst.y,
+                               inst.w[:m], inst.h[:m], fx, fy, fw, fh)
+    a = oracle.dct_coeffs(rho)
+    rng = np.random.default_rng(seed)
+    xs = rng.integers(0, n, count); ys = rng.integers(0, n, count)
+    psi, ex, ey = oracle.potential_at(a, inst.region[2] - inst.region[0],
+                                      inst.region[3] - inst.region[1], xs, ys)
+    return xs, ys, psi, ex, ey
+
+
 def test_tc_matches_fft_path_full_size(F):
-    """At 2048 x 2048 bins (2.2M cells) the oracle's maps are out of reach;
-    the two solve paths agree within the tensor-core path's bound."""
+    """At 2048 x 2048 bins (2.2M cells): psi, E_x, E_y at 64 sampled bins
+    against the oracle's series, and every output against the transform
+    path, within the tensor-core path's bound."""
     inst = synth.make_instance("precision")
     t = gpu_eval(F, inst, solve_path=F.FFTPL_SOLVE_TC_BF16X3)
+    xs, ys, psi, ex, ey = oracle_samples(inst, 64, 2048)
+    for k, ref in (("psi", psi), ("ex", ex), ("ey", ey)):
+        assert rel(t[k][ys, xs], ref) < TOL_TC, k
     f = gpu_eval(F, inst, solve_path=F.FFTPL_SOLVE_FFT)
     for k in ("psi", "ex", "ey"):
         assert rel(t[k], f[k]) < TOL_TC, k
@@ -234,6 +256,9 @@ def test_tc_largest_grid_matches_fft_path(F):
     inst.net_ptr = np.array([0, 2], np.int32); inst.pin_cell = np.array([0, 1], np.int32)
     inst.pin_dx = np.zeros(2, np.float32); inst.pin_dy = np.zeros(2, np.float32)
     t = gpu_eval(F, inst, solve_path=F.FFTPL_SOLVE_TC_BF16X3)
+    xs, ys, psi, ex, ey = oracle_samples(inst, 32, 4096)
+    for k, ref in (("psi", psi), ("ex", ex), ("ey", ey)):
+        assert rel(t[k][ys, xs], ref) < TOL_TC, k
     f = gpu_eval(F, inst, solve_path=F.FFTPL_SOLVE_FFT)
     for k in ("psi", "ex", "ey"):
         assert rel(t[k], f[k]) < TOL_TC, k
