@@ -41,7 +41,7 @@ def stage_bytes(m, n, P, E):
         "scatter": 16 * m + 8 * nn,           # x, y, w, h; zero + write D
         "rows_fwd": 12 * nn,                  # read D, M; write T1
         "cols": 12 * nn,                      # read T1; write PT, RT
-        "rows_inv": 20 * nn,                  # read PT, RT; write psi, E_x, E_y
+        "rows_inv": 16 * nn,                  # read PT, RT; write E_x, E_y (psi on demand)
         "wa": 12 * P + 4 * E + 16 * m,        # pins, net_ptr, x, y; gradient out
         "cells": 16 * m + 8 * nn + 16 * m,    # x, y, w, h, E_x, E_y; read gW, write gN
     }

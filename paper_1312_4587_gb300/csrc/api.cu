@@ -286,6 +286,7 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
         CK(launch_cells(c, xs, ys, gNx, gNy, gWx, gWy, s));
     } else {
         if (dens && grads) {
+            if ((what & EV_ADJOINT) && !c.tc) CK(launch_rows_psi(c, s));
             Stage st(c, 5, s);
             CK(launch_gather(c, xs, ys, gNx, gNy, (what & EV_ADJOINT) != 0, s));
         }
@@ -294,6 +295,17 @@ fftpl_status enqueue_eval(Ctx& c, const float* x, const float* y, float gamma, i
     c.rho_valid = false;
     c.split_valid = false;
     c.fields_valid = dens;
+    // the tensor-core solve writes psi; the adjoint gather formed it above
+    c.psi_valid = dens && (c.tc != nullptr || (what & EV_ADJOINT));
+    return FFTPL_OK;
+}
+
+// psi for the current fields: the transform path forms it from PT on demand.
+fftpl_status ensure_psi(Ctx& c, cudaStream_t s) {
+    if (!c.psi_valid) {
+        CK(launch_rows_psi(c, s));
+        c.psi_valid = true;
+    }
     return FFTPL_OK;
 }
 
@@ -812,6 +824,7 @@ fftpl_status fftpl_gather(fftpl_t h, const float* x, const float* y, int32_t mod
     if (c.m_mov > 0 && (!x || !y || !gx || !gy)) return set_err(c, FFTPL_EINVAL, "null argument");
     if (mode != 0 && mode != 1) return set_err(c, FFTPL_EINVAL, "mode must be 0 or 1");
     if (!c.fields_valid) return set_err(c, FFTPL_ESTATE, "no density evaluation yet");
+    if (mode == 1) TRY(ensure_psi(c, c.stream));
     CK(launch_gather(c, x, y, gx, gy, mode == 1, c.stream));
     return FFTPL_OK;
 }
@@ -868,6 +881,7 @@ static fftpl_status eval_impl(Ctx& c, const float* x, const float* y, float gamm
         c.fields_valid = true;
         c.rho_valid = false;
         c.split_valid = false;
+        c.psi_valid = c.tc != nullptr;
         return FFTPL_OK;
     }
     return enqueue_eval(c, x, y, gamma, what, gNx, gNy, gWx, gWy, stage);
@@ -954,7 +968,10 @@ fftpl_status fftpl_fields(fftpl_t h, const float** rho, const float** psi, const
         }
         *rho = c.rho;
     }
-    if (psi) *psi = c.psi;
+    if (psi) {
+        TRY(ensure_psi(c, c.stream));
+        *psi = c.psi;
+    }
     if (ex || ey) {
         if (!c.ex) {
             TRY(dalloc(c, &c.ex, (size_t)c.n * c.n));
@@ -1191,6 +1208,7 @@ fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32
     c.fields_valid = true;
     c.rho_valid = false;
     c.split_valid = false;
+    c.psi_valid = c.tc != nullptr;
     return FFTPL_OK;
 }
 

@@ -457,6 +457,8 @@ struct Ctx {
     int prof_used = 0;
 
     bool rho_valid = false, fields_valid = false, split_valid = false;
+    bool psi_valid = false;     // psi matches the current fields (the transform
+                                // path forms it on demand)
     std::string last_error;
     std::vector<void*> dev_allocs;
     size_t dev_bytes = 0;
@@ -495,6 +497,8 @@ cudaError_t launch_bin_ranges(Ctx& c, const float* x, const float* y, int32_t* r
 cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s);
 cudaError_t launch_cols_spectral(Ctx& c, cudaStream_t s);
 cudaError_t launch_rows_inv(Ctx& c, cudaStream_t s);
+// psi rows from PT (transform path; formed on demand, not in the evaluation)
+cudaError_t launch_rows_psi(Ctx& c, cudaStream_t s);
 cudaError_t launch_rho(Ctx& c, cudaStream_t s);
 cudaError_t launch_split_field(Ctx& c, cudaStream_t s);
 cudaError_t launch_q_to_f(const long long* q, float scale, float* out, int count, cudaStream_t s);

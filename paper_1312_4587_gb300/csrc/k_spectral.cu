@@ -13,7 +13,7 @@
 //   cols      : T1 rows  -> DCT-II along y -> divide -> inverse along y for P
 //               and R -> PT[y][u], RT[y][u] (written transposed); the energy
 //               N = 1/2 A_b sum B Psi (Parseval) is reduced here
-//   rows_inv  : PT, RT rows -> psi, E_x, E_y rows
+//   rows_inv  : PT, RT rows -> E_x, E_y rows (psi from PT on demand)
 //
 // Each 1-D cosine transform of length n is one complex FFT of length n
 // (Makhoul's reordering: v[k] = r[2k], v[n-1-k] = r[2k+1]; A[u] =
@@ -459,15 +459,17 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
 }
 
 // ------------------------------------------------- pass 3: inverse rows
-// CTA: 4 rows y.  Round A: psi (cosine sum of P) for two rows per IFFT and
-// E_y (cosine sum of R) for two rows per IFFT; E_y is parked in shared
-// memory.  Round B: E_x (sine sum of w_u P) for two rows per IFFT, written
-// with E_y as the interleaved field map E2[y][x] = (E_x, E_y).
+// CTA: 4 rows y, one round of four inverse FFTs: buffers 0 and 1 hold E_x
+// (the sine sum of w_u P, via reversed coefficients: c[u'] = s[N-u'],
+// u' >= 1, c[0] = 0, s[u] = w_u P[u]; E_x[x] = (-1)^x cosine-sum(c)[x]) for
+// rows (0, 1) and (2, 3); buffers 2 and 3 hold E_y (the cosine sum of R).
+// Written as the interleaved field map E2[y][x] = (E_x, E_y).  The potential
+// psi (the cosine sum of P) is not needed by the evaluation (the energy comes
+// from the column pass by Parseval) and is formed on demand by k_rows_psi.
 template <int LOGN>
 __global__ void __launch_bounds__(kSpecThreads, LOGN >= 12 ? 1 : 2)
-k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __restrict__ psi,
-           float2* __restrict__ E2, const float2* __restrict__ tw, const float2* __restrict__ ph,
-           float pi_lx) {
+k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float2* __restrict__ E2,
+           const float2* __restrict__ tw, const float2* __restrict__ ph, float pi_lx) {
     constexpr int N = 1 << LOGN;
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = NB;
@@ -475,64 +477,85 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float* __
     constexpr int HALF = N / 2 + 1;
     constexpr int NP = padded(N);
     extern __shared__ float2 sm[];
-    float* eys = reinterpret_cast<float*>(sm + NB * NP);  // E_y parked [ROWS][N]
     const int y0 = blockIdx.x * ROWS;
-    // round A: buffer 2f holds psi of rows (2f, 2f+1), buffer 2f+1 holds E_y
-#pragma unroll 4
+#pragma unroll 2
     for (int idx = threadIdx.x; idx < (ROWS / 2) * HALF; idx += T) {
         int f = idx / HALF, u = idx % HALF;
         int un = (N - u) & (N - 1);
-        const float* src[2] = {PT, RT};
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const float* A = src[q] + (size_t)(y0 + 2 * f) * N;
+        // E_y: cosine sums of the R rows (2f, 2f+1)
+        {
+            const float* A = RT + (size_t)(y0 + 2 * f) * N;
             const float* Bq = A + N;
             float au = A[u & (N - 1)], bu = Bq[u & (N - 1)];
             float an = (u > 0) ? A[un] : 0.0f, bn = (u > 0) ? Bq[un] : 0.0f;
             float cau = (u == 0) ? au : 0.5f * au, cbu = (u == 0) ? bu : 0.5f * bu;
             float can = 0.5f * an, cbn = 0.5f * bn;
             if (u == N / 2) { can = cau; cbn = cbu; }
-            float2* row = sm + (2 * f + q) * NP;
+            float2* row = sm + (2 + f) * NP;
             row[pidx(u & (N - 1))] = pack_inv(cau, can, cbu, cbn, ph[u]);
             if (u > 0 && u < N / 2) row[pidx(N - u)] = pack_inv(can, cau, cbn, cbu, ph[N - u]);
+        }
+        // E_x: reversed sine coefficients of the P rows (2f, 2f+1)
+        {
+            const float* Pa = PT + (size_t)(y0 + 2 * f) * N;
+            const float* Pb = Pa + N;
+            float wu = pi_lx * (float)u, wn = pi_lx * (float)(N - u);
+            // c[u] = s[N-u] = w_{N-u} P[N-u]  (u >= 1);  c[N-u] = s[u] = w_u P[u]
+            float ca_u = (u == 0) ? 0.0f : 0.5f * wn * Pa[N - u];
+            float cb_u = (u == 0) ? 0.0f : 0.5f * wn * Pb[N - u];
+            float ca_n = (u == 0) ? 0.0f : 0.5f * wu * Pa[u];
+            float cb_n = (u == 0) ? 0.0f : 0.5f * wu * Pb[u];
+            if (u == N / 2) { ca_n = ca_u; cb_n = cb_u; }
+            float2* row = sm + f * NP;
+            row[pidx(u & (N - 1))] = pack_inv(ca_u, ca_n, cb_u, cb_n, ph[u]);
+            if (u > 0 && u < N / 2) row[pidx(N - u)] = pack_inv(ca_n, ca_u, cb_n, cb_u, ph[N - u]);
         }
     }
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, true);
     for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
         int r = idx >> LOGN, x = idx & (N - 1);
-        int f = r >> 1;
         int k = pidx(mk_src(x, N));
-        float2 zp = sm[(2 * f) * NP + k], ze = sm[(2 * f + 1) * NP + k];
-        psi[(size_t)(y0 + r) * N + x] = (r & 1) ? zp.y : zp.x;
-        eys[r * N + x] = (r & 1) ? ze.y : ze.x;
+        float2 zx = sm[(r >> 1) * NP + k], zy = sm[(2 + (r >> 1)) * NP + k];
+        float vx = (r & 1) ? zx.y : zx.x, vy = (r & 1) ? zy.y : zy.x;
+        E2[(size_t)(y0 + r) * N + x] = make_float2((x & 1) ? -vx : vx, vy);
     }
-    __syncthreads();
-    // round B: E_x rows (2 per buffer).  c[u'] = s[N-u'] (u' >= 1), c[0] = 0,
-    // s[u] = w_u P[u]; E_x[x] = (-1)^x cosine-sum(c)[x].
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < (ROWS / 2) * HALF; idx += T) {
+}
+
+// psi on demand: CTA of 4 rows y, the cosine sums of the P rows (2f, 2f+1)
+// in buffer f.
+template <int LOGN>
+__global__ void __launch_bounds__(kSpecThreads, LOGN >= 12 ? 1 : 2)
+k_rows_psi(const float* __restrict__ PT, float* __restrict__ psi, const float2* __restrict__ tw,
+           const float2* __restrict__ ph) {
+    constexpr int N = 1 << LOGN;
+    constexpr int ROWS = kSpecBuffers;
+    constexpr int NB = ROWS / 2;
+    constexpr int T = kSpecThreads;
+    constexpr int HALF = N / 2 + 1;
+    constexpr int NP = padded(N);
+    extern __shared__ float2 sm[];
+    const int y0 = blockIdx.x * ROWS;
+    for (int idx = threadIdx.x; idx < NB * HALF; idx += T) {
         int f = idx / HALF, u = idx % HALF;
-        const float* Pa = PT + (size_t)(y0 + 2 * f) * N;
-        const float* Pb = Pa + N;
-        float wu = pi_lx * (float)u, wn = pi_lx * (float)(N - u);
-        // c[u] = s[N-u] = w_{N-u} P[N-u]  (u >= 1);  c[N-u] = s[u] = w_u P[u]
-        float ca_u = (u == 0) ? 0.0f : 0.5f * wn * Pa[N - u];
-        float cb_u = (u == 0) ? 0.0f : 0.5f * wn * Pb[N - u];
-        float ca_n = (u == 0) ? 0.0f : 0.5f * wu * Pa[u];
-        float cb_n = (u == 0) ? 0.0f : 0.5f * wu * Pb[u];
-        if (u == N / 2) { ca_n = ca_u; cb_n = cb_u; }
+        int un = (N - u) & (N - 1);
+        const float* A = PT + (size_t)(y0 + 2 * f) * N;
+        const float* Bq = A + N;
+        float au = A[u & (N - 1)], bu = Bq[u & (N - 1)];
+        float an = (u > 0) ? A[un] : 0.0f, bn = (u > 0) ? Bq[un] : 0.0f;
+        float cau = (u == 0) ? au : 0.5f * au, cbu = (u == 0) ? bu : 0.5f * bu;
+        float can = 0.5f * an, cbn = 0.5f * bn;
+        if (u == N / 2) { can = cau; cbn = cbu; }
         float2* row = sm + f * NP;
-        row[pidx(u & (N - 1))] = pack_inv(ca_u, ca_n, cb_u, cb_n, ph[u]);
-        if (u > 0 && u < N / 2) row[pidx(N - u)] = pack_inv(ca_n, ca_u, cb_n, cb_u, ph[N - u]);
+        row[pidx(u & (N - 1))] = pack_inv(cau, can, cbu, cbn, ph[u]);
+        if (u > 0 && u < N / 2) row[pidx(N - u)] = pack_inv(can, cau, cbn, cbu, ph[N - u]);
     }
     __syncthreads();
-    fft_block<LOGN, NB / 2>(sm, tw, true);
+    fft_block<LOGN, NB>(sm, tw, true);
     for (int idx = threadIdx.x; idx < ROWS * N; idx += T) {
         int r = idx >> LOGN, x = idx & (N - 1);
         float2 z = sm[(r >> 1) * NP + pidx(mk_src(x, N))];
-        float val = (r & 1) ? z.y : z.x;
-        E2[(size_t)(y0 + r) * N + x] = make_float2((x & 1) ? -val : val, eys[r * N + x]);
+        psi[(size_t)(y0 + r) * N + x] = (r & 1) ? z.y : z.x;
     }
 }
 
@@ -562,11 +585,12 @@ static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {
         kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.T1, c.PT, c.RT, c.tw, c.ph, pi_lx, pi_ly,
                                                         (float)c.opt.helmholtz_eps, c.acc,
                                                         det_red(c, 0));
-    } else {
+    } else if (which == 2) {
         auto kf = k_rows_inv<LOGN>;
-        size_t smem_inv = smem + (size_t)kSpecBuffers * N * sizeof(float);
-        kf<<<N / kSpecBuffers, kSpecThreads, smem_inv, s>>>(c.PT, c.RT, c.psi, c.E2, c.tw, c.ph,
-                                                            pi_lx);
+        kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.PT, c.RT, c.E2, c.tw, c.ph, pi_lx);
+    } else {
+        auto kf = k_rows_psi<LOGN>;
+        kf<<<N / kSpecBuffers, kSpecThreads, smem / 2, s>>>(c.PT, c.psi, c.tw, c.ph);
     }
     c.launches++;
     e = cudaGetLastError();
@@ -581,8 +605,8 @@ static void prepare_logn() {
     cudaFuncSetAttribute(k_rows_fwd<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_rows_fwd<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_cols<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_rows_inv<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem + (int)(kSpecBuffers * (1 << LOGN) * sizeof(float)));
+    cudaFuncSetAttribute(k_rows_inv<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_rows_psi<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem / 2);
 }
 
 void prepare_spectral(int logn) {
@@ -618,5 +642,6 @@ static cudaError_t dispatch(Ctx& c, int which, cudaStream_t s) {
 cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s) { return dispatch(c, 0, s); }
 cudaError_t launch_cols_spectral(Ctx& c, cudaStream_t s) { return dispatch(c, 1, s); }
 cudaError_t launch_rows_inv(Ctx& c, cudaStream_t s) { return dispatch(c, 2, s); }
+cudaError_t launch_rows_psi(Ctx& c, cudaStream_t s) { return dispatch(c, 3, s); }
 
 }  // namespace fftpl

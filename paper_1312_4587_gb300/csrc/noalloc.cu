@@ -153,6 +153,7 @@ extern "C" fftpl_status fftpl_solve_noalloc(const float* rho, int32_t n, double 
     if (e == cudaSuccess) e = launch_rows_fwd(c, s);
     if (e == cudaSuccess) e = launch_cols_spectral(c, s);
     if (e == cudaSuccess) e = launch_rows_inv(c, s);
+    if (e == cudaSuccess) e = launch_rows_psi(c, s);
     if (e == cudaSuccess) e = launch_split_field(c, s);
     if (e == cudaSuccess && N) {
         double acc[kAccDoubles];
