@@ -239,37 +239,44 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
     const int y0 = blockIdx.x * ROWS;
     // per-thread sums of at most 8 n / 256 non-negative terms in float32
     float tau = 0.0f, charge = 0.0f;
-    // ROWS*N values, 4 per thread and iteration (float4 loads), unrolled so
-    // that many loads are in flight
-    constexpr int V4 = ROWS * N / 4;
+    // Buffer f packs rows 2f (real part) and 2f+1 (imaginary part) in
+    // Makhoul's order: item p reads samples 2p and 2p+1 of both rows
+    // (8-byte loads, a warp reads 256 contiguous bytes of each row) and
+    // writes positions p and N-1-p (consecutive across the warp: no bank
+    // conflicts)
+    constexpr int ITEMS_IN = NB * (N / 2);
 #pragma unroll 4
-    for (int it = 0; it < (V4 + T - 1) / T; ++it) {
-        int q = threadIdx.x + it * T;
-        if (V4 % T != 0 && q >= V4) break;
-        int idx = 4 * q;
-        int r = idx >> LOGN, x = idx & (N - 1);
-        size_t b = (size_t)(y0 + r) * N + x;
-        float d4[4], m4[4];
-        float4 mv = *reinterpret_cast<const float4*>(M + b);
-        m4[0] = mv.x; m4[1] = mv.y; m4[2] = mv.z; m4[3] = mv.w;
+    for (int it = 0; it < (ITEMS_IN + T - 1) / T; ++it) {
+        const int q = threadIdx.x + it * T;
+        if (ITEMS_IN % T != 0 && q >= ITEMS_IN) break;
+        const int f = q / (N / 2), pp = q % (N / 2);
+        const size_t b0 = (size_t)(y0 + 2 * f) * N + 2 * pp, b1 = b0 + N;
+        float d[4], mm[4];
+        const float2 m0 = *reinterpret_cast<const float2*>(M + b0);
+        const float2 m1 = *reinterpret_cast<const float2*>(M + b1);
+        mm[0] = m0.x; mm[1] = m0.y; mm[2] = m1.x; mm[3] = m1.y;
         if (QUANT) {
-            longlong2 q0 = *reinterpret_cast<const longlong2*>(Dq + b);
-            longlong2 q1 = *reinterpret_cast<const longlong2*>(Dq + b + 2);
-            d4[0] = (float)q0.x * 2.3283064365386963e-10f;
-            d4[1] = (float)q0.y * 2.3283064365386963e-10f;
-            d4[2] = (float)q1.x * 2.3283064365386963e-10f;
-            d4[3] = (float)q1.y * 2.3283064365386963e-10f;
+            const longlong2 q0 = *reinterpret_cast<const longlong2*>(Dq + b0);
+            const longlong2 q1 = *reinterpret_cast<const longlong2*>(Dq + b1);
+            d[0] = (float)q0.x * 2.3283064365386963e-10f;
+            d[1] = (float)q0.y * 2.3283064365386963e-10f;
+            d[2] = (float)q1.x * 2.3283064365386963e-10f;
+            d[3] = (float)q1.y * 2.3283064365386963e-10f;
         } else {
-            float4 dv = *reinterpret_cast<const float4*>(D + b);
-            d4[0] = dv.x; d4[1] = dv.y; d4[2] = dv.z; d4[3] = dv.w;
+            const float2 v0 = *reinterpret_cast<const float2*>(D + b0);
+            const float2 v1 = *reinterpret_cast<const float2*>(D + b1);
+            d[0] = v0.x; d[1] = v0.y; d[2] = v1.x; d[3] = v1.y;
         }
-        float* row = reinterpret_cast<float*>(sm + (r >> 1) * NP);
+        float rv[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            tau += fmaxf(0.0f, d4[t] - (cap - m4[t]));
-            charge += d4[t] + m4[t];
-            row[2 * pidx(mk_pos(x + t, N)) + (r & 1)] = (d4[t] + m4[t]) * inv_ab;
+            tau += fmaxf(0.0f, d[t] - (cap - mm[t]));
+            charge += d[t] + mm[t];
+            rv[t] = (d[t] + mm[t]) * inv_ab;
         }
+        float2* buf = sm + f * NP;
+        buf[pidx(pp)] = make_float2(rv[0], rv[2]);
+        buf[pidx(N - 1 - pp)] = make_float2(rv[1], rv[3]);
     }
     reduce2(tau, charge, acc, ACC_TAU, ACC_CHARGE, dr);
     __syncthreads();
@@ -345,19 +352,19 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
     constexpr int NP = padded(N);
     extern __shared__ float2 sm[];
     const int u0 = blockIdx.x * ROWS;
-    constexpr int V4 = ROWS * N / 4;
+    // buffer f packs rows 2f, 2f+1 in Makhoul's order (as in k_rows_fwd)
+    constexpr int ITEMS_IN = (ROWS / 2) * (N / 2);
 #pragma unroll 4
-    for (int it = 0; it < (V4 + T - 1) / T; ++it) {
-        int q = threadIdx.x + it * T;
-        if (V4 % T != 0 && q >= V4) break;
-        int idx = 4 * q;
-        int r = idx >> LOGN, y = idx & (N - 1);
-        float4 v = *reinterpret_cast<const float4*>(T1 + (size_t)(u0 + r) * N + y);
-        float* row = reinterpret_cast<float*>(sm + (r >> 1) * NP);
-        row[2 * pidx(mk_pos(y + 0, N)) + (r & 1)] = v.x;
-        row[2 * pidx(mk_pos(y + 1, N)) + (r & 1)] = v.y;
-        row[2 * pidx(mk_pos(y + 2, N)) + (r & 1)] = v.z;
-        row[2 * pidx(mk_pos(y + 3, N)) + (r & 1)] = v.w;
+    for (int it = 0; it < (ITEMS_IN + T - 1) / T; ++it) {
+        const int q = threadIdx.x + it * T;
+        if (ITEMS_IN % T != 0 && q >= ITEMS_IN) break;
+        const int f = q / (N / 2), pp = q % (N / 2);
+        const size_t b0 = (size_t)(u0 + 2 * f) * N + 2 * pp;
+        const float2 a = *reinterpret_cast<const float2*>(T1 + b0);
+        const float2 c = *reinterpret_cast<const float2*>(T1 + b0 + N);
+        float2* buf = sm + f * NP;
+        buf[pidx(pp)] = make_float2(a.x, c.x);
+        buf[pidx(N - 1 - pp)] = make_float2(a.y, c.y);
     }
     __syncthreads();
     fft_block<LOGN, NB / 2>(sm, tw, false);

@@ -64,14 +64,67 @@ __device__ __forceinline__ float2 pin_xy(const WaIo& io, int c, float ox, float 
     return make_float2(__fadd_rn(p.x, ox), __fadd_rn(p.y, oy));
 }
 
+// One axis of a two-pin net, with d = |p1 - p2| and e = exp(-d/g) (the
+// per-net shift of Eq. 3 leaves the terms 1 and e): W~ = d (1 - e)/(1 + e)
+// = d tanh(d / 2g), and the pin at the maximum moves W~ by
+// dW~/dd = tanh(d/2g) + (d/2g) sech^2(d/2g) = (1 - e)/(1 + e) + 2 (d/g) e/(1 + e)^2
+// (the pin at the minimum by its negative).  LSE: W = d + 2 g ln(1 + e),
+// dW/dd = (1 - e)/(1 + e).  Returns W~ (or W - d for LSE); *g1 = gradient
+// of pin 1.
+template <bool LSE>
+__device__ __forceinline__ float wa_axis2(float p1, float p2, float l2g, float inv_g, float* g1) {
+    const float d = fabsf(p1 - p2);
+    const float e = exp2f(-d * l2g);
+    const float r = __fdividef(1.0f, 1.0f + e);   // 1 + e in [1, 2]
+    const float th = (1.0f - e) * r;
+    float gd, w;
+    if (LSE) {
+        gd = th;
+        w = __fdividef(2.0f, inv_g) * log1pf(e);
+    } else {
+        gd = fmaf(2.0f * d * inv_g * e, r * r, th);
+        w = d * th;
+    }
+    *g1 = p1 >= p2 ? gd : -gd;
+    return w;
+}
+
+template <bool CSR, bool LSE>
+__device__ __forceinline__ void wa_core2(const float (&rx)[2], const float (&ry)[2], int base,
+                                         const WaIo& io, float l2g, float inv_g, float& wsum,
+                                         float& hsum) {
+    float gx, gy;
+    const float wx = wa_axis2<LSE>(rx[0], rx[1], l2g, inv_g, &gx);
+    const float wy = wa_axis2<LSE>(ry[0], ry[1], l2g, inv_g, &gy);
+    const float span = fabsf(rx[0] - rx[1]) + fabsf(ry[0] - ry[1]);
+    hsum += span;
+    wsum += LSE ? span + (wx + wy) : wx + wy;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float sg = k == 0 ? 1.0f : -1.0f;
+        if (CSR) {
+            int sl = io.pin_slot[base + 32 * k];
+            if (sl >= 0) io.gpin[sl] = make_float2(sg * gx, sg * gy);
+        } else {
+            int c = io.pin_cell[base + 32 * k];
+            if (c >= 0) red_add_f2(io.gW + c, sg * gx, sg * gy);
+        }
+    }
+}
+
 // WA of one net whose D pin coordinates are in registers: max/min, the
 // exponential sums, W~ and HPWL into wsum/hsum, and the pin gradients out
 // (the pin's cell number, or its deterministic slot, is re-read at the pin's
 // slot base + 32 k: an L1 hit, cheaper than holding it in registers).
+// Two-pin nets (D = 2) take the closed form above.
 template <int D, bool CSR, bool LSE>
 __device__ __forceinline__ void wa_core(const float (&rx)[D], const float (&ry)[D], int base,
                                         const WaIo& io, float l2g, float inv_g, float& wsum,
                                         float& hsum) {
+    if constexpr (D == 2) {
+        wa_core2<CSR, LSE>(rx, ry, base, io, l2g, inv_g, wsum, hsum);
+        return;
+    }
     // the exponentials are recomputed in the gradient loop (the same
     // operations, so the same values) rather than held in 4 D registers
     float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;

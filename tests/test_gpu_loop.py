@@ -84,7 +84,9 @@ def test_two_hundred_iterations_statistics(F):
         _, _, rows, _ = oracle.nesterov(inst, 200, dw_ref=dw, x=xp)
         ens.append((rows[49]["hpwl"], rows[-1]["hpwl"], rows[-1]["tau"]))
     ens = np.array(ens)
-    gx, gy, grows, ran = run_gpu(F, inst, 200, dw_ref=dw)
+    # the same configuration as the oracle runs: gamma fixed at the tiny
+    # instance's 0.5 bin widths (the library's default is the schedule)
+    gx, gy, grows, ran = run_gpu(F, inst, 200, dw_ref=dw, gamma_fixed=inst.gamma)
     assert ran == 200
     for col, k in ((0, 49), (1, 199)):
         mean = ens[:, col].mean()
