@@ -212,11 +212,13 @@ def run_reference(args, ws, rank):
 
 
 def run_serving(args):
-    """Serving stream: Poisson arrivals (50 jobs/s) of placement jobs with
-    5K-500K cells (bins the next power of two >= sqrt(cells), 12 % macros),
-    300 iterations each, under a 150 GB budget, with continuous batching;
-    then the same jobs all at once (the server's capacity) and one at a
-    time for comparison."""
+    """The serving workload: Poisson arrivals at
+    50 jobs/s of 2,000 placement jobs with 5K-500K cells (log-uniform; bins
+    the next power of two >= sqrt(cells), 12 % macros), 300 iterations each,
+    under a 150 GB budget, with continuous batching.  The netlists come from a
+    pool of distinct seeded instances and every job draws its own start
+    positions.  Then the same jobs all at once (the server's capacity), and
+    the first jobs of the stream one at a time for comparison."""
     import numpy as np
 
     import synth
@@ -227,28 +229,34 @@ def run_serving(args):
     for k in range(args.serving_pool):
         cfg = synth.serving_job_config(rng)
         pool.append(synth.make_instance(cfg.name, seed=2000 + k, cfg=cfg))
-    jobs = [pool[k % len(pool)] for k in range(args.serving_jobs)]
+    jobs = [serve.with_start(pool[k % len(pool)], 5000 + k) for k in range(args.serving_jobs)]
     arrivals = serve.poisson_arrivals(rng, len(jobs), args.serving_rate)
-    out = {"jobs": len(jobs), "distinct_instances": len(pool), "arrival_rate_per_s": args.serving_rate,
-           "iters_per_job": args.serving_iters, "budget_GB": 150,
-           "cells": [int(min(j.m_mov for j in pool)), int(max(j.m_mov for j in pool))]}
-    with serve.Server(budget_bytes=150 << 30, max_active=64, iters_per_tick=5) as s:
-        st, _ = serve.run_stream(jobs, arrivals, args.serving_iters, s)
-    out.update({"jobs_per_s": st["jobs_per_s"], "iter_p50_ms": st["iter_p50_ms"],
+    cells = [j.m_mov for j in jobs]
+    out = {"jobs": len(jobs), "distinct_netlists": len(pool),
+           "start_positions": "one seeded Gaussian start per job",
+           "arrival_rate_per_s": args.serving_rate, "iters_per_job": args.serving_iters,
+           "budget_GB": 150, "cells": [int(min(cells)), int(max(cells))],
+           "mean_cells": float(np.mean(cells))}
+
+    def stats(st):
+        return {"jobs_per_s": st["jobs_per_s"], "iter_p50_ms": st["iter_p50_ms"],
                 "iter_p99_ms": st["iter_p99_ms"], "job_p50_ms": st["job_p50_ms"],
                 "job_p99_ms": st["job_p99_ms"], "peak_active": st["peak_active"],
-                "peak_device_GB": st["peak_device_bytes"] / 2**30, "failed": st["failed"]})
+                "peak_device_GB": st["peak_device_bytes"] / 2**30,
+                "completed": st["completed"], "failed": st["failed"]}
+
+    with serve.Server(budget_bytes=150 << 30, max_active=64, iters_per_tick=5) as s:
+        st, _ = serve.run_stream(jobs, arrivals, args.serving_iters, s)
+    out.update(stats(st))
     # capacity: the same jobs all submitted at once, continuously batched
     with serve.Server(budget_bytes=150 << 30, max_active=64, iters_per_tick=5) as s:
         stc, _ = serve.run_stream(jobs, np.zeros(len(jobs)), args.serving_iters, s)
-    out["saturated"] = {"jobs_per_s": stc["jobs_per_s"], "iter_p50_ms": stc["iter_p50_ms"],
-                        "iter_p99_ms": stc["iter_p99_ms"], "job_p50_ms": stc["job_p50_ms"],
-                        "job_p99_ms": stc["job_p99_ms"], "peak_active": stc["peak_active"]}
-    # the same jobs one at a time, back to back (all submitted at once)
+    out["saturated"] = stats(stc)
+    # the first jobs of the stream one at a time, back to back
+    k1 = min(len(jobs), args.serving_alone)
     with serve.Server(budget_bytes=150 << 30, max_active=1, iters_per_tick=5) as s:
-        st1, _ = serve.run_stream(jobs, np.zeros(len(jobs)), args.serving_iters, s)
-    out["alone"] = {"jobs_per_s": st1["jobs_per_s"], "iter_p50_ms": st1["iter_p50_ms"],
-                    "iter_p99_ms": st1["iter_p99_ms"]}
+        st1, _ = serve.run_stream(jobs[:k1], np.zeros(k1), args.serving_iters, s)
+    out["alone"] = dict(stats(st1), jobs=k1)
     return out
 
 
@@ -704,9 +712,12 @@ def main():
                     help="skip the per-result errors against the oracle")
     ap.add_argument("--no-tc-path", action="store_true",
                     help="skip the tensor-core solve path comparison")
-    ap.add_argument("--serving-jobs", type=int, default=200,
-                    help="jobs in the serving stream (0: skip; the full stream is 2000)")
-    ap.add_argument("--serving-pool", type=int, default=16)
+    ap.add_argument("--serving-jobs", type=int, default=2000,
+                    help="jobs in the serving stream (0: skip)")
+    ap.add_argument("--serving-pool", type=int, default=64,
+                    help="distinct netlists the stream's jobs draw from")
+    ap.add_argument("--serving-alone", type=int, default=200,
+                    help="jobs of the stream also run one at a time")
     ap.add_argument("--serving-rate", type=float, default=50.0)
     ap.add_argument("--serving-iters", type=int, default=300)
     args = ap.parse_args()

@@ -347,14 +347,19 @@ int64_t fftpl_launch_count(fftpl_t h);
 /* A stream of placement jobs served with continuous batching (build system
  * pattern; the paper places one design at a time).  Each job is one
  * instance plus start positions and an iteration count; it runs Algorithm 1
- * with the Nesterov step (as fftpl_step).  fftpl_server_tick admits queued
- * jobs while their device memory fits the budget and a slot is free, then
- * launches iters_per_tick iterations of every active job, each job on its
- * own stream so that jobs of different sizes run concurrently on the device,
- * waits for them, and retires finished jobs (final positions copied to the
- * host, device memory released).  Jobs that arrive while others run join at
- * the next tick.  With dry_run the server executes nothing on a GPU: each
- * launch only advances the job's count (admission, budget and latency
+ * with the Nesterov step (as fftpl_step), each iteration replayed from the
+ * job's captured loop graph on the job's own stream, so that jobs of
+ * different sizes run concurrently on the device.  fftpl_server_tick never
+ * waits for the device: it admits queued jobs in arrival order while their
+ * estimated device memory fits the budget and a slot is free (their handles
+ * are then created by worker threads), launches the next iters_per_tick
+ * iterations of every active job whose previous ones have completed (polled
+ * with events: no job waits for another), and hands finished jobs to the
+ * workers, which copy the final positions to the host and return the
+ * device memory to the library's stream-ordered pool without synchronising
+ * the device.  Jobs that arrive while others run join at the next tick.
+ * With dry_run the server executes nothing on a GPU: each launch completes
+ * at once and only advances the job's count (admission, budget and latency
  * bookkeeping can be exercised on any host, with fftpl_server_set_clock). */
 
 typedef struct fftpl_server* fftpl_server_t;
@@ -365,7 +370,8 @@ typedef struct {
     int32_t iters_per_tick;   /* loop iterations per job and tick (>= 1) */
     int32_t deterministic;    /* run every job in deterministic mode */
     int32_t dry_run;          /* bookkeeping only, no device work */
-    int32_t reserved[4];
+    int32_t workers;          /* threads that create and retire handles (0: 4) */
+    int32_t reserved[3];
 } fftpl_server_options;
 
 enum { FFTPL_JOB_QUEUED = 0, FFTPL_JOB_ACTIVE = 1, FFTPL_JOB_DONE = 2, FFTPL_JOB_FAILED = 3 };
@@ -404,7 +410,8 @@ fftpl_status fftpl_server_submit(fftpl_server_t s, const fftpl_region* region, i
                                  const fftpl_cells* cells, const fftpl_nets* nets,
                                  const fftpl_pins* pins, const fftpl_options* opt,
                                  const float* x0, const float* y0, int32_t iters, int64_t* id);
-/* One round of admit / launch / retire (synchronises the device). */
+/* One round of admit / launch / retire; returns without waiting for the
+ * device.  *active counts the jobs being created, running or retired. */
 fftpl_status fftpl_server_tick(fftpl_server_t s, int32_t* active, int32_t* queued);
 /* Job state; x, y (host, m_mov, may be NULL) receive the final positions
  * once the job is done. */

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -45,6 +46,73 @@ fftpl_status set_err(Ctx& c, fftpl_status st, const std::string& msg) {
     return st;
 }
 
+// Device memory of every handle comes from one stream-ordered pool per
+// device that keeps freed blocks for reuse (release threshold: never), so
+// that creating and destroying handles allocates with cudaMallocFromPoolAsync
+// and frees with cudaFreeAsync on the handle's stream: no call here waits
+// for the whole device (cudaMalloc / cudaFree synchronise it), and a server
+// retiring one job does not stall the others.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+
+cudaError_t device_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = ~0ULL;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// The small pinned host mirror of a handle's FP64 sums, from a process-wide
+// arena (page-locked allocations and frees synchronise the device, so the
+// slots are recycled instead).
+constexpr size_t kHostSlot = kAccDoubles * sizeof(double);
+std::mutex g_host_mu;
+std::vector<double*> g_host_free;
+
+cudaError_t host_slot(double** p) {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    if (g_host_free.empty()) {
+        constexpr int kSlots = 256;
+        char* block = nullptr;
+        cudaError_t e = cudaMallocHost((void**)&block, kSlots * kHostSlot);
+        if (e != cudaSuccess) return e;
+        for (int k = kSlots - 1; k >= 0; --k)
+            g_host_free.push_back(reinterpret_cast<double*>(block + k * kHostSlot));
+    }
+    *p = g_host_free.back();
+    g_host_free.pop_back();
+    return cudaSuccess;
+}
+
+void host_slot_release(double* p) {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    g_host_free.push_back(p);
+}
+
 template <typename T>
 fftpl_status dalloc(Ctx& c, T** p, size_t count) {
     *p = nullptr;
@@ -55,27 +123,31 @@ fftpl_status dalloc(Ctx& c, T** p, size_t count) {
             return set_err(c, FFTPL_ENOMEM, "injected allocation failure");
         }
     }
-    cudaError_t e = cudaMalloc((void**)p, bytes);
+    cudaError_t e = pool_alloc((void**)p, bytes, c.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
-        return set_err(c, FFTPL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return set_err(c, FFTPL_ENOMEM,
+                       std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
     }
     c.dev_allocs.push_back((void*)*p);
     c.dev_bytes += bytes;
     return FFTPL_OK;
 }
 
-// Device temporaries of one create call, freed when it returns.
+// Device temporaries of one create call, freed (in stream order) when it
+// returns.
 struct TempDev {
+    cudaStream_t s;
     std::vector<void*> ptrs;
+    explicit TempDev(cudaStream_t st) : s(st) {}
     ~TempDev() {
-        for (void* p : ptrs) cudaFree(p);
+        for (void* p : ptrs) cudaFreeAsync(p, s);
     }
     template <typename T>
     cudaError_t alloc(T** p, size_t count) {
         *p = nullptr;
-        cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+        cudaError_t e = pool_alloc((void**)p, std::max<size_t>(count, 1) * sizeof(T), s);
         if (e == cudaSuccess) ptrs.push_back((void*)*p);
         else cudaGetLastError();
         return e;
@@ -90,14 +162,19 @@ struct TempDev {
 
 bool finite_pos(float v) { return isfinite(v) && v > 0.0f; }
 
+// Waits for the handle's own streams only, then returns its device memory
+// to the pool in stream order.
 void free_ctx(fftpl_ctx* c) {
     if (!c) return;
-    if (c->stream || c->side) cudaDeviceSynchronize();
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
     if (c->eval_graph) cudaGraphExecDestroy(c->eval_graph);
     if (c->loop_graph) cudaGraphExecDestroy(c->loop_graph);
-    for (void* p : c->dev_allocs) cudaFree(p);
+    for (void* p : c->dev_allocs) cudaFreeAsync(p, c->stream);
+    if (!c->dev_allocs.empty() && c->stream) cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
     tc_free(*c);
-    if (c->acc_host) cudaFreeHost(c->acc_host);
+    if (c->acc_host) host_slot_release(c->acc_host);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
@@ -449,7 +526,7 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     const int m = c.m_mov, E = c.E;
     const int64_t P = c.P;
     cudaStream_t s = c.stream;
-    TempDev tmp;
+    TempDev tmp(s);
     int *d_np = nullptr, *d_pc = nullptr, *d_key = nullptr, *d_slot = nullptr;
     float *d_dx = nullptr, *d_dy = nullptr;
     CK(tmp.alloc(&d_np, (size_t)E + 1));
@@ -643,7 +720,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     CK(cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
-    CK(cudaMallocHost((void**)&c.acc_host, kAccDoubles * sizeof(double)));
+    CK(host_slot(&c.acc_host));
 
     size_t nn = (size_t)n * n;
     int mt = c.m_mov + c.m_fix;
@@ -712,13 +789,13 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     // fixed-cell map M = rho_t F (Section III-B), order-free int64 sums
     {
         long long* q = nullptr;
-        CK(cudaMalloc((void**)&q, nn * sizeof(long long)));
+        CK(pool_alloc((void**)&q, nn * sizeof(long long), s));
         cudaError_t e = cudaMemsetAsync(q, 0, nn * sizeof(long long), s);
         if (e == cudaSuccess && c.m_fix > 0)
             e = launch_scatter(c, c.fix_x, c.fix_y, c.w + c.m_mov, c.h + c.m_mov, c.m_fix, nullptr, q, s);
         if (e == cudaSuccess) e = launch_q_to_f(q, (float)c.opt.target_density, c.M, (int)nn, s);
+        cudaFreeAsync(q, s);
         cudaError_t e2 = cudaStreamSynchronize(s);
-        cudaFree(q);
         if (e == cudaSuccess) e = e2;
         CK(e);
     }
@@ -1119,8 +1196,8 @@ fftpl_status fftpl::loop_enqueue(Ctx& c) {
 // One loop iteration: replayed from a graph captured on first use when
 // use_graphs is set (every other input of the iteration lives on the device:
 // the control scalars, positions and the record counter).
-static fftpl_status loop_iter(Ctx& c) {
-    if (!c.opt.use_graphs || c.profiling) return loop_enqueue(c);
+fftpl_status fftpl::loop_iter(Ctx& c, bool launch) {
+    if (!c.opt.use_graphs || c.profiling) return launch ? loop_enqueue(c) : FFTPL_OK;
     const void* key[3] = {c.recs, c.gN, c.gW};
     if (!c.loop_graph || memcmp(key, c.loop_key, sizeof(key)) != 0) {
         if (c.loop_graph) {
@@ -1144,15 +1221,33 @@ static fftpl_status loop_iter(Ctx& c) {
         c.loop_graph_nkernels = c.launches - before;
         c.launches = before;  // counted at replay
     }
+    if (!launch) return FFTPL_OK;
     CK(cudaGraphLaunch(c.loop_graph, c.stream));
     c.launches += c.loop_graph_nkernels;
+    return FFTPL_OK;
+}
+
+fftpl_status fftpl::serve_prepare(Ctx& c, const float* x0, const float* y0, int iters) {
+    const size_t m = (size_t)c.m_mov;
+    if (!c.hx) {
+        TRY(dalloc(c, &c.hx, 2 * m));
+        c.hy = c.hx + m;
+    }
+    if (m) {
+        CK(cudaMemcpyAsync(c.hx, x0, m * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(c.hy, y0, m * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+    }
+    TRY(fftpl_place_init(&static_cast<fftpl_ctx&>(c), c.hx, c.hy));
+    TRY(loop_records(c, iters, 0.0));
+    TRY(loop_iter(c, false));
+    CK(cudaStreamSynchronize(c.stream));
     return FFTPL_OK;
 }
 
 fftpl_status fftpl::loop_records(Ctx& c, int cap, double base_k) {
     if (c.recs_cap < std::max(cap, 1)) {
         if (c.recs) {
-            cudaFree(c.recs);
+            cudaFreeAsync(c.recs, c.stream);
             c.dev_allocs.erase(std::find(c.dev_allocs.begin(), c.dev_allocs.end(), (void*)c.recs));
             c.dev_bytes -= (size_t)c.recs_cap * kRecFields * sizeof(double);
             c.recs = nullptr;
@@ -1161,7 +1256,8 @@ fftpl_status fftpl::loop_records(Ctx& c, int cap, double base_k) {
         c.recs_cap = std::max(cap, 1);
     }
     double hdr[2] = {(double)cap, base_k};
-    CK(cudaMemcpy(c.ctrl + C_REC_CAP, hdr, sizeof(hdr), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(c.ctrl + C_REC_CAP, hdr, sizeof(hdr), cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
     return FFTPL_OK;
 }
 
@@ -1181,7 +1277,7 @@ fftpl_status fftpl_step(fftpl_t h, int32_t iters, fftpl_iter_record* recs, int32
     // its remaining iterations' kernels in the queue
     constexpr int kChunk = 16;
     for (int it = 0; it < iters; it += kChunk) {
-        for (int j = it; j < std::min(iters, it + kChunk); ++j) TRY(loop_iter(c));
+        for (int j = it; j < std::min(iters, it + kChunk); ++j) TRY(loop_iter(c, true));
         if (c.opt.stop_on_tau && it + kChunk < iters) {
             double done = 0.0;
             CK(cudaMemcpyAsync(&done, c.ctrl + C_DONE, sizeof(double), cudaMemcpyDeviceToHost,

@@ -474,6 +474,13 @@ inline DetRed det_red(const Ctx& c, int r) {
 
 // Enqueues one placement-loop iteration on the handle's streams (no sync).
 fftpl_status loop_enqueue(Ctx& c);
+// One iteration replayed from the handle's loop graph (captured on first use
+// when use_graphs is set); launch = false only captures it.
+fftpl_status loop_iter(Ctx& c, bool launch);
+// For the server (on a worker thread): start positions from host memory,
+// loop initialisation, room for iters records and the loop graph; returns
+// with the handle's stream idle.
+fftpl_status serve_prepare(Ctx& c, const float* x0, const float* y0, int iters);
 // Makes room for cap iteration records and numbers them from base_k.
 fftpl_status loop_records(Ctx& c, int cap, double base_k);
 

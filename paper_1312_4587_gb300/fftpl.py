@@ -88,7 +88,7 @@ class fftpl_iter_record(C.Structure):
 class fftpl_server_options(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int32),
                 ("iters_per_tick", C.c_int32), ("deterministic", C.c_int32),
-                ("dry_run", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("dry_run", C.c_int32), ("workers", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class fftpl_job_info(C.Structure):

@@ -19,11 +19,11 @@ from . import fftpl as F
 
 class Server:
     def __init__(self, budget_bytes=150 << 30, max_active=64, iters_per_tick=1,
-                 deterministic=False, dry_run=False):
+                 deterministic=False, dry_run=False, workers=4):
         self.options = F.fftpl_server_default_options(
             hbm_budget_bytes=int(budget_bytes), max_active=int(max_active),
             iters_per_tick=int(iters_per_tick), deterministic=int(bool(deterministic)),
-            dry_run=int(bool(dry_run)))
+            dry_run=int(bool(dry_run)), workers=int(workers))
         self.s = F.fftpl_server_create(self.options)
         self.m = {}
 
@@ -67,6 +67,19 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def with_start(inst, seed):
+    """The instance with its own seeded Gaussian start positions (a distinct
+    placement job on the same netlist)."""
+    import copy
+
+    import synth
+    j = copy.copy(inst)
+    m = inst.m_mov
+    j.x, j.y = synth.gaussian_start(np.random.default_rng(seed), inst.region, inst.w[:m],
+                                    inst.h[:m])
+    return j
 
 
 def poisson_arrivals(rng, count, rate_per_s):
