@@ -169,7 +169,15 @@ typedef struct {
                                mode divided by w_u^2 + w_v^2 + eps and the
                                (0,0) mode kept as a_00 / eps (placement
                                units^-2; finite, >= 0, else FFTPL_EINVAL) */
-    int32_t reserved[2];
+    double alpha_max_cap_bins; /* Nesterov loop: the step bound alpha_max never
+                               exceeds this many bin widths (> 0; 0: no
+                               bound; default 16).  The rule alpha_max =
+                               max(alpha_max_0, 2 a) of Section IV-A was
+                               made for the paper's line search; the
+                               Barzilai-Borwein steps have none, and without
+                               a ceiling their largest moves doubled up to
+                               the region's size on the 210K- and 2.2M-cell
+                               instances */
 } fftpl_options;
 
 /* FP64 scalars of one evaluation. */

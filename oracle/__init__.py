@@ -70,7 +70,8 @@ class LoopOpts(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("gamma_fixed", C.c_double),
                 ("dw_ref", C.c_double), ("alpha_max0_bins", C.c_double),
                 ("stop_on_tau", C.c_int), ("tau_stop", C.c_double),
-                ("wirelength", C.c_int), ("helmholtz_eps", C.c_double)]
+                ("wirelength", C.c_int), ("helmholtz_eps", C.c_double),
+                ("alpha_max_cap_bins", C.c_double)]
 
 # wirelength models
 WL_WA, WL_LSE = 0, 1
@@ -341,7 +342,7 @@ def nesterov(inst, iters, **kw):
 
 
 def nesterov_run(x0, lo, hi, wb, objective, iters, lambda0=0.0, gamma_fixed=1.0, dw_ref=3.5e5,
-                 alpha_max0_bins=0.044, stop_on_tau=False, tau_stop=0.1):
+                 alpha_max0_bins=0.044, stop_on_tau=False, tau_stop=0.1, alpha_max_cap_bins=0.0):
     """The loop of orc_nesterov (Nesterov step, Section IV-A control) on an
     objective given as a Python callable objective(v, gamma) -> dict with
     gW, gN (arrays like v) and W, hpwl, N, tau, gN_l1, gW_l1 (gamma == 0 and
@@ -362,7 +363,7 @@ def nesterov_run(x0, lo, hi, wb, objective, iters, lambda0=0.0, gamma_fixed=1.0,
 
     fn = ObjectiveFn(cb)
     opts = LoopOpts(float(lambda0), float(gamma_fixed), float(dw_ref), float(alpha_max0_bins),
-                    int(stop_on_tau), float(tau_stop), 0, 0.0)
+                    int(stop_on_tau), float(tau_stop), 0, 0.0, float(alpha_max_cap_bins))
     recs = (IterRec * max(iters, 1))()
     ran = lib().orc_nesterov_run(C.c_int(nv), _ptr(x), _ptr(lo), _ptr(hi), C.c_double(wb), fn,
                                  None, C.byref(opts), C.c_int(iters), C.cast(recs, _P))
@@ -380,7 +381,7 @@ def cg(inst, iters, **kw):
 
 def _loop(fn, inst, iters, lambda0=0.0, gamma_fixed=None, dw_ref=3.5e5, alpha_max0_bins=0.044,
           stop_on_tau=False, tau_stop=0.1, x=None, y=None, wirelength=WL_WA,
-          helmholtz_eps=0.0):
+          helmholtz_eps=0.0, alpha_max_cap_bins=16.0):
     m, k, w, h, fw, fh = _inst_arrays(inst)
     x = _f32(inst.x if x is None else x).copy()
     y = _f32(inst.y if y is None else y).copy()
@@ -390,7 +391,8 @@ def _loop(fn, inst, iters, lambda0=0.0, gamma_fixed=None, dw_ref=3.5e5, alpha_ma
     dx, dy = _f32(inst.pin_dx), _f32(inst.pin_dy)
     gf = inst.gamma if gamma_fixed is None else gamma_fixed
     opts = LoopOpts(float(lambda0), float(gf), float(dw_ref), float(alpha_max0_bins),
-                    int(stop_on_tau), float(tau_stop), int(wirelength), float(helmholtz_eps))
+                    int(stop_on_tau), float(tau_stop), int(wirelength), float(helmholtz_eps),
+                    float(alpha_max_cap_bins))
     recs = (IterRec * max(iters, 1))()
     R = _region(inst.region)
     ran = getattr(lib(), fn)(C.byref(R), C.c_int(inst.n), C.c_double(inst.target_density),

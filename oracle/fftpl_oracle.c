@@ -703,6 +703,7 @@ typedef struct {
     double tau_stop;     /* 0.1 */
     int wirelength;      /* 0 weighted average (Eq. 3), 1 log-sum-exp */
     double helmholtz_eps; /* 0 Poisson (Eq. 8), > 0 Helmholtz (Eq. 4) */
+    double alpha_max_cap_bins; /* Nesterov loop: alpha_max <= this many bins (0: none) */
 } orc_loop_opts;
 
 /* The objective as the loop sees it: at the point v (nvar doubles, all x
@@ -734,8 +735,17 @@ typedef void (*orc_objective_fn)(void* ctx, const double* v, double gamma, doubl
  *   u_{k+1} = Pi(v_k - alpha_k g_k)
  *   a_{k+1} = (1 + sqrt(1 + 4 a_k^2))/2, beta = (a_k - 1)/a_{k+1}
  *   v_{k+1} = Pi(u_{k+1} + beta (u_{k+1} - u_k))
- *   alpha_max_{k+1} = max(alpha_max_0, 2 max_i |u_{k+1} - v_k|)
- *   gamma_{k+1} = gamma(tau_k) unless fixed. */
+ *   alpha_max_{k+1} = max(alpha_max_0, 2 max_i |u_{k+1} - v_k|), kept at
+ *   or below max(alpha_max_0, cap wb) when the option's cap (bins) is > 0:
+ *   the doubling rule of Section IV-A was made for the paper's line search,
+ *   and with Barzilai-Borwein steps alone the largest move can double every
+ *   iteration up to the size of the region
+ *   gamma_{k+1} = gamma(tau_k) unless fixed.
+ * Adaptive restart (the gradient test of O'Donoghue and Candes, "Adaptive
+ * restart for accelerated gradient schemes", 2015), taken one iteration
+ * late: when g_k . (u_{k+1} - u_k) > 0 the step went uphill for the
+ * gradient at v_k, and the sequence starts over, a_{k+1} := 1, so that the
+ * next momentum weight is 0. */
 int orc_nesterov_run(int nvar, double* x, const double* lo, const double* hi, double wb,
                      orc_objective_fn f, void* ctx, const orc_loop_opts* o, int iters,
                      orc_iter_rec* recs) {
@@ -787,16 +797,18 @@ int orc_nesterov_run(int nvar, double* x, const double* lo, const double* hi, do
         }
         double a_next = orc_nesterov_a(a_k);
         double beta = (a_k - 1.0) / a_next;
-        double step_max = 0.0;
+        double step_max = 0.0, uphill = 0.0;
         for (size_t i = 0; i < m2; ++i) {
             double un = dmin(hi[i], dmax(lo[i], v[i] - alpha * g[i]));
             step_max = dmax(step_max, fabs(un - v[i]));
+            uphill += g[i] * (un - u[i]);
             double vn = dmin(hi[i], dmax(lo[i], un + beta * (un - u[i])));
             vp[i] = v[i];
             gp[i] = g[i];
             u[i] = un;
             v[i] = vn;
         }
+        if (uphill > 0.0) a_next = 1.0;
         if (recs) {
             recs[k].W = ev.W; recs[k].hpwl = ev.hpwl; recs[k].N = ev.N; recs[k].tau = ev.tau;
             recs[k].lambda = lambda; recs[k].gamma = gamma; recs[k].alpha = alpha;
@@ -804,6 +816,8 @@ int orc_nesterov_run(int nvar, double* x, const double* lo, const double* hi, do
         }
         a_k = a_next;
         alpha_max = dmax(alpha_max0, 2.0 * step_max);
+        if (o->alpha_max_cap_bins > 0.0)
+            alpha_max = dmin(alpha_max, dmax(alpha_max0, o->alpha_max_cap_bins * wb));
         if (o->gamma_fixed <= 0.0) gamma = orc_gamma(ev.tau, wb);
         if (o->stop_on_tau && ev.tau <= o->tau_stop) { ++k; break; }
     }

@@ -248,6 +248,8 @@ fftpl_status validate(Ctx& c, const fftpl_region* R, int n, const fftpl_cells* c
             return set_err(c, FFTPL_EINVAL, "unknown optimizer");
         if (!(opt->helmholtz_eps >= 0.0) || !isfinite(opt->helmholtz_eps))
             return set_err(c, FFTPL_EINVAL, "helmholtz_eps must be finite and >= 0");
+        if (!(opt->alpha_max_cap_bins >= 0.0) || !isfinite(opt->alpha_max_cap_bins))
+            return set_err(c, FFTPL_EINVAL, "alpha_max_cap_bins must be finite and >= 0");
     }
     return FFTPL_OK;
 }
@@ -440,6 +442,7 @@ void fftpl_default_options(fftpl_options* o) {
     o->wirelength = FFTPL_WL_WA;
     o->optimizer = FFTPL_OPT_NESTEROV;
     o->helmholtz_eps = 0.0;
+    o->alpha_max_cap_bins = 16.0;
 }
 
 fftpl_status fftpl_fillers(const fftpl_region* R, const fftpl_cells* cells,
@@ -1118,6 +1121,7 @@ fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
     ctrl[C_WB] = c.wb;
     ctrl[C_HALF_AB] = 0.5 * c.Ab;
     ctrl[C_MOV_AREA] = c.mov_area > 0 ? c.mov_area : 1.0;
+    ctrl[C_ALPHA_CAP] = c.opt.alpha_max_cap_bins * c.wb;
     cudaStream_t s = c.stream;
     CK(cudaMemcpyAsync(c.ctrl, ctrl.data(), ctrl.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(launch_place_init(c, x0, y0, s));

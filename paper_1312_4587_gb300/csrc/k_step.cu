@@ -82,7 +82,7 @@ k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
     if (b.ctrl[C_DONE] != 0.0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float alpha = (float)b.ctrl[C_ALPHA], beta = (float)b.ctrl[C_BETA];
-    float step = 0.0f;
+    float step = 0.0f, uphill = 0.0f;
     if (i < 2 * m) {
         bool isx = i < m;
         int c = isx ? i : i - m;
@@ -91,6 +91,7 @@ k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
         float vi = b.v[i], gi = b.g[i], ui = b.u[i];
         float un = fminf(hi, fmaxf(lo, vi - alpha * gi));
         step = fabsf(un - vi);
+        uphill = gi * (un - ui);
         float vn = fminf(hi, fmaxf(lo, un + beta * (un - ui)));
         b.vprev[i] = vi;
         b.gprev[i] = gi;
@@ -98,6 +99,8 @@ k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
         b.v[i] = vn;
     }
     block_max(step, b.acc, ACC_STEPMAX);
+    // g_k . (u_{k+1} - u_k) for the adaptive restart (ctrl_record)
+    reduce2(uphill, 0.0f, b.acc, ACC_GD, -1, b.dr);
     if (last_cta(b.counters + 2) && threadIdx.x == 0) ctrl_record(b.ctrl, b.acc, b.recs);
 }
 

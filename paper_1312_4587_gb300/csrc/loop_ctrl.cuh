@@ -16,6 +16,7 @@ enum {
     // conjugate-gradient loop: |g_{k-1}|^2, f_k, slope along d/|d|_inf,
     // |d|_inf, restart flag, and the values recorded for iteration k
     C_GG_PREV, C_FK, C_SLOPE, C_DINF, C_RESTART, C_W_K, C_HP_K, C_N_K, C_TAU_K,
+    C_ALPHA_CAP,   // ceiling of alpha_max in the Nesterov loop (0: none)
     C_COUNT
 };
 constexpr int kRecFields = 8;
@@ -98,7 +99,11 @@ __device__ __forceinline__ double gamma_schedule(double tau, double wb) {
 }
 
 // After the position update: record iteration k, then alpha_max_{k+1},
-// gamma_{k+1}, k+1 and the stop test tau <= tau_stop.
+// gamma_{k+1}, k+1 and the stop test tau <= tau_stop.  Adaptive restart
+// (the gradient test of O'Donoghue and Candes, 2015), one iteration late:
+// when g_k . (u_{k+1} - u_k) > 0 the momentum sequence starts over,
+// a_{k+1} = 1, so that the next momentum weight is 0.  alpha_max_{k+1} is
+// kept at or below the handle's ceiling (alpha_max_cap_bins bin widths).
 __device__ __forceinline__ void ctrl_record(double* ctrl, const double* acc, double* recs) {
     int k = (int)ctrl[C_K];
     double tau = acc_sum(acc, ACC_TAU) / ctrl[C_MOV_AREA];
@@ -115,8 +120,10 @@ __device__ __forceinline__ void ctrl_record(double* ctrl, const double* acc, dou
         r[6] = ctrl[C_ALPHA];
         r[7] = step_max;
     }
-    ctrl[C_A] = ctrl[C_A_NEXT];
-    ctrl[C_ALPHA_MAX] = fmax(ctrl[C_ALPHA_MAX0], 2.0 * step_max);
+    ctrl[C_A] = acc_sum(acc, ACC_GD) > 0.0 ? 1.0 : ctrl[C_A_NEXT];
+    double amax = fmax(ctrl[C_ALPHA_MAX0], 2.0 * step_max);
+    if (ctrl[C_ALPHA_CAP] > 0.0) amax = fmin(amax, fmax(ctrl[C_ALPHA_CAP], ctrl[C_ALPHA_MAX0]));
+    ctrl[C_ALPHA_MAX] = amax;
     if (ctrl[C_GAMMA_FIXED] <= 0.0) ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
     ctrl[C_K] = (double)(k + 1);
     if (ctrl[C_STOP_ON_TAU] != 0.0 && tau <= ctrl[C_TAU_STOP]) ctrl[C_DONE] = 1.0;

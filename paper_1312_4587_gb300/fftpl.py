@@ -63,7 +63,7 @@ class fftpl_options(C.Structure):
                 ("alpha_max0_bins", C.c_double), ("tau_stop", C.c_double),
                 ("stop_on_tau", C.c_int32), ("use_graphs", C.c_int32),
                 ("wirelength", C.c_int32), ("optimizer", C.c_int32),
-                ("helmholtz_eps", C.c_double), ("reserved", C.c_int32 * 2)]
+                ("helmholtz_eps", C.c_double), ("alpha_max_cap_bins", C.c_double)]
 
 
 class fftpl_eval_report(C.Structure):

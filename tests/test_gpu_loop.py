@@ -124,3 +124,20 @@ def test_state_save_and_resume(F):
         F.fftpl_place_positions(p.h, xb, yb)
     assert torch.equal(xa, xb) and torch.equal(ya, yb)
     assert [r["hpwl"] for r in rows_a] == [r["hpwl"] for r in rows_b]
+
+
+def test_first_iterations_match_oracle_large(F):
+    """The 210K-cell instance with the library's default loop options (gamma
+    schedule, dw_ref 3.5e5, the alpha_max ceiling): 10 iterations against the
+    oracle's loop, positions within 1e-4 relative L2, the sums within 1e-4."""
+    inst = synth.make_instance("large")
+    ox, oy, orows, oran = oracle.nesterov(inst, 10, gamma_fixed=0.0)
+    gx, gy, grows, gran = run_gpu(F, inst, 10)
+    assert gran == oran == 10
+    assert rel(np.concatenate([gx, gy]), np.concatenate([ox, oy])) < 1e-4
+    for k in range(10):
+        for key, rtol, atol in (("hpwl", 1e-4, 0), ("W", 1e-4, 0), ("N", 1e-4, 0),
+                                ("lam", 1e-4, 0), ("gamma", 1e-4, 0), ("tau", 0, 1e-4),
+                                ("alpha", 1e-3, 0), ("step_max", 1e-3, 0)):
+            a, b = grows[k][key], orows[k][key]
+            assert abs(a - b) <= rtol * abs(b) + atol, (k, key, a, b)

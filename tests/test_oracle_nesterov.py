@@ -149,3 +149,53 @@ def test_stop_on_overflow(orc):
                                     alpha_max0_bins=1.0, stop_on_tau=True, tau_stop=0.085)
     assert ran == 3
     assert [r["tau"] for r in rows] == pytest.approx([0.1, 0.09, (7 - 2 * B1) / 100], rel=1e-12)
+
+
+def test_adaptive_restart(orc):
+    """Scripted gradients g = -1, -1, 0.001, -1, -1 from x_0 = 0 (alpha_max_0 = 1):
+    k=0: alpha = 1, u_1 = v_1 = 1.  k=1: dg = 0 keeps alpha = 1, u_2 = 2,
+    v_2 = 2 + beta_1.  k=2: the BB ratio moves 0.00128, below 0.01 alpha_max =
+    0.02, so alpha = 20 and u_3 = v_2 - 0.02 = 1.98 + beta_1 > u_2: the step went
+    up the gradient (g_2 (u_3 - u_2) > 0), so the sequence restarts after
+    v_3 = u_3 + beta_2 (u_3 - u_2) is formed: a_3 = 1, and the momentum weight
+    of iteration 3 is 0, so v_4 = u_4 exactly (without the restart it would be
+    u_4 + (a_3 - 1)/a_4 (u_4 - u_3))."""
+    grads = [-1.0, -1.0, 0.001, -1.0, -1.0]
+    seen = []
+
+    def objective(v, gamma):
+        k = len(seen)
+        seen.append(float(v[0]))
+        g = np.array([grads[k]])
+        return dict(gW=g, gN=np.zeros(1), W=0.0, hpwl=0.0, N=0.0, tau=0.5, gW_l1=1.0, gN_l1=1.0)
+
+    u, rows, ran = orc.nesterov_run([0.0], [-100.0], [100.0], 1.0, objective, 5, lambda0=1.0,
+                                    alpha_max0_bins=1.0)
+    assert ran == 5
+    u3 = 2 + B1 - 0.02
+    v3 = u3 + B2 * (u3 - 2)
+    assert seen[:4] == pytest.approx([0.0, 1.0, 2 + B1, v3], rel=1e-12, abs=1e-15)
+    assert rows[2]["alpha"] == pytest.approx(20.0, rel=1e-9)
+    # iteration 3: BB ratio |v_3 - v_2| / |g_3 - g_2|, inside [0.01, 1] alpha_max
+    a3 = abs(v3 - (2 + B1)) / 1.001
+    u4 = v3 + a3
+    assert rows[3]["alpha"] == pytest.approx(a3, rel=1e-12)
+    assert seen[4] == pytest.approx(u4, rel=1e-12)
+
+
+def test_step_bound_ceiling(orc):
+    """alpha_max doubles with the last largest move but not past the ceiling:
+    c = 2 from x_0 = 10, alpha_max_0 = 1, ceiling 3 bins (w_b = 1).
+    k=0: move 1 -> alpha_max 2.  k=1: alpha = 2/18, move 2 -> alpha_max
+    min(4, 3) = 3.  k=2: alpha = 3 / g_2 with g_2 = 2 v_2, move 3 -> alpha_max
+    min(6, 3) = 3 again (without the ceiling: 4, then 8)."""
+    _, rows, _ = orc.nesterov_run([10.0], [-100.0], [100.0], 1.0, quad(2.0), 4, lambda0=1.0,
+                                  alpha_max0_bins=1.0, alpha_max_cap_bins=3.0)
+    v2 = 7 - 2 * B1
+    assert [r["step_max"] for r in rows[:3]] == pytest.approx([1.0, 2.0, 3.0], rel=1e-12)
+    assert rows[2]["alpha"] == pytest.approx(3.0 / (2 * v2), rel=1e-12)
+    u3 = v2 - 3.0
+    v3 = u3 + B2 * (u3 - 7.0)
+    # k=3: the BB ratio 1/2 moves |v_3| (about 1.9), inside [0.03, 3]
+    assert rows[3]["alpha"] == pytest.approx(0.5, rel=1e-12)
+    assert rows[3]["step_max"] == pytest.approx(abs(v3), rel=1e-12)
