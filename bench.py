@@ -267,13 +267,21 @@ def tc_flops(n):
     return 2 * 3 * 7 * n ** 3
 
 
-def run_tc_path(args, inst, x, y, g, flush, stream):
-    """The same step on solve_path FFTPL_SOLVE_TC_BF16X3 (its own handle):
-    per-step time and the tensor-core stages against the bf16 peak."""
+def tcr_flops(n):
+    """FLOPs of one radix tensor-core solve: DFTs of 3 n rows in all (n/2 along
+    x, n/2 + n along y, n along x back), each row 2 products of 2 x 128 x 128
+    x n/64 multiply-adds, three bf16 products each."""
+    return 3 * n * (2 * 2 * 128 * 128 * (n // 64)) * 3
+
+
+def run_tc_path(args, inst, x, y, g, flush, stream, radix=False):
+    """The same step on a tensor-core solve path (its own handle): the dense
+    products (FFTPL_SOLVE_TC_BF16X3) or the radix DFTs (FFTPL_SOLVE_TC_RADIX);
+    per-step time and the solve's stages against the bf16 peak."""
     import torch
     from paper_1312_4587_gb300 import fftpl as F
-    prob = F.Problem(inst, use_graphs=0 if args.no_graphs else 1,
-                     solve_path=F.FFTPL_SOLVE_TC_BF16X3)
+    path = F.FFTPL_SOLVE_TC_RADIX if radix else F.FFTPL_SOLVE_TC_BF16X3
+    prob = F.Problem(inst, use_graphs=0 if args.no_graphs else 1, solve_path=path)
     h = prob.h
     for _ in range(max(3, args.warmup)):
         F.fftpl_eval(h, x, y, inst.gamma, *g, sync=False)
@@ -300,10 +308,11 @@ def run_tc_path(args, inst, x, y, g, flush, stream):
     prob.close()
     solve_ms = sum(st[i] / max(nl[i], 1) for i in (1, 2, 3))
     _, bf16, kind = load_peaks()
-    tflops = tc_flops(inst.n) / (solve_ms * 1e-3) / 1e12
-    return {"solve_path": "tc_bf16x3", "ms_per_step": round(ms, 5),
+    flops = tcr_flops(inst.n) if radix else tc_flops(inst.n)
+    tflops = flops / (solve_ms * 1e-3) / 1e12
+    return {"solve_path": "tc_radix" if radix else "tc_bf16x3", "ms_per_step": round(ms, 5),
             "value": round(1000.0 / ms, 2), "unit": UNIT,
-            "solve_ms": round(solve_ms, 5), "solve_flops": tc_flops(inst.n),
+            "solve_ms": round(solve_ms, 5), "solve_flops": flops,
             "roofline": {"bound": "tensor", "achieved": round(tflops, 1),
                          "peak": bf16, "unit": "TFLOP/s",
                          "frac": round(tflops / bf16, 4),
@@ -681,6 +690,8 @@ def run_ours(args, ws, rank, local):
         line["variants"]["fillers"] = run_fillers(args, inst, flush, stream)
     if not args.no_tc_path and n >= F.FFTPL_TC_MIN_N:
         line["tc_path"] = run_tc_path(args, inst, x, y, g, flush, stream)
+    if not args.no_tc_path and n >= F.FFTPL_TCR_MIN_N:
+        line["tc_radix_path"] = run_tc_path(args, inst, x, y, g, flush, stream, radix=True)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baselines(inst)
         line["cpu_baseline"] = cb[0]

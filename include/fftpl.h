@@ -118,14 +118,27 @@ typedef struct {
  * hi*hi + hi*lo + lo*hi in float32 (relative error about 1e-5 per product,
  * against 1e-7 for the FFT path).  It costs 42 n^3 flops per solve (the FFT
  * path O(n^2 log n)), needs n >= FFTPL_TC_MIN_N, and holds 36 n^2 extra
- * bytes of device memory (bf16 tables and intermediates). */
+ * bytes of device memory (bf16 tables and intermediates).
+ * FFTPL_SOLVE_TC_RADIX keeps the transform path's passes (Makhoul's
+ * reordering of each cosine or sine transform into a complex DFT of length
+ * n, two real rows per DFT) and computes every DFT on the tensor cores as two
+ * small dense products of a four-step factorisation n = 64 n2: 64-point
+ * DFTs (a 128 x 128 real block), twiddles exp(-+2 pi i j2 k1 / n) in that
+ * product's epilogue, then n2-point DFTs (block-diagonal over 64 / n2 rows),
+ * with the same bf16 x 3 split and FP32 accumulation: 3072 R n flops for
+ * the DFTs of R rows (6.4 GFLOP for the n / 2 rows of one pass at n = 2048)
+ * instead of the dense form's O(n^3).  Needs n >= 256 and
+ * holds 48 n^2 extra bytes of device memory. */
 enum {
-    FFTPL_SOLVE_FFT = 0,      /* real-to-real transforms built on FP32 FFTs */
-    FFTPL_SOLVE_TC_BF16X3 = 1 /* dense DCT matrices on tcgen05 tensor cores,
-                                 operands split into bf16 hi+lo, 3 products,
-                                 FP32 accumulation */
+    FFTPL_SOLVE_FFT = 0,       /* real-to-real transforms built on FP32 FFTs */
+    FFTPL_SOLVE_TC_BF16X3 = 1, /* dense DCT matrices on tcgen05 tensor cores,
+                                  operands split into bf16 hi+lo, 3 products,
+                                  FP32 accumulation */
+    FFTPL_SOLVE_TC_RADIX = 2   /* the transform path's DFTs as radix-64 x n/64
+                                  products on tcgen05 tensor cores, bf16 x 3 */
 };
 #define FFTPL_TC_MIN_N 128
+#define FFTPL_TCR_MIN_N 256
 
 /* Wirelength models.  FFTPL_WL_WA: the weighted average of Eq. 3.
  * FFTPL_WL_LSE: the log-sum-exp model Section II names, per net and axis

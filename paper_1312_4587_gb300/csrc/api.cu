@@ -174,6 +174,7 @@ void free_ctx(fftpl_ctx* c) {
     if (!c->dev_allocs.empty() && c->stream) cudaStreamSynchronize(c->stream);
     cudaGetLastError();
     tc_free(*c);
+    tcr_free(*c);
     if (c->acc_host) host_slot_release(c->acc_host);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -237,10 +238,13 @@ fftpl_status validate(Ctx& c, const fftpl_region* R, int n, const fftpl_cells* c
     if (opt) {
         if (!(opt->target_density > 0.0) || !isfinite(opt->target_density))
             return set_err(c, FFTPL_EINVAL, "target_density must be > 0");
-        if (opt->solve_path != FFTPL_SOLVE_FFT && opt->solve_path != FFTPL_SOLVE_TC_BF16X3)
+        if (opt->solve_path != FFTPL_SOLVE_FFT && opt->solve_path != FFTPL_SOLVE_TC_BF16X3 &&
+            opt->solve_path != FFTPL_SOLVE_TC_RADIX)
             return set_err(c, FFTPL_EINVAL, "unknown solve_path");
         if (opt->solve_path == FFTPL_SOLVE_TC_BF16X3 && n < FFTPL_TC_MIN_N)
             return set_err(c, FFTPL_EINVAL, "the tensor-core solve path needs n >= 128");
+        if (opt->solve_path == FFTPL_SOLVE_TC_RADIX && n < FFTPL_TCR_MIN_N)
+            return set_err(c, FFTPL_EINVAL, "the radix tensor-core solve path needs n >= 256");
         if (!(opt->dw_ref > 0.0)) return set_err(c, FFTPL_EINVAL, "dw_ref must be > 0");
         if (opt->wirelength != FFTPL_WL_WA && opt->wirelength != FFTPL_WL_LSE)
             return set_err(c, FFTPL_EINVAL, "unknown wirelength model");
@@ -291,7 +295,11 @@ struct Stage {
 // Spectral solve of the current D (and M) into psi and E2, with the overflow,
 // charge and energy sums: stages 1-3 of the profile.
 fftpl_status enqueue_solve(Ctx& c, cudaStream_t s) {
-    if (c.tc) {
+    if (c.tcr) {
+        { Stage st(c, 1, s); CK(launch_tcr(c, 0, s)); }
+        { Stage st(c, 2, s); CK(launch_tcr(c, 1, s)); }
+        { Stage st(c, 3, s); CK(launch_tcr(c, 2, s)); }
+    } else if (c.tc) {
         { Stage st(c, 1, s); CK(launch_tc(c, 0, s)); CK(launch_tc(c, 1, s)); }
         { Stage st(c, 2, s); CK(launch_tc(c, 2, s)); }
         { Stage st(c, 3, s); CK(launch_tc(c, 3, s)); }
@@ -305,6 +313,7 @@ fftpl_status enqueue_solve(Ctx& c, cudaStream_t s) {
 
 // The overflow and charge sums of the current D alone.
 cudaError_t launch_tau(Ctx& c, cudaStream_t s) {
+    if (c.tcr) return launch_tcr(c, 3, s);
     return c.tc ? launch_tc(c, 0, s) : launch_rows_fwd(c, s);
 }
 
@@ -779,6 +788,8 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
         if (c.opt.solve_path == FFTPL_SOLVE_TC_BF16X3)
             cap0 = std::max<long long>(cap0, std::max<long long>((long long)n * n / 1024,
                                                                  (long long)(n / 128) * (n / 128)));
+        if (c.opt.solve_path == FFTPL_SOLVE_TC_RADIX)
+            cap0 = std::max<long long>(cap0, ((long long)(n / 2) * (n / 2 + 1) + 255) / 256);
         long long cap1 = std::max<long long>(
             ((long long)(c.nslabs - c.nbig) + kWaThreads / 32 - 1) / (kWaThreads / 32),
             ((long long)c.nbig + kBigWarps - 1) / kBigWarps);
@@ -808,6 +819,16 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
         uint16_t* block = nullptr;
         TRY(dalloc(c, &block, tc_elems(n)));
         cudaError_t e = tc_setup(c, block, s);
+        if (e == cudaErrorInvalidValue)
+            return set_err(c, FFTPL_ECUDA, "cuTensorMapEncodeTiled unavailable or failed");
+        CK(e);
+    }
+    if (c.opt.solve_path == FFTPL_SOLVE_TC_RADIX) {
+        uint16_t* block = nullptr;
+        float2* zv = nullptr;
+        TRY(dalloc(c, &block, tcr_elems(n)));
+        TRY(dalloc(c, &zv, 2 * nn));
+        cudaError_t e = tcr_setup(c, block, zv, s);
         if (e == cudaErrorInvalidValue)
             return set_err(c, FFTPL_ECUDA, "cuTensorMapEncodeTiled unavailable or failed");
         CK(e);

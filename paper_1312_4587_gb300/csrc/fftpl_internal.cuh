@@ -441,6 +441,8 @@ struct Ctx {
 
     // tensor-core solve path (solve_path FFTPL_SOLVE_TC_BF16X3), k_tc.cu
     struct TcPlan* tc = nullptr;
+    // radix tensor-core path (solve_path FFTPL_SOLVE_TC_RADIX), k_tc.cu
+    struct TcrPlan* tcr = nullptr;
 
     // captured CUDA graph of fftpl_eval for one set of buffers
     cudaGraphExec_t eval_graph = nullptr;
@@ -548,6 +550,16 @@ cudaError_t launch_tc(Ctx& c, int part, cudaStream_t s);
 cudaError_t tc_debug_gemm(const void* ah, const void* al, const void* bh, const void* bl, int M,
                           int N, int K, float* d, int nsplit, int no_loads, int* err,
                           cudaStream_t s);
+// radix tensor-core path (k_tc.cu): tcr_setup lays the plan out in a device
+// block of tcr_elems(n) bf16 elements and 2 n^2 float2 (Z, V) owned by the
+// handle; launch_tcr part 0 the row pass, 1 the column pass, 2 the inverse
+// row pass, 3 the overflow and charge sums alone.  launch_tcr_stage
+// (k_spectral.cu): the pre- and post-processing kernels between its DFTs.
+size_t tcr_elems(int n);
+cudaError_t tcr_setup(Ctx& c, uint16_t* block, float2* zv, cudaStream_t s);
+void tcr_free(Ctx& c);
+cudaError_t launch_tcr(Ctx& c, int part, cudaStream_t s);
+cudaError_t launch_tcr_stage(Ctx& c, int which, const float2* V, float2* Z, cudaStream_t s);
 cudaError_t launch_cells(Ctx& c, const float* x, const float* y, float* gNx, float* gNy,
                          float* gWx, float* gWy, cudaStream_t s);
 // placement loop

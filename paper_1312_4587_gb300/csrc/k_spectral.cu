@@ -566,6 +566,299 @@ k_rows_psi(const float* __restrict__ PT, float* __restrict__ psi, const float2* 
     }
 }
 
+// ------------------------------------- tensor-core radix path: the rows
+// The solve path FFTPL_SOLVE_TC_RADIX (k_tc.cu) computes every complex DFT
+// of length n as two small dense products on the tensor cores.  These
+// kernels do the same pre- and post-processing as the three passes above,
+// row by row in global memory: Z holds complex rows of length n (Makhoul's
+// packing of two real rows, or the packed spectrum of an inverse pair) that
+// go into the DFT, V the complex rows that come out.
+
+// rho rows (2r, 2r+1) packed: Z[r][k] = rho_2r[2k] + i rho_2r+1[2k] (k < n/2),
+// Z[r][n-1-k] = rho_2r[2k+1] + i rho_2r+1[2k+1]; with the overflow and charge
+// sums of k_rows_fwd.
+template <bool QUANT>
+__global__ void __launch_bounds__(256)
+k_tcr_pack_rho(int n, int rows2, const float* __restrict__ D, const long long* __restrict__ Dq,
+               const float* __restrict__ M, float inv_ab, float cap, float2* __restrict__ Z,
+               double* __restrict__ acc, DetRed dr) {
+    const int half = n >> 1;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float tau = 0.0f, charge = 0.0f;
+    if (q < (long long)rows2 * half) {
+        const int r = (int)(q / half), k = (int)(q % half);
+        const size_t b0 = (size_t)(2 * r) * n + 2 * k, b1 = b0 + n;
+        float d[4], mm[4];
+        const float2 m0 = *reinterpret_cast<const float2*>(M + b0);
+        const float2 m1 = *reinterpret_cast<const float2*>(M + b1);
+        mm[0] = m0.x; mm[1] = m0.y; mm[2] = m1.x; mm[3] = m1.y;
+        if (QUANT) {
+            const longlong2 q0 = *reinterpret_cast<const longlong2*>(Dq + b0);
+            const longlong2 q1 = *reinterpret_cast<const longlong2*>(Dq + b1);
+            d[0] = (float)q0.x * 2.3283064365386963e-10f;
+            d[1] = (float)q0.y * 2.3283064365386963e-10f;
+            d[2] = (float)q1.x * 2.3283064365386963e-10f;
+            d[3] = (float)q1.y * 2.3283064365386963e-10f;
+        } else {
+            const float2 v0 = *reinterpret_cast<const float2*>(D + b0);
+            const float2 v1 = *reinterpret_cast<const float2*>(D + b1);
+            d[0] = v0.x; d[1] = v0.y; d[2] = v1.x; d[3] = v1.y;
+        }
+        float rv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            tau += fmaxf(0.0f, d[t] - (cap - mm[t]));
+            charge += d[t] + mm[t];
+            rv[t] = (d[t] + mm[t]) * inv_ab;
+        }
+        float2* zr = Z + (size_t)r * n;
+        zr[k] = make_float2(rv[0], rv[2]);
+        zr[n - 1 - k] = make_float2(rv[1], rv[3]);
+    }
+    reduce2(tau, charge, acc, ACC_TAU, ACC_CHARGE, dr);
+}
+
+// Rows (2r, 2r+1) of a real map packed the same way (no sums).
+__global__ void __launch_bounds__(256)
+k_tcr_pack_rows(int n, int rows2, const float* __restrict__ A, float2* __restrict__ Z) {
+    const int half = n >> 1;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)rows2 * half) return;
+    const int r = (int)(q / half), k = (int)(q % half);
+    const size_t b0 = (size_t)(2 * r) * n + 2 * k;
+    const float2 a = *reinterpret_cast<const float2*>(A + b0);
+    const float2 c = *reinterpret_cast<const float2*>(A + b0 + n);
+    float2* zr = Z + (size_t)r * n;
+    zr[k] = make_float2(a.x, c.x);
+    zr[n - 1 - k] = make_float2(a.y, c.y);
+}
+
+// DCT-II spectra of packed pairs: A_j[u] = Re(ph[u] V_j[u]) with
+// V_1 = (Z[u] + conj Z[n-u]) / 2, V_2 = (Z[u] - conj Z[n-u]) / 2i, the two
+// rows of pair r; written transposed, T[u][8 g .. 8 g + 7] for the 4 pairs
+// of group g (as k_rows_fwd writes T1).
+__global__ void __launch_bounds__(256)
+k_tcr_post_fwd(int n, int groups, const float2* __restrict__ V, const float2* __restrict__ ph,
+               float* __restrict__ T) {
+    const int half = n / 2 + 1;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)groups * half) return;
+    const int g = (int)(q / half), u = (int)(q % half);
+    float a[8], an[8];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float2* vr = V + (size_t)(4 * g + t) * n;
+        const float2 zu = vr[u & (n - 1)], zn = vr[(n - u) & (n - 1)];
+        const float2 v1 = make_float2(0.5f * (zu.x + zn.x), 0.5f * (zu.y - zn.y));
+        const float2 v2 = make_float2(0.5f * (zu.y + zn.y), 0.5f * (zn.x - zu.x));
+        const float2 p = ph[u], pn = ph[n - u];
+        a[2 * t] = v1.x * p.x - v1.y * p.y;
+        a[2 * t + 1] = v2.x * p.x - v2.y * p.y;
+        an[2 * t] = v1.x * pn.x + v1.y * pn.y;
+        an[2 * t + 1] = v2.x * pn.x + v2.y * pn.y;
+    }
+    float4* dst = reinterpret_cast<float4*>(T + (size_t)(u & (n - 1)) * n + 8 * g);
+    dst[0] = make_float4(a[0], a[1], a[2], a[3]);
+    dst[1] = make_float4(a[4], a[5], a[6], a[7]);
+    if (u > 0 && u < n / 2) {
+        float4* dn = reinterpret_cast<float4*>(T + (size_t)(n - u) * n + 8 * g);
+        dn[0] = make_float4(an[0], an[1], an[2], an[3]);
+        dn[1] = make_float4(an[4], an[5], an[6], an[7]);
+    }
+}
+
+// Column spectra of u-row pairs r (V, as in k_cols): divide by
+// w_u^2 + w_v^2 (+ eps), drop the (0,0) mode, the energy, and the packed
+// inverse inputs: Z[r] for P (cosine sums of Psi), Z[rows2 + r] for R
+// (cosine sums of the reversed w_v Psi).
+__global__ void __launch_bounds__(256)
+k_tcr_spectral(int n, int rows2, const float2* __restrict__ V, const float2* __restrict__ ph,
+               float pi_lx, float pi_ly, float eps, float2* __restrict__ Z,
+               double* __restrict__ acc, DetRed dr) {
+    const int half = n / 2 + 1;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    dfloat energy = df_zero();
+    if (q < (long long)rows2 * half) {
+        const int r = (int)(q / half), v = (int)(q % half);
+        const float2* vr = V + (size_t)r * n;
+        const float2 zu = vr[v & (n - 1)], zn = vr[(n - v) & (n - 1)];
+        const float2 v1 = make_float2(0.5f * (zu.x + zn.x), 0.5f * (zu.y - zn.y));
+        const float2 v2 = make_float2(0.5f * (zu.y + zn.y), 0.5f * (zn.x - zu.x));
+        const float2 p = ph[v], qq = ph[n - v];
+        float B[2][2];
+        B[0][0] = v1.x * p.x - v1.y * p.y;
+        B[1][0] = v2.x * p.x - v2.y * p.y;
+        B[0][1] = v1.x * qq.x + v1.y * qq.y;
+        B[1][1] = v2.x * qq.x + v2.y * qq.y;
+        const float invn2 = 1.0f / ((float)n * (float)n);
+        const float wv = pi_ly * (float)v, wvn = pi_ly * (float)(n - v);
+        const float ev = (v == 0) ? 1.0f : 2.0f;
+        const bool has_n = (v > 0 && v < n / 2);
+        float c1v[2], c1n[2], c2v[2], c2n[2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int u = 2 * r + rr;
+            const float wu = pi_lx * (float)u;
+            const float eu = (u == 0) ? 1.0f : 2.0f;
+            const float a0 = eu * ev * invn2 * B[rr][0];
+            const float psi0 = (u == 0 && v == 0 && !(eps > 0.0f))
+                                   ? 0.0f
+                                   : __fdividef(a0, wu * wu + wv * wv + eps);
+            float psin = 0.0f;
+            if (has_n) {
+                const float an = eu * 2.0f * invn2 * B[rr][1];
+                psin = __fdividef(an, wu * wu + wvn * wvn + eps);
+                energy = df_add(energy, B[rr][1] * psin);
+            }
+            energy = df_add(energy, B[rr][0] * psi0);
+            c1v[rr] = (v == 0) ? psi0 : 0.5f * psi0;
+            c1n[rr] = 0.5f * psin;
+            c2v[rr] = (v == 0) ? 0.0f : 0.5f * wvn * psin;
+            c2n[rr] = (v == 0) ? 0.0f : 0.5f * wv * psi0;
+            if (v == n / 2) {
+                c1n[rr] = c1v[rr];
+                c2v[rr] = 0.5f * wv * psi0;
+                c2n[rr] = c2v[rr];
+            }
+        }
+        float2* zp = Z + (size_t)r * n;
+        float2* zr = Z + (size_t)(rows2 + r) * n;
+        zp[v & (n - 1)] = pack_inv(c1v[0], c1n[0], c1v[1], c1n[1], p);
+        zr[v & (n - 1)] = pack_inv(c2v[0], c2n[0], c2v[1], c2n[1], p);
+        if (has_n) {
+            zp[n - v] = pack_inv(c1n[0], c1v[0], c1n[1], c1v[1], qq);
+            zr[n - v] = pack_inv(c2n[0], c2v[0], c2n[1], c2v[1], qq);
+        }
+    }
+    reduce2(df_val(energy), 0.0f, acc, ACC_N, -1, dr);
+}
+
+// Inverse outputs of the column pass: pair r of P (V[r]) and of R
+// (V[rows2 + r]) unshuffled (y <- position mk_src(y); R times (-1)^y) and
+// written transposed, PT[y][8 g .. 8 g + 7], RT likewise.
+__global__ void __launch_bounds__(256)
+k_tcr_post_cols(int n, int rows2, const float2* __restrict__ V, float* __restrict__ PT,
+                float* __restrict__ RT) {
+    const int groups = rows2 / 4;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)groups * n) return;
+    const int g = (int)(q / n), y = (int)(q % n);
+    const int k = mk_src(y, n);
+    const float sgn = (y & 1) ? -1.0f : 1.0f;
+    float p[8], rr[8];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float2 zp = V[(size_t)(4 * g + t) * n + k];
+        const float2 zr = V[(size_t)(rows2 + 4 * g + t) * n + k];
+        p[2 * t] = zp.x; p[2 * t + 1] = zp.y;
+        rr[2 * t] = sgn * zr.x; rr[2 * t + 1] = sgn * zr.y;
+    }
+    float4* dp = reinterpret_cast<float4*>(PT + (size_t)y * n + 8 * g);
+    float4* dr4 = reinterpret_cast<float4*>(RT + (size_t)y * n + 8 * g);
+    dp[0] = make_float4(p[0], p[1], p[2], p[3]);
+    dp[1] = make_float4(p[4], p[5], p[6], p[7]);
+    dr4[0] = make_float4(rr[0], rr[1], rr[2], rr[3]);
+    dr4[1] = make_float4(rr[4], rr[5], rr[6], rr[7]);
+}
+
+// Inverse inputs of the row pass for y-row pairs r: Z[r] E_x (reversed sine
+// coefficients of w_u P), Z[rows2 + r] E_y (cosine sums of R), as the fill
+// of k_rows_inv.
+__global__ void __launch_bounds__(256)
+k_tcr_pack_inv(int n, int rows2, const float* __restrict__ PT, const float* __restrict__ RT,
+               const float2* __restrict__ ph, float pi_lx, float2* __restrict__ Z) {
+    const int half = n / 2 + 1;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)rows2 * half) return;
+    const int r = (int)(q / half), u = (int)(q % half);
+    const int un = (n - u) & (n - 1);
+    {
+        const float* A = RT + (size_t)(2 * r) * n;
+        const float* Bq = A + n;
+        const float au = A[u & (n - 1)], bu = Bq[u & (n - 1)];
+        const float an = (u > 0) ? A[un] : 0.0f, bn = (u > 0) ? Bq[un] : 0.0f;
+        const float cau = (u == 0) ? au : 0.5f * au, cbu = (u == 0) ? bu : 0.5f * bu;
+        float can = 0.5f * an, cbn = 0.5f * bn;
+        if (u == n / 2) { can = cau; cbn = cbu; }
+        float2* row = Z + (size_t)(rows2 + r) * n;
+        row[u & (n - 1)] = pack_inv(cau, can, cbu, cbn, ph[u]);
+        if (u > 0 && u < n / 2) row[n - u] = pack_inv(can, cau, cbn, cbu, ph[n - u]);
+    }
+    {
+        const float* Pa = PT + (size_t)(2 * r) * n;
+        const float* Pb = Pa + n;
+        const float wu = pi_lx * (float)u, wn = pi_lx * (float)(n - u);
+        const float ca_u = (u == 0) ? 0.0f : 0.5f * wn * Pa[n - u];
+        const float cb_u = (u == 0) ? 0.0f : 0.5f * wn * Pb[n - u];
+        float ca_n = (u == 0) ? 0.0f : 0.5f * wu * Pa[u];
+        float cb_n = (u == 0) ? 0.0f : 0.5f * wu * Pb[u];
+        if (u == n / 2) { ca_n = ca_u; cb_n = cb_u; }
+        float2* row = Z + (size_t)r * n;
+        row[u & (n - 1)] = pack_inv(ca_u, ca_n, cb_u, cb_n, ph[u]);
+        if (u > 0 && u < n / 2) row[n - u] = pack_inv(ca_n, ca_u, cb_n, cb_u, ph[n - u]);
+    }
+}
+
+// Inverse outputs of the row pass: E2[y][x] = ((-1)^x E_x, E_y) for the rows
+// of pair r, unshuffled.
+__global__ void __launch_bounds__(256)
+k_tcr_post_rows(int n, int rows2, const float2* __restrict__ V, float2* __restrict__ E2) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)rows2 * n) return;
+    const int r = (int)(q / n), x = (int)(q % n);
+    const int k = mk_src(x, n);
+    const float2 zx = V[(size_t)r * n + k], zy = V[(size_t)(rows2 + r) * n + k];
+    const float s = (x & 1) ? -1.0f : 1.0f;
+    E2[(size_t)(2 * r) * n + x] = make_float2(s * zx.x, zy.x);
+    E2[(size_t)(2 * r + 1) * n + x] = make_float2(s * zx.y, zy.y);
+}
+
+static inline unsigned tcr_blocks(long long items) { return (unsigned)((items + 255) / 256); }
+
+cudaError_t launch_tcr_stage(Ctx& c, int which, const float2* V, float2* Z, cudaStream_t s) {
+    const int n = c.n, rows2 = n / 2;
+    const float pi_lx = (float)(M_PI / c.Lx), pi_ly = (float)(M_PI / c.Ly);
+    switch (which) {
+        case 0: {   // rho rows -> Z (with the overflow and charge sums)
+            const float inv_ab = (float)(1.0 / c.Ab);
+            const float cap = (float)(c.opt.target_density * c.Ab);
+            const unsigned nb = tcr_blocks((long long)rows2 * (n / 2));
+            if (c.opt.deterministic)
+                k_tcr_pack_rho<true><<<nb, 256, 0, s>>>(n, rows2, nullptr, c.Dq, c.M, inv_ab, cap,
+                                                        Z, c.acc, det_red(c, 0));
+            else
+                k_tcr_pack_rho<false><<<nb, 256, 0, s>>>(n, rows2, c.D, nullptr, c.M, inv_ab, cap,
+                                                         Z, c.acc, det_red(c, 0));
+            break;
+        }
+        case 1:     // row spectra -> T1 (transposed)
+            k_tcr_post_fwd<<<tcr_blocks((long long)(rows2 / 4) * (n / 2 + 1)), 256, 0, s>>>(
+                n, rows2 / 4, V, c.ph, c.T1);
+            break;
+        case 2:     // T1 rows -> Z
+            k_tcr_pack_rows<<<tcr_blocks((long long)rows2 * (n / 2)), 256, 0, s>>>(n, rows2, c.T1, Z);
+            break;
+        case 3:     // column spectra -> divide, energy -> Z (P rows, then R rows)
+            k_tcr_spectral<<<tcr_blocks((long long)rows2 * (n / 2 + 1)), 256, 0, s>>>(
+                n, rows2, V, c.ph, pi_lx, pi_ly, (float)c.opt.helmholtz_eps, Z, c.acc,
+                det_red(c, 0));
+            break;
+        case 4:     // P, R sums -> PT, RT (transposed)
+            k_tcr_post_cols<<<tcr_blocks((long long)(rows2 / 4) * n), 256, 0, s>>>(n, rows2, V,
+                                                                                  c.PT, c.RT);
+            break;
+        case 5:     // PT, RT rows -> Z (E_x rows, then E_y rows)
+            k_tcr_pack_inv<<<tcr_blocks((long long)rows2 * (n / 2 + 1)), 256, 0, s>>>(
+                n, rows2, c.PT, c.RT, c.ph, pi_lx, Z);
+            break;
+        default:    // E_x, E_y sums -> E2
+            k_tcr_post_rows<<<tcr_blocks((long long)rows2 * n), 256, 0, s>>>(n, rows2, V, c.E2);
+            break;
+    }
+    c.launches++;
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ launch
 template <int LOGN>
 static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {

@@ -54,8 +54,15 @@ constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait
 // chains of K/4 stay within 2e-4.  kAcc * BN = 512 columns is all of an SM's
 // tensor memory, which the one CTA per SM owns.
 constexpr int kAcc = 4;
+// Row pitch of the radix path's staged epilogue tile (256 bytes of data plus
+// 8, so that the 32 lanes' 8-byte stores of one row each fall on distinct
+// banks two lanes at a time).
+constexpr int kStgRow = 264;
+static_assert(2 * 128 * kStgRow <= kStages * kStageBytes, "staging tile exceeds the ring");
+static_assert(2 * 128 * 128 * 4 <= kStages * kStageBytes, "staging rows exceed the ring");
 
-enum Epi { EPI_F32 = 0, EPI_SPLIT = 1, EPI_SPECTRAL = 2, EPI_PSI_EX = 3, EPI_EY = 4 };
+enum Epi { EPI_F32 = 0, EPI_SPLIT = 1, EPI_SPECTRAL = 2, EPI_PSI_EX = 3, EPI_EY = 4,
+           EPI_TWIDDLE = 5, EPI_CPLX = 6 };
 
 struct EpiArgs {
     __nv_bfloat16* hi;   // EPI_SPLIT / EPI_SPECTRAL outputs [row][ld]
@@ -70,6 +77,13 @@ struct EpiArgs {
     DetRed dr;
     int* err;
     int no_loads;        // test hook: issue no TMA loads (the waits then expire)
+    // radix path (EPI_TWIDDLE, EPI_CPLX): DFT length n = 64 n2, g = 64 / n2
+    // rows per second-stage tile, twiddles tw[k] = exp(-2 pi i k / n),
+    // inv: conjugate twiddles, V: complex output rows [r][n]
+    int n2, g, inv;
+    int ln2, lg;         // log2 n2, log2 g (n2 and g are powers of two)
+    const float2* tw;
+    float2* V;
 };
 
 // ------------------------------------------------------------- PTX helpers
@@ -348,6 +362,51 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
                     dh[q] = sh[q];
                     dl[q] = sl[q];
                 }
+            } else if (EPI == EPI_TWIDDLE) {
+                // row = 2 k1 + c (c: real / imaginary part), column = r n2 + j2:
+                // Y[r][k1][j2] times exp(-+2 pi i j2 k1 / n), written as the
+                // second stage's operand A2[(r / g) 64 + k1][(r % g) 2 n2 + c n2 + j2]
+                const int k1 = row >> 1, cc = row & 1;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float other = __shfl_xor_sync(0xffffffffu, v[j], 1);
+                    const int col = col0 + j;
+                    const int j2 = col & (ep.n2 - 1);
+                    const float2 w = ep.tw[j2 * k1];
+                    const float wi = ep.inv ? -w.y : w.y;
+                    const float re = cc ? other : v[j], im = cc ? v[j] : other;
+                    v[j] = cc ? fmaf(re, wi, im * w.x) : fmaf(re, w.x, -im * wi);
+                }
+                __align__(16) __nv_bfloat16 h[32], l[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) split_bf16(v[j], h[j], l[j]);
+                // the tile's output is rows [n0, n0 + 128) of A2, whole: staged
+                // in the (now idle) operand ring, rows kStgRow bytes apart, hi
+                // then lo; 4 consecutive j2 of one r per store (n2 is a
+                // multiple of 4)
+                for (int j = 0; j < 32; j += 4) {
+                    const int col = col0 + j;
+                    const int r = col >> ep.ln2, j2 = col & (ep.n2 - 1);
+                    const int lr = ((r >> ep.lg) << 6) + k1 - n0;
+                    const int kk = (((r & (ep.g - 1)) << 1) + cc) * ep.n2 + j2;
+                    uint8_t* at = smem + (size_t)lr * kStgRow + 2 * kk;
+                    *reinterpret_cast<uint2*>(at) = *reinterpret_cast<const uint2*>(h + j);
+                    *reinterpret_cast<uint2*>(at + 128 * kStgRow) =
+                        *reinterpret_cast<const uint2*>(l + j);
+                }
+            } else if (EPI == EPI_CPLX) {
+                // row = (G, k1), column = q 2 n2 + c n2 + k2: component c of
+                // V[G g + q][k1 + 64 k2].  The tile's output is the 2 g whole
+                // rows from V[(m0 / 64) g]: staged in the idle operand ring
+                const int lg = (row >> 6) - (m0 >> 6), k1 = row & 63;
+                float* stg = reinterpret_cast<float*>(smem);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = col0 + j;
+                    const int q = col >> (ep.ln2 + 1), cc = (col >> ep.ln2) & 1;
+                    const int k2 = col & (ep.n2 - 1);
+                    stg[((size_t)(lg * ep.g + q) * ep.n + k1 + 64 * k2) * 2 + cc] = v[j];
+                }
             } else if (EPI == EPI_PSI_EX) {
                 if (col0 < ep.n) {
                     float4* dst = reinterpret_cast<float4*>(ep.f32 + (size_t)row * ep.n + col0);
@@ -365,6 +424,26 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
                 for (int j = 0; j < 32; ++j) dst[2 * j] = v[j];
             }
         }
+    }
+    if (EPI == EPI_TWIDDLE && store) {
+        // rows [n0, n0 + 128) of A2 (hi, lo): 256 bytes each, 8 bytes a
+        // thread (the staged rows are kStgRow = 8 mod 16 bytes apart)
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * 128 * 32; i += kThreads) {
+            const int half = i >> 12, lr = (i >> 5) & 127, q = i & 31;
+            const uint2 val = *reinterpret_cast<const uint2*>(
+                smem + (size_t)(half * 128 + lr) * kStgRow + 8 * q);
+            __nv_bfloat16* dst = (half ? ep.lo : ep.hi) + (size_t)(n0 + lr) * 128;
+            reinterpret_cast<uint2*>(dst)[q] = val;
+        }
+    }
+    if (EPI == EPI_CPLX && store) {
+        // 2 g rows of n complex values from V[(m0 / 64) g]: 64 KiB, contiguous
+        __syncthreads();
+        const size_t count4 = (size_t)2 * ep.g * ep.n * 2 / 4;
+        const float4* src = reinterpret_cast<const float4*>(smem);
+        float4* dst = reinterpret_cast<float4*>(ep.V + (size_t)(m0 >> 6) * ep.g * ep.n);
+        for (size_t i = threadIdx.x; i < count4; i += kThreads) dst[i] = src[i];
     }
     if (EPI == EPI_SPECTRAL) reduce2(df_val(energy), 0.0f, ep.acc, ACC_N, -1, ep.dr);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -396,6 +475,65 @@ __global__ void k_tc_tables(int n, double pi_lx, double pi_ly, __nv_bfloat16* C_
     split_bf16((float)(pi_ly * k * s), Sy_hi[idx], Sy_lo[idx]);
 }
 
+
+// Radix path tables: the 64-point DFT as a real 128 x 128 block
+// F1[2 k1 + c'][c 64 + j1] and the n2-point DFT block-diagonal over g rows,
+// F2[q 2 n2 + c' n2 + k2][q' 2 n2 + c n2 + j2] (0 for q != q'), for the
+// forward (exp(-i theta)) and inverse (exp(+i theta)) directions, split into
+// bf16 hi and lo.  Entry (c' <- c): cos for c = c', +sin (re <- im) and
+// -sin (im <- re) forward, the opposite signs inverse.  Arguments reduced
+// exactly: theta = 2 pi (j k mod L) / L.
+__global__ void k_tcr_tables(int n2, int g, __nv_bfloat16* F1, __nv_bfloat16* F2) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 128 * 128) return;
+    const int m = idx / 128, kk = idx % 128;
+    for (int dir = 0; dir < 2; ++dir) {
+        const double sg = dir == 0 ? 1.0 : -1.0;
+        {
+            const int k1 = m >> 1, co = m & 1, ci = kk >> 6, j1 = kk & 63;
+            double sn, cs;
+            sincospi(2.0 * (double)((j1 * k1) % 64) / 64.0, &sn, &cs);
+            const double val = co == ci ? cs : (co == 0 ? sg * sn : -sg * sn);
+            __nv_bfloat16* base = F1 + (size_t)dir * 2 * 128 * 128;
+            split_bf16((float)val, base[idx], base[128 * 128 + idx]);
+        }
+        {
+            const int qo = m / (2 * n2), co = (m % (2 * n2)) / n2, k2 = m % n2;
+            const int qi = kk / (2 * n2), ci = (kk % (2 * n2)) / n2, j2 = kk % n2;
+            double val = 0.0;
+            if (qo == qi && qo < g) {
+                double sn, cs;
+                sincospi(2.0 * (double)((j2 * k2) % n2) / (double)n2, &sn, &cs);
+                val = co == ci ? cs : (co == 0 ? sg * sn : -sg * sn);
+            }
+            __nv_bfloat16* base = F2 + (size_t)dir * 2 * 128 * 128;
+            split_bf16((float)val, base[idx], base[128 * 128 + idx]);
+        }
+    }
+}
+
+// Complex rows Z[r][0..n) into the first stage's operand, bf16 hi/lo:
+// Xt[r n2 + j2][c 64 + j1] = component c of Z[r][n2 j1 + j2] (one CTA per
+// row, staged in shared memory, padded one element in 32).
+__global__ void __launch_bounds__(128)
+k_tcr_split(int n, int n2, const float2* __restrict__ Z, __nv_bfloat16* __restrict__ xh,
+            __nv_bfloat16* __restrict__ xl) {
+    extern __shared__ float2 zs[];
+    const int r = blockIdx.x;
+    const float2* zr = Z + (size_t)r * n;
+    for (int i = threadIdx.x; i < n; i += 128) zs[i + (i >> 5)] = zr[i];
+    __syncthreads();
+    const int t = threadIdx.x, c = t >> 6, j1 = t & 63;
+    for (int j2 = 0; j2 < n2; ++j2) {
+        const int i = n2 * j1 + j2;
+        const float2 z = zs[i + (i >> 5)];
+        __nv_bfloat16 h, l;
+        split_bf16(c ? z.y : z.x, h, l);
+        const size_t at = ((size_t)r * n2 + j2) * 128 + t;
+        xh[at] = h;
+        xl[at] = l;
+    }
+}
 
 // rho = (D + M) / A_b split into bf16 hi/lo, four bins per thread, with the
 // overflow and charge sums of the transform path's row pass.
@@ -483,6 +621,10 @@ void prepare_gemm() {
         set_smem_attr<tc::EPI_SPECTRAL>();
         set_smem_attr<tc::EPI_PSI_EX>();
         set_smem_attr<tc::EPI_EY>();
+        set_smem_attr<tc::EPI_TWIDDLE>();
+        set_smem_attr<tc::EPI_CPLX>();
+        cudaFuncSetAttribute(tc::k_tcr_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((4096 + 4096 / 32) * sizeof(float2)));
     });
 }
 
@@ -626,6 +768,129 @@ cudaError_t launch_tc(Ctx& c, int part, cudaStream_t s) {
         const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(s, p.join, 0) : ej;
         if (e == cudaSuccess) e = e7;
         if (e == cudaSuccess) e = ew;
+    }
+    return e;
+}
+
+// ----------------------------------------------- radix path (f3)
+// Every complex DFT of length n = 64 n2 on R rows as two products on the
+// tensor cores (a four-step factorisation): stage 1, the 64-point DFTs
+// over j1 for every (row, j2), D1 = F1 Xt^T (M = 128, N = R n2, K = 128),
+// with the twiddles exp(-+2 pi i j2 k1 / n) in its epilogue; stage 2, the
+// n2-point DFTs over j2, D2 = A2 F2^T (M = R n2, N = 128, K = 128), g rows
+// side by side in one tile (F2 block-diagonal), written as complex rows.
+struct TcrPlan {
+    int n = 0, n2 = 0, g = 0;
+    __nv_bfloat16 *F1 = nullptr, *F2 = nullptr, *X[2] = {}, *A2[2] = {};
+    CUtensorMap mF1[2][2], mF2[2][2], mX[2], mA2[2];
+    float2 *Z = nullptr, *V = nullptr;
+};
+
+size_t tcr_elems(int n) {
+    // bf16: F1, F2 (2 directions x hi/lo x 128^2), X and A2 (hi/lo x 2 n^2 each)
+    return 8 * 128 * 128 + 8 * (size_t)n * n;
+}
+
+cudaError_t tcr_setup(Ctx& c, uint16_t* block, float2* zv, cudaStream_t s) {
+    const int n = c.n;
+    TcrPlan* p = new (std::nothrow) TcrPlan();
+    if (!p) return cudaErrorMemoryAllocation;
+    p->n = n;
+    p->n2 = n / 64;
+    p->g = 64 / p->n2 > 0 ? 64 / p->n2 : 1;
+    __nv_bfloat16* q = reinterpret_cast<__nv_bfloat16*>(block);
+    auto take = [&](size_t count) { __nv_bfloat16* r = q; q += count; return r; };
+    p->F1 = take(4 * 128 * 128);
+    p->F2 = take(4 * 128 * 128);
+    const size_t rows = (size_t)n * p->n2;   // R_max n2 with R_max = n rows
+    for (int h = 0; h < 2; ++h) {
+        p->X[h] = take(rows * 128);
+        p->A2[h] = take(rows * 128);
+    }
+    p->Z = zv;
+    p->V = zv + (size_t)n * n;
+    bool ok = true;
+    for (int dir = 0; dir < 2; ++dir)
+        for (int h = 0; h < 2; ++h) {
+            ok = ok && make_map(&p->mF1[dir][h], p->F1 + (size_t)(2 * dir + h) * 128 * 128, 128, 128);
+            ok = ok && make_map(&p->mF2[dir][h], p->F2 + (size_t)(2 * dir + h) * 128 * 128, 128, 128);
+        }
+    for (int h = 0; h < 2; ++h)
+        ok = ok && make_map(&p->mX[h], p->X[h], (int)rows, 128) &&
+             make_map(&p->mA2[h], p->A2[h], (int)rows, 128);
+    if (!ok) {
+        delete p;
+        return cudaErrorInvalidValue;
+    }
+    prepare_gemm();
+    c.tcr = p;
+    tc::k_tcr_tables<<<(128 * 128 + 255) / 256, 256, 0, s>>>(p->n2, p->g, p->F1, p->F2);
+    return cudaGetLastError();
+}
+
+void tcr_free(Ctx& c) {
+    delete c.tcr;
+    c.tcr = nullptr;
+}
+
+// DFT of rows Z[0..R) into V[0..R): forward (exp(-i ...)) or inverse
+// (exp(+i ...), no 1/n), as the transform path's FFTs.
+static cudaError_t tcr_dft(Ctx& c, int R, int inv, cudaStream_t s) {
+    TcrPlan& p = *c.tcr;
+    const int n = p.n;
+    tc::k_tcr_split<<<R, 128, (size_t)(n + n / 32) * sizeof(float2), s>>>(n, p.n2, p.Z, p.X[0],
+                                                                          p.X[1]);
+    cudaError_t e = cudaGetLastError();
+    c.launches++;
+    if (e != cudaSuccess) return e;
+    tc::EpiArgs ep{};
+    ep.n = n;
+    ep.n2 = p.n2;
+    ep.g = p.g;
+    ep.ln2 = 0;
+    while ((1 << ep.ln2) < p.n2) ep.ln2++;
+    ep.lg = 0;
+    while ((1 << ep.lg) < p.g) ep.lg++;
+    ep.inv = inv;
+    ep.tw = c.tw;
+    ep.err = c.err;
+    ep.dr = det_red(c, 0);
+    ep.hi = p.A2[0];
+    ep.lo = p.A2[1];
+    const int cols = R * p.n2;
+    e = gemm<tc::EPI_TWIDDLE>(p.mF1[inv], p.mX, 128, cols, 128, 3, ep, s);
+    c.launches++;
+    if (e != cudaSuccess) return e;
+    ep.V = p.V;
+    e = gemm<tc::EPI_CPLX>(p.mA2, p.mF2[inv], cols, 128, 128, 3, ep, s);
+    c.launches++;
+    return e;
+}
+
+// part 0: the row pass (rho -> T1, with the overflow and charge sums);
+// 1: the column pass (T1 -> spectra, divide, energy -> PT, RT); 2: the
+// inverse row pass (PT, RT -> E2); 3: the overflow and charge sums alone.
+cudaError_t launch_tcr(Ctx& c, int part, cudaStream_t s) {
+    TcrPlan& p = *c.tcr;
+    const int n = p.n;
+    cudaError_t e = cudaSuccess;
+    auto step = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    if (part == 0) {
+        step(launch_tcr_stage(c, 0, p.V, p.Z, s));
+        step(tcr_dft(c, n / 2, 0, s));
+        step(launch_tcr_stage(c, 1, p.V, p.Z, s));
+    } else if (part == 1) {
+        step(launch_tcr_stage(c, 2, p.V, p.Z, s));
+        step(tcr_dft(c, n / 2, 0, s));
+        step(launch_tcr_stage(c, 3, p.V, p.Z, s));
+        step(tcr_dft(c, n, 1, s));
+        step(launch_tcr_stage(c, 4, p.V, p.Z, s));
+    } else if (part == 2) {
+        step(launch_tcr_stage(c, 5, p.V, p.Z, s));
+        step(tcr_dft(c, n, 1, s));
+        step(launch_tcr_stage(c, 6, p.V, p.Z, s));
+    } else {
+        step(launch_tcr_stage(c, 0, p.V, p.Z, s));
     }
     return e;
 }

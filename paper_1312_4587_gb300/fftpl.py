@@ -24,8 +24,9 @@ FFTPL_OK, FFTPL_EINVAL, FFTPL_ENOMEM, FFTPL_ECUDA, FFTPL_ETIMEOUT, FFTPL_ESTATE,
     FFTPL_EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "FFTPL_OK", 1: "FFTPL_EINVAL", 2: "FFTPL_ENOMEM", 3: "FFTPL_ECUDA",
                 4: "FFTPL_ETIMEOUT", 5: "FFTPL_ESTATE", 6: "FFTPL_EUNSUPPORTED"}
-FFTPL_SOLVE_FFT, FFTPL_SOLVE_TC_BF16X3 = 0, 1
+FFTPL_SOLVE_FFT, FFTPL_SOLVE_TC_BF16X3, FFTPL_SOLVE_TC_RADIX = 0, 1, 2
 FFTPL_TC_MIN_N = 128
+FFTPL_TCR_MIN_N = 256
 FFTPL_WL_WA, FFTPL_WL_LSE = 0, 1
 FFTPL_OPT_NESTEROV, FFTPL_OPT_CG = 0, 1
 FFTPL_NUM_STAGES = 8
