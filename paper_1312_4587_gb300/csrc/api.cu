@@ -746,6 +746,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     TRY(dalloc(c, &c.T1, nn));
     TRY(dalloc(c, &c.PT, nn));
     TRY(dalloc(c, &c.RT, nn));
+    spec_maps_init(c);
     TRY(dalloc(c, &c.psi, nn));
     TRY(dalloc(c, &c.E2, nn));
     TRY(dalloc(c, &c.tw, n));

@@ -16,6 +16,7 @@
 //   accumulators    acc[ACC_*] doubles, err word
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -400,6 +401,11 @@ struct Ctx {
     float *M = nullptr, *D = nullptr;
     long long* Dq = nullptr;
     float *T1 = nullptr, *PT = nullptr, *RT = nullptr;
+    // tensor maps of T1 (boxes of 8 columns), PT and RT (boxes of 4 columns),
+    // 256 rows (n if smaller): the transposed tiles of the row and column
+    // passes leave shared memory through the tensor-memory-access unit
+    CUtensorMap map_t1{}, map_pt{}, map_rt{};
+    bool spec_tma = false;
     float *psi = nullptr, *ex = nullptr, *ey = nullptr, *rho = nullptr;
     float2* E2 = nullptr;       // interleaved field (E_x, E_y) [n][n]
     float2 *tw = nullptr, *ph = nullptr;
@@ -508,6 +514,12 @@ cudaError_t launch_cols_spectral(Ctx& c, cudaStream_t s);
 cudaError_t launch_rows_inv(Ctx& c, cudaStream_t s);
 // psi rows from PT (transform path; formed on demand, not in the evaluation)
 cudaError_t launch_rows_psi(Ctx& c, cudaStream_t s);
+// Tensor maps for the transposed stores of the transform passes (host only,
+// no allocation); clears c.spec_tma if the driver cannot encode them.
+void spec_maps_init(Ctx& c);
+// 2-D float32 tensor [rows][cols] in boxes of box_inner columns x box_outer rows.
+bool make_map_f32(CUtensorMap* map, const float* base, int rows, int cols, int box_inner,
+                  int box_outer);
 cudaError_t launch_rho(Ctx& c, cudaStream_t s);
 cudaError_t launch_split_field(Ctx& c, cudaStream_t s);
 cudaError_t launch_q_to_f(const long long* q, float scale, float* out, int count, cudaStream_t s);

@@ -36,6 +36,40 @@ namespace fftpl {
 __host__ __device__ constexpr int padded(int n) { return n + n / 16; }
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 
+// ------------------------------------- stores through the TMA unit
+// A pass that writes its output transposed first lays the tile out in shared
+// memory in the output's order, then one thread stores it box by box with
+// cp.async.bulk.tensor: the tile leaves the SM as whole rows of the box
+// instead of one 16- or 32-byte piece per thread and store instruction.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Every thread that wrote part of a tile: its shared-memory writes become
+// visible to the asynchronous proxy (before the barrier that precedes the
+// store).
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The box at (c0, c1) (c0 innermost) of a 2-D tensor map from shared memory.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0,
+                                             int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+            (unsigned long long)(uintptr_t)map),
+        "r"(c0), "r"(c1), "r"(smem_addr(src))
+        : "memory");
+}
+
+// Commit the stores issued so far and wait until they are complete (the
+// hardware wait of the bulk-copy group: it ends when the copies have been
+// written, not a spin loop).
+__device__ __forceinline__ void tma_store_drain() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // Twiddle exp(-+2 pi i k / 16) for the small exponents a radix-16 butterfly
 // uses (cos and sin of multiples of pi/8).
 __device__ __forceinline__ float2 w16(int e, bool inv) {
@@ -229,13 +263,13 @@ __global__ void __maxnreg__(LOGN >= 12 ? 255 : 96)
 k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
            const float* __restrict__ M, float inv_ab, float cap, float* __restrict__ T1,
            const float2* __restrict__ tw, const float2* __restrict__ ph, double* __restrict__ acc,
-           DetRed dr) {
+           DetRed dr, const __grid_constant__ CUtensorMap mT1, int tma) {
     constexpr int N = 1 << LOGN;
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = 2 * NB;
     constexpr int T = kSpecThreads;
     constexpr int NP = padded(N);
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(128) float2 sm[];
     const int y0 = blockIdx.x * ROWS;
     // per-thread sums of at most 8 n / 256 non-negative terms in float32
     float tau = 0.0f, charge = 0.0f;
@@ -326,6 +360,38 @@ k_rows_fwd(const float* __restrict__ D, const long long* __restrict__ Dq,
     }
     __syncthreads();
     // transposed write: T1[u][y0 .. y0+7]
+    if (tma && (smem_addr(sm) & 127u) == 0) {
+        // the eight values of each u go through registers into the tile
+        // [u][8] (which replaces the rows), stored in boxes of BOX values of u
+        constexpr int CNT = (N + T - 1) / T;
+        constexpr int BOX = N < 256 ? N : 256;
+        float4 va[CNT], vb[CNT];
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) {
+            const int u = threadIdx.x + k * T;
+            if (N % T == 0 || u < N) {
+                va[k] = make_float4(sf[0 * N + u], sf[1 * N + u], sf[2 * N + u], sf[3 * N + u]);
+                vb[k] = make_float4(sf[4 * N + u], sf[5 * N + u], sf[6 * N + u], sf[7 * N + u]);
+            }
+        }
+        __syncthreads();
+        float4* tile = reinterpret_cast<float4*>(sm);
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) {
+            const int u = threadIdx.x + k * T;
+            if (N % T == 0 || u < N) {
+                tile[2 * u] = va[k];
+                tile[2 * u + 1] = vb[k];
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < N / BOX; ++b) tma_store_2d(&mT1, tile + 2 * b * BOX, y0, b * BOX);
+            tma_store_drain();
+        }
+        return;
+    }
     for (int u = threadIdx.x; u < N; u += T) {
         float4 a = make_float4(sf[0 * N + u], sf[1 * N + u], sf[2 * N + u], sf[3 * N + u]);
         float4 b = make_float4(sf[4 * N + u], sf[5 * N + u], sf[6 * N + u], sf[7 * N + u]);
@@ -344,13 +410,14 @@ template <int LOGN>
 __global__ void __launch_bounds__(kSpecThreads, LOGN >= 12 ? 1 : 2)
 k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__ RT,
        const float2* __restrict__ tw, const float2* __restrict__ ph, float pi_lx, float pi_ly,
-       float eps, double* __restrict__ acc, DetRed dr) {
+       float eps, double* __restrict__ acc, DetRed dr, const __grid_constant__ CUtensorMap mPT,
+       const __grid_constant__ CUtensorMap mRT, int tma) {
     constexpr int N = 1 << LOGN;
     constexpr int NB = kSpecBuffers;
     constexpr int ROWS = NB;
     constexpr int T = kSpecThreads;
     constexpr int NP = padded(N);
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(128) float2 sm[];
     const int u0 = blockIdx.x * ROWS;
     // buffer f packs rows 2f, 2f+1 in Makhoul's order (as in k_rows_fwd)
     constexpr int ITEMS_IN = (ROWS / 2) * (N / 2);
@@ -455,6 +522,46 @@ k_cols(const float* __restrict__ T1, float* __restrict__ PT, float* __restrict__
     __syncthreads();
     fft_block<LOGN, NB>(sm, tw, true);
     // unshuffle: y even <- k = y/2, y odd <- k = N-1-(y-1)/2
+    if (tma && (smem_addr(sm) & 127u) == 0) {
+        // through registers into the tiles PT[y][u0..u0+3] and RT[y][...]
+        // (16 bytes per y, in place of the buffers), stored in boxes of BOX y
+        constexpr int CNT = (N + T - 1) / T;
+        constexpr int BOX = N < 256 ? N : 256;
+        float4 pv[CNT], rv[CNT];
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) {
+            const int y = threadIdx.x + k * T;
+            if (N % T == 0 || y < N) {
+                const int q = pidx(mk_src(y, N));
+                const float sgn = (y & 1) ? -1.0f : 1.0f;
+                const float2 p0 = sm[0 * NP + q], r0 = sm[1 * NP + q];
+                const float2 p1 = sm[2 * NP + q], r1 = sm[3 * NP + q];
+                pv[k] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                rv[k] = make_float4(sgn * r0.x, sgn * r0.y, sgn * r1.x, sgn * r1.y);
+            }
+        }
+        __syncthreads();
+        float4* tP = reinterpret_cast<float4*>(sm);
+        float4* tR = tP + N;
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) {
+            const int y = threadIdx.x + k * T;
+            if (N % T == 0 || y < N) {
+                tP[y] = pv[k];
+                tR[y] = rv[k];
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < N / BOX; ++b) {
+                tma_store_2d(&mPT, tP + b * BOX, u0, b * BOX);
+                tma_store_2d(&mRT, tR + b * BOX, u0, b * BOX);
+            }
+            tma_store_drain();
+        }
+        return;
+    }
     for (int y = threadIdx.x; y < N; y += T) {
         int k = pidx(mk_src(y, N));
         float sgn = (y & 1) ? -1.0f : 1.0f;
@@ -483,7 +590,7 @@ k_rows_inv(const float* __restrict__ PT, const float* __restrict__ RT, float2* _
     constexpr int T = kSpecThreads;
     constexpr int HALF = N / 2 + 1;
     constexpr int NP = padded(N);
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(128) float2 sm[];
     const int y0 = blockIdx.x * ROWS;
 #pragma unroll 2
     for (int idx = threadIdx.x; idx < (ROWS / 2) * HALF; idx += T) {
@@ -541,7 +648,7 @@ k_rows_psi(const float* __restrict__ PT, float* __restrict__ psi, const float2* 
     constexpr int T = kSpecThreads;
     constexpr int HALF = N / 2 + 1;
     constexpr int NP = padded(N);
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(128) float2 sm[];
     const int y0 = blockIdx.x * ROWS;
     for (int idx = threadIdx.x; idx < NB * HALF; idx += T) {
         int f = idx / HALF, u = idx % HALF;
@@ -873,18 +980,21 @@ static cudaError_t launch_all_logn(Ctx& c, int which, cudaStream_t s) {
             auto kf = k_rows_fwd<LOGN, true>;
             kf<<<N / (2 * kSpecBuffers), kSpecThreads, smem, s>>>(nullptr, c.Dq, c.M, inv_ab, cap,
                                                                    c.T1, c.tw, c.ph, c.acc,
-                                                                   det_red(c, 0));
+                                                                   det_red(c, 0), c.map_t1,
+                                                                   c.spec_tma ? 1 : 0);
         } else {
             auto kf = k_rows_fwd<LOGN, false>;
             kf<<<N / (2 * kSpecBuffers), kSpecThreads, smem, s>>>(c.D, nullptr, c.M, inv_ab, cap,
                                                                    c.T1, c.tw, c.ph, c.acc,
-                                                                   det_red(c, 0));
+                                                                   det_red(c, 0), c.map_t1,
+                                                                   c.spec_tma ? 1 : 0);
         }
     } else if (which == 1) {
         auto kf = k_cols<LOGN>;
         kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.T1, c.PT, c.RT, c.tw, c.ph, pi_lx, pi_ly,
                                                         (float)c.opt.helmholtz_eps, c.acc,
-                                                        det_red(c, 0));
+                                                        det_red(c, 0), c.map_pt, c.map_rt,
+                                                        c.spec_tma ? 1 : 0);
     } else if (which == 2) {
         auto kf = k_rows_inv<LOGN>;
         kf<<<N / kSpecBuffers, kSpecThreads, smem, s>>>(c.PT, c.RT, c.E2, c.tw, c.ph, pi_lx);
@@ -937,6 +1047,14 @@ static cudaError_t dispatch(Ctx& c, int which, cudaStream_t s) {
         case 12: return launch_all_logn<12>(c, which, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+void spec_maps_init(Ctx& c) {
+    const int n = c.n, box = n < 256 ? n : 256;
+    c.spec_tma = c.T1 && c.PT && c.RT && n >= 16 &&
+                 make_map_f32(&c.map_t1, c.T1, n, n, 8, box) &&
+                 make_map_f32(&c.map_pt, c.PT, n, n, 4, box) &&
+                 make_map_f32(&c.map_rt, c.RT, n, n, 4, box);
 }
 
 cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s) { return dispatch(c, 0, s); }

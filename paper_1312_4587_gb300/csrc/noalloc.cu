@@ -137,6 +137,7 @@ extern "C" fftpl_status fftpl_solve_noalloc(const float* rho, int32_t n, double 
     c.T1 = reinterpret_cast<float*>(base + kOffT1);
     c.PT = reinterpret_cast<float*>(base + kOffPT);
     c.RT = reinterpret_cast<float*>(base + kOffRT);
+    spec_maps_init(c);
     c.E2 = reinterpret_cast<float2*>(base + kOffE2);
     c.tw = reinterpret_cast<float2*>(base + kOffTw);
     c.ph = reinterpret_cast<float2*>(base + kOffPh);
