@@ -1,6 +1,6 @@
 """Degenerate instances against the oracle: no nets, no movable cells (fixed
 cells and their nets only), every cell outside the region, and the smallest
-grid (n = 16), in both reduction modes, on the default bounds."""
+grids (n = 16 and 32), in both reduction modes, on the default bounds."""
 import numpy as np
 import pytest
 
@@ -44,6 +44,7 @@ CASES = {
                                pin_dx=np.zeros(0, np.float32), pin_dy=np.zeros(0, np.float32)),
     "outside": lambda: (lambda b: variant(x=b.x + 1000.0, y=b.y + 1000.0))(synth.make_instance("tiny")),
     "n16": lambda: variant(n=16),
+    "n32": lambda: variant(n=32),
     "no_movable": no_movable,
 }
 
