@@ -56,13 +56,13 @@ STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "ce
 # source it was taken from is unchanged: key = first 16 hex digits of the
 # SHA-256 of the kernel file followed by fftpl_internal.cuh.
 STAGE_TRAFFIC = {
-    "scatter": ("k_density.cu", "709f5bccb71b81ce", 50708224 + 633344),
-    "rows_fwd": ("k_spectral.cu", "5e25095a26939b69", 33646592 + 0),
-    "cols": ("k_spectral.cu", "5e25095a26939b69", 17411072 + 545536),
-    "rows_inv": ("k_spectral.cu", "5e25095a26939b69", 33637120 + 2355200),
+    "scatter": ("k_density.cu", "4c14c008544e7a94", 50785280 + 617984),
+    "rows_fwd": ("k_spectral.cu", "2b363b92fb434061", 33648640 + 26368),
+    "cols": ("k_spectral.cu", "2b363b92fb434061", 17366272 + 496128),
+    "rows_inv": ("k_spectral.cu", "2b363b92fb434061", 33613824 + 412928),
     # k_wa and k_wa_big
-    "wa": ("k_wire.cu", "8c07f78e2007ca47", 103054848 + 3672576 + 65446144 + 566784),
-    "cells": ("k_wire.cu", "8c07f78e2007ca47", 76478464 + 14801664),
+    "wa": ("k_wire.cu", "f43e1c29439a9042", 103016704 + 3927552 + 65446912 + 525312),
+    "cells": ("k_wire.cu", "f43e1c29439a9042", 76428032 + 13393408),
 }
 
 
