@@ -527,8 +527,10 @@ const char* fftpl_last_error(fftpl_t h) {
 //     cells ordered by (label, distance, index) with two counting sorts).
 //  2. Nets of degree >= 2 ordered by their lowest cell number (counting
 //     sort), grouped by degree, largest first, into slabs of up to 32 nets;
-//     pin k of slab net j at slot base + 32 k + j.  Degree-1 nets have no
-//     wirelength and are left out.
+//     pin k of slab net j at slot base + 32 k + j.  Degrees kBigMin..kBigMax
+//     instead take L = grp_lanes(d) lanes per net, 32 / L nets per slab:
+//     pin k of slab net j at base + 32 (k / L) + j L + k % L.  Degree-1 nets
+//     have no wirelength and are left out.
 //  3. The pin records written in slab layout on the device.
 // In deterministic mode also the cell-ordered pin slots (pins of each cell,
 // by internal number, contiguous and in net order).
@@ -539,7 +541,8 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     const int64_t P = c.P;
     cudaStream_t s = c.stream;
     TempDev tmp(s);
-    int *d_np = nullptr, *d_pc = nullptr, *d_key = nullptr, *d_slot = nullptr;
+    int *d_np = nullptr, *d_pc = nullptr, *d_key = nullptr, *d_slot = nullptr,
+        *d_lanes = nullptr;
     float *d_dx = nullptr, *d_dy = nullptr;
     CK(tmp.alloc(&d_np, (size_t)E + 1));
     CK(tmp.alloc(&d_pc, (size_t)P));
@@ -547,6 +550,7 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     CK(tmp.alloc(&d_dy, (size_t)P));
     CK(tmp.alloc(&d_key, (size_t)E));
     CK(tmp.alloc(&d_slot, (size_t)E));
+    CK(tmp.alloc(&d_lanes, (size_t)E));
     CK(cudaMemcpyAsync(d_np, np, ((size_t)E + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     if (P > 0) {
         CK(cudaMemcpyAsync(d_pc, pc, (size_t)P * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -606,22 +610,26 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     std::vector<int4> slabs;
     std::vector<int64_t> first_slab((size_t)maxd + 1, 0);
     int64_t slots = 0;
+    auto lanes_of = [](int d) { return d >= kBigMin && d <= kBigMax ? grp_lanes(d) : 1; };
     for (int d = maxd; d >= 2; --d) {
         first_slab[d] = (int64_t)slabs.size();
-        for (int s0 = 0; s0 < dcnt[d]; s0 += 32) {
-            slabs.push_back(make_int4((int)slots, d, std::min(32, dcnt[d] - s0), 0));
-            slots += 32LL * d;
+        const int L = lanes_of(d), G = 32 / L;
+        for (int s0 = 0; s0 < dcnt[d]; s0 += G) {
+            slabs.push_back(make_int4((int)slots, d, std::min(G, dcnt[d] - s0), L > 1 ? L : 0));
+            slots += 32LL * ((d + L - 1) / L);
         }
     }
     if (slots > 0x7fffffffLL) return set_err(c, FFTPL_EINVAL, "too many pins");
     c.nslabs = (int)slabs.size();
     c.slab_slots = slots;
-    std::vector<int32_t> net_slot((size_t)E, -1), seen((size_t)maxd + 1, 0);
+    std::vector<int32_t> net_slot((size_t)E, -1), net_lanes((size_t)E, 1),
+        seen((size_t)maxd + 1, 0);
     for (int e : by_key) {
-        int d = np[e + 1] - np[e], j = seen[d]++;
-        net_slot[e] = slabs[(size_t)(first_slab[d] + j / 32)].x + (j % 32);
+        const int d = np[e + 1] - np[e], j = seen[d]++, L = lanes_of(d), G = 32 / L;
+        net_slot[e] = slabs[(size_t)(first_slab[d] + j / G)].x + (j % G) * L;
+        net_lanes[e] = L;
     }
-    // the slabs of degree kBigMin..kBigMax first (k_wa_big), the others
+    // the slabs of degree kBigMin..kBigMax first (k_wa_grp), the others
     // after them in the same order (k_wa); the slot layout is unchanged
     auto is_big = [](const int4& sl) { return sl.y >= kBigMin && sl.y <= kBigMax; };
     std::stable_partition(slabs.begin(), slabs.end(), is_big);
@@ -678,11 +686,14 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     CK(cudaMemsetAsync(c.pin_dx, 0, ns * sizeof(float), s));
     CK(cudaMemsetAsync(c.pin_dy, 0, ns * sizeof(float), s));
     if (c.pin_slot) CK(cudaMemsetAsync(c.pin_slot, 0xff, ns * sizeof(int32_t), s));
-    if (E > 0)
+    if (E > 0) {
         CK(cudaMemcpyAsync(d_slot, net_slot.data(), (size_t)E * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_lanes, net_lanes.data(), (size_t)E * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s));
+    }
     CK(launch_fill_slabs(m, E, d_np, d_pc, d_dx, d_dy, c.cell_rank, c.fix_x, c.fix_y, d_slot,
-                         d_cslot, c.pin_cell, c.pin_dx, c.pin_dy, c.pin_slot, s));
+                         d_lanes, d_cslot, c.pin_cell, c.pin_dx, c.pin_dy, c.pin_slot, s));
     CK(cudaStreamSynchronize(s));
     return FFTPL_OK;
 }
@@ -782,7 +793,6 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
     CK(cudaMemcpyAsync(c.tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.ph, ph.data(), (n + 1) * sizeof(float2), cudaMemcpyHostToDevice, s));
     TRY(build_slabs(c, nets, pins));
-    CK(prepare_wa(c));
     if (c.opt.deterministic) {
         // capacity in blocks of every kernel that reduces on each stream
         long long cap0 = std::max<long long>((long long)n / 4, (2LL * c.m_mov + kCellThreads - 1) / kCellThreads);
@@ -793,7 +803,7 @@ static fftpl_status create_impl(Ctx& c, const fftpl_region* R, int32_t n, const 
             cap0 = std::max<long long>(cap0, ((long long)(n / 2) * (n / 2 + 1) + 255) / 256);
         long long cap1 = std::max<long long>(
             ((long long)(c.nslabs - c.nbig) + kWaThreads / 32 - 1) / (kWaThreads / 32),
-            ((long long)c.nbig + kBigWarps - 1) / kBigWarps);
+            ((long long)c.nbig + kWaThreads / 32 - 1) / (kWaThreads / 32));
         cap1 = std::max<long long>(cap1, ((long long)c.m_mov + kCellThreads - 1) / kCellThreads);
         c.det_cap[0] = (int)std::max<long long>(cap0, 1);
         c.det_cap[1] = (int)std::max<long long>(cap1, 1);
@@ -1145,6 +1155,7 @@ fftpl_status fftpl_place_init(fftpl_t h, const float* x0, const float* y0) {
     ctrl[C_MOV_AREA] = c.mov_area > 0 ? c.mov_area : 1.0;
     ctrl[C_ALPHA_CAP] = c.opt.alpha_max_cap_bins * c.wb;
     cudaStream_t s = c.stream;
+    ctrl_mirror(ctrl.data());
     CK(cudaMemcpyAsync(c.ctrl, ctrl.data(), ctrl.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(launch_place_init(c, x0, y0, s));
     if (c.opt.gamma_fixed <= 0.0) {
@@ -1185,7 +1196,8 @@ static fftpl_status loop_eval(Ctx& c, bool cells) {
         Stage st(c, 4, c.side);
         if (!c.opt.deterministic)
             CK(cudaMemsetAsync(c.gW2, 0, (size_t)c.m_mov * sizeof(float2), c.side));
-        CK(launch_wa_impl(c, vx, vy, 1.0f, c.ctrl + C_GAMMA, c.ctrl + C_DONE, false, c.side));
+        CK(launch_wa_impl(c, vx, vy, 1.0f, ctrl_f(c.ctrl) + F_INV_G, ctrl_f(c.ctrl) + F_DONE,
+                          false, c.side));
     }
     CK(cudaEventRecord(c.ev_join, c.side));
     TRY(enqueue_solve(c, s));

@@ -32,11 +32,14 @@ constexpr int kSpecThreads = 256;   // threads of the transform kernels
 constexpr int kSpecBuffers = 4;     // complex length-n buffers per CTA
 constexpr int kCellThreads = 256;
 constexpr int kWaThreads = 256;
-// Slabs of degree kBigMin..kBigMax go to the shared-memory WA kernel
-// (k_wa_big, kBigWarps warps per block); the rest to k_wa.
+// Nets of degree kBigMin..kBigMax go to the WA kernel with several lanes per
+// net (k_wa_grp, grp_lanes(d) lanes each, at most 4 pins per lane); the rest
+// to k_wa (one lane per net).
 constexpr int kBigMin = 7;
 constexpr int kBigMax = 64;
-constexpr int kBigWarps = 2;
+__host__ __device__ constexpr int grp_lanes(int d) {
+    return d <= 8 ? 2 : (d <= 16 ? 4 : (d <= 32 ? 8 : 16));
+}
 constexpr int kWaPinCap = 2048;     // pins staged in shared memory per WA CTA
 
 // accumulator slots (FP64 sums written by the kernels)
@@ -377,6 +380,13 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
+// WA smoothing factors of gamma in float32: 1/gamma and log2(e)/gamma (the
+// exponentials are exp2(t log2(e) / gamma)), the same on host and device.
+__host__ __device__ inline void wa_scale(float gamma, float* inv_g, float* l2g) {
+    *inv_g = 1.0f / gamma;
+    *l2g = (float)(1.4426950408889634 / (double)gamma);
+}
+
 // -------------------------------------------------------- the context
 struct Ctx {
     // problem
@@ -410,9 +420,10 @@ struct Ctx {
     float2* E2 = nullptr;       // interleaved field (E_x, E_y) [n][n]
     float2 *tw = nullptr, *ph = nullptr;
     // pins re-laid into degree slabs (see k_wire.cu): slot base + 32 k + lane
-    int4* slabs = nullptr;      // {base slot, degree, net count, 0}
+    int4* slabs = nullptr;      // {base slot, degree, net count, lanes per net (0: one
+                                // net per lane)}
     int nslabs = 0;
-    int nbig = 0;               // the first nbig slabs: degree kBigMin..kBigMax (k_wa_big)
+    int nbig = 0;               // the first nbig slabs: degree kBigMin..kBigMax (k_wa_grp)
     int big_dmax = 0;           // their largest degree
     int num_sms = 1;            // of the handle's device
     int64_t slab_slots = 0;
@@ -498,8 +509,6 @@ void set_global_error(const std::string& msg);
 // ------------------------------------------------------------ launchers
 // (each returns the CUDA error of the launch)
 void prepare_spectral(int logn);
-// shared-memory opt-in of the WA kernels for this handle (create time)
-cudaError_t prepare_wa(const Ctx& c);
 cudaError_t launch_scatter(Ctx& c, const float* x, const float* y, const float* w,
                            const float* h, int m, float* D, long long* Dq, cudaStream_t s);
 // movable cells into the handle's D / Dq; write_pos: also the interleaved
@@ -528,7 +537,7 @@ cudaError_t launch_gather(Ctx& c, const float* x, const float* y, float* gx, flo
 cudaError_t launch_wa(Ctx& c, const float* x, const float* y, float gamma, cudaStream_t s);
 // interleave = false: pos2 already written (by launch_scatter_mov)
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
-                           const double* gamma_dev, const double* done, bool interleave,
+                           const float* scale_dev, const float* done, bool interleave,
                            cudaStream_t s);
 cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s);
 // 1 when the WA kernel runs slab pairs per warp (large instances)
@@ -547,8 +556,9 @@ cudaError_t launch_net_key(int m, int E, const int* np, const int* pc, const int
                            cudaStream_t s);
 cudaError_t launch_fill_slabs(int m, int E, const int* np, const int* pc, const float* dx,
                               const float* dy, const int* rank, const float* fix_x,
-                              const float* fix_y, const int* net_slot, const int* cslot, int* spc,
-                              float* sdx, float* sdy, int* sslot, cudaStream_t s);
+                              const float* fix_y, const int* net_slot, const int* net_lanes,
+                              const int* cslot, int* spc, float* sdx, float* sdy, int* sslot,
+                              cudaStream_t s);
 
 // tensor-core solve path (k_tc.cu): tc_setup lays the plan out in a device
 // block of tc_elems(n) bf16 elements owned by the handle and fills its

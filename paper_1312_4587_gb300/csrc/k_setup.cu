@@ -86,17 +86,19 @@ __global__ void k_fill_slabs(int E, const int* __restrict__ np, const int* __res
                              const float* __restrict__ dx, const float* __restrict__ dy, int m,
                              const int* __restrict__ rank, const float* __restrict__ fix_x,
                              const float* __restrict__ fix_y, const int* __restrict__ net_slot,
-                             const int* __restrict__ cslot, int* __restrict__ spc,
-                             float* __restrict__ sdx, float* __restrict__ sdy,
-                             int* __restrict__ sslot) {
+                             const int* __restrict__ net_lanes, const int* __restrict__ cslot,
+                             int* __restrict__ spc, float* __restrict__ sdx,
+                             float* __restrict__ sdy, int* __restrict__ sslot) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     const int base = net_slot[e];
     if (base < 0) return;
+    // L lanes per net: pin k at base + 32 (k / L) + k % L (L = 1: base + 32 k)
+    const int L = net_lanes[e];
     const int p0 = np[e], d = np[e + 1] - p0;
     for (int k = 0; k < d; ++k) {
         const int p = p0 + k;
-        const size_t slot = (size_t)base + 32 * (size_t)k;
+        const size_t slot = (size_t)base + 32 * (size_t)(k / L) + (size_t)(k % L);
         const int cc = pc[p];
         if (cc < m) {
             spc[slot] = rank[cc];
@@ -137,11 +139,12 @@ cudaError_t launch_net_key(int m, int E, const int* np, const int* pc, const int
 
 cudaError_t launch_fill_slabs(int m, int E, const int* np, const int* pc, const float* dx,
                               const float* dy, const int* rank, const float* fix_x,
-                              const float* fix_y, const int* net_slot, const int* cslot, int* spc,
-                              float* sdx, float* sdy, int* sslot, cudaStream_t s) {
+                              const float* fix_y, const int* net_slot, const int* net_lanes,
+                              const int* cslot, int* spc, float* sdx, float* sdy, int* sslot,
+                              cudaStream_t s) {
     if (E <= 0) return cudaSuccess;
-    k_fill_slabs<<<nb(E), 256, 0, s>>>(E, np, pc, dx, dy, m, rank, fix_x, fix_y, net_slot, cslot,
-                                       spc, sdx, sdy, sslot);
+    k_fill_slabs<<<nb(E), 256, 0, s>>>(E, np, pc, dx, dy, m, rank, fix_x, fix_y, net_slot,
+                                       net_lanes, cslot, spc, sdx, sdy, sslot);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,8 @@ __global__ void __launch_bounds__(kCellThreads, 6)
 k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
              const int* __restrict__ rank, const int* __restrict__ cell_pin_ptr,
              const float2* __restrict__ gpin, const float2* __restrict__ gW2) {
-    if (b.ctrl[C_DONE] != 0.0) return;
+    const float* cf = ctrl_f(b.ctrl);
+    if (cf[F_DONE] != 0.0f) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float nx = 0.0f, ny = 0.0f, wx = 0.0f, wy = 0.0f;
     if (i < m) {
@@ -55,10 +56,11 @@ k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
 
 // g = gW + lambda gN; sums for alpha_k; last CTA: alpha_k and beta_k.
 __global__ void __launch_bounds__(kCellThreads) k_loop_g(int m2, LoopBufs b) {
-    if (b.ctrl[C_DONE] != 0.0) return;
+    const float* cf = ctrl_f(b.ctrl);
+    if (cf[F_DONE] != 0.0f) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const float lam = (float)b.ctrl[C_LAMBDA];
-    const bool first = b.ctrl[C_K] == 0.0;
+    const float lam = cf[F_LAMBDA];
+    const bool first = cf[F_FIRST] != 0.0f;
     float dg = 0.0f, dv = 0.0f, gi = 0.0f;
     if (i < m2) {
         float gg = fmaf(lam, b.gN[i], b.gW[i]);
@@ -79,9 +81,10 @@ __global__ void __launch_bounds__(kCellThreads) k_loop_g(int m2, LoopBufs b) {
 // clamp keeps the cell inside the region.  Last CTA: record and advance.
 __global__ void __launch_bounds__(kCellThreads)
 k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
-    if (b.ctrl[C_DONE] != 0.0) return;
+    const float* cf = ctrl_f(b.ctrl);
+    if (cf[F_DONE] != 0.0f) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const float alpha = (float)b.ctrl[C_ALPHA], beta = (float)b.ctrl[C_BETA];
+    const float alpha = cf[F_ALPHA], beta = cf[F_BETA];
     float step = 0.0f, uphill = 0.0f;
     if (i < 2 * m) {
         bool isx = i < m;
@@ -111,10 +114,11 @@ k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
 // g = gW + lambda gN; sums |g|^2 and g . g_prev, max |g|; last CTA: beta,
 // f_k and the values recorded for iteration k.
 __global__ void __launch_bounds__(kCellThreads) k_cg_g(int m2, LoopBufs b) {
-    if (b.ctrl[C_DONE] != 0.0) return;
+    const float* cf = ctrl_f(b.ctrl);
+    if (cf[F_DONE] != 0.0f) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const float lam = (float)b.ctrl[C_LAMBDA];
-    const bool first = b.ctrl[C_K] == 0.0;
+    const float lam = cf[F_LAMBDA];
+    const bool first = cf[F_FIRST] != 0.0f;
     float sq = 0.0f, gp = 0.0f, gi = 0.0f;
     if (i < m2) {
         float gg = fmaf(lam, b.gN[i], b.gW[i]);
@@ -131,10 +135,11 @@ __global__ void __launch_bounds__(kCellThreads) k_cg_g(int m2, LoopBufs b) {
 // d = -g + beta d; sum g . d and max |d|; last CTA: restart test, |d|_inf
 // and the slope.
 __global__ void __launch_bounds__(kCellThreads) k_cg_dir(int m2, LoopBufs b) {
-    if (b.ctrl[C_DONE] != 0.0) return;
+    const float* cf = ctrl_f(b.ctrl);
+    if (cf[F_DONE] != 0.0f) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const float beta = (float)b.ctrl[C_BETA];
-    const bool first = b.ctrl[C_K] == 0.0;
+    const float beta = cf[F_BETA];
+    const bool first = cf[F_FIRST] != 0.0f;
     float gd = 0.0f, da = 0.0f;
     if (i < m2) {
         float gi = b.g[i];
@@ -157,17 +162,17 @@ __device__ __forceinline__ void cg_coord(int i, int m, const Grid& gr, float x1,
     const float half = __fmul_rn(0.5f, isx ? b.w[c] : b.h[c]);
     lo = __fadd_rn(isx ? gr.x0 : gr.y0, half);
     hi = __fsub_rn(isx ? x1 : y1, half);
-    dir = b.ctrl[C_RESTART] != 0.0 ? -b.g[i] : b.vprev[i];
+    dir = ctrl_f(b.ctrl)[F_RESTART] != 0.0f ? -b.g[i] : b.vprev[i];
 }
 
 // trial point v = clamp(u + a_max dir / |d|_inf)
 __global__ void __launch_bounds__(kCellThreads)
 k_cg_trial(int m, Grid gr, float x1, float y1, LoopBufs b) {
-    if (b.ctrl[C_DONE] != 0.0) return;
+    const float* cf = ctrl_f(b.ctrl);
+    if (cf[F_DONE] != 0.0f) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 2 * m) return;
-    const double dinf = b.ctrl[C_DINF];
-    const float scale = dinf > 0.0 ? (float)(b.ctrl[C_ALPHA_MAX] / dinf) : 0.0f;
+    const float scale = cf[F_SCALE_TRIAL];
     float dir, lo, hi;
     cg_coord(i, m, gr, x1, y1, b, dir, lo, hi);
     b.v[i] = fminf(hi, fmaxf(lo, fmaf(scale, dir, b.u[i])));
@@ -183,11 +188,11 @@ __global__ void k_cg_alpha(double* ctrl, const double* acc) {
 // record and advance.
 __global__ void __launch_bounds__(kCellThreads)
 k_cg_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
-    if (b.ctrl[C_DONE] != 0.0) return;
+    const float* cf = ctrl_f(b.ctrl);
+    if (cf[F_DONE] != 0.0f) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 2 * m) {
-        const double dinf = b.ctrl[C_DINF];
-        const float scale = dinf > 0.0 ? (float)(b.ctrl[C_ALPHA] / dinf) : 0.0f;
+        const float scale = cf[F_SCALE_UPDATE];
         float dir, lo, hi;
         cg_coord(i, m, gr, x1, y1, b, dir, lo, hi);
         const float un = fminf(hi, fmaxf(lo, fmaf(scale, dir, b.u[i])));
@@ -221,6 +226,7 @@ __global__ void k_place_init(int m, Grid gr, float x1, float y1, const float* __
 __global__ void k_gamma0(double* ctrl, const double* acc) {
     double tau = acc_sum(acc, ACC_TAU) / ctrl[C_MOV_AREA];
     ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
+    ctrl_mirror(ctrl);
 }
 
 static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }

@@ -17,17 +17,18 @@
 
 namespace fftpl {
 
-// Nets are re-laid at create time into slabs of up to 32 nets of one degree
-// d (slab = {first pin slot, d, net count}); pin k of the slab's net j sits
-// at slot base + 32 k + j.  One warp per slab, one lane per net: every lane
-// walks the same d pins (no divergence), each pin-record read of the warp is
-// one contiguous access, and the cell-centre gathers of a slab touch nearby
-// lines (cells are numbered by regions of the netlist).  k_wa takes the
-// slabs of degree 2..6 (the bulk of the nets; a body specialised for the
-// degree, pin coordinates in registers, two slabs per warp for degree 2..4
-// on large instances) and those above kBigMax (runtime degree, coordinates
-// staged in pxy); k_wa_big the slabs of degree kBigMin..kBigMax (records
-// and coordinates in shared memory).
+// Nets are re-laid at create time into slabs of nets of one degree d (slab
+// = {first pin slot, d, net count, lanes per net}).  Below kBigMin and
+// above kBigMax a slab holds up to 32 nets, pin k of its net j at slot
+// base + 32 k + j: one warp per slab, one lane per net, every lane walks the
+// same d pins (no divergence), each pin-record read of the warp is one
+// contiguous access, and the cell-centre gathers of a slab touch nearby
+// lines (cells are numbered by regions of the netlist).  k_wa takes these
+// (degree 2..6: the bulk of the nets, a body specialised for the degree,
+// pin coordinates in registers, two slabs per warp for degree 2..4 on large
+// instances; above kBigMax: runtime degree, coordinates staged in pxy).
+// k_wa_grp takes the slabs of degree kBigMin..kBigMax, several lanes per net
+// with shuffle reductions (see wa_group).
 
 // (x, y) -> interleaved positions at each cell's internal number, so that
 // one 8-byte load (one sector) fetches a pin's cell centre and the pins of a
@@ -35,8 +36,8 @@ namespace fftpl {
 __global__ void __launch_bounds__(256)
 k_interleave(int m, const float* __restrict__ x, const float* __restrict__ y,
              const int* __restrict__ rank, float2* __restrict__ pos,
-             const double* __restrict__ done) {
-    if (done && *done != 0.0) return;
+             const float* __restrict__ done) {
+    if (done && *done != 0.0f) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) pos[rank[i]] = make_float2(x[i], y[i]);
 }
@@ -319,16 +320,19 @@ __device__ __forceinline__ void wa_slab(const WaIo& io, const int4& sl, int lane
 // room for a warp per slab and latency matters more).
 template <bool CSR, bool LSE>
 __global__ void __launch_bounds__(kWaThreads, 4)
-k_wa(int nslabs, int pairs, const int4* __restrict__ slabs, WaIo io, float gamma,
-     const double* __restrict__ gamma_dev, double* __restrict__ acc,
-     const double* __restrict__ done, DetRed dr) {
-    if (done && *done != 0.0) return;
+k_wa(int nslabs, int pairs, const int4* __restrict__ slabs, WaIo io, float inv_g, float l2g,
+     const float* __restrict__ scale_dev, double* __restrict__ acc,
+     const float* __restrict__ done, DetRed dr) {
+    if (done && *done != 0.0f) return;
     const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (gamma_dev) gamma = (float)*gamma_dev;
-    const float inv_g = 1.0f / gamma;
-    // exp(t / g) = exp2(t * log2(e) / g)
-    const float l2g = (float)(1.4426950408889634 / (double)gamma);
+    // 1/gamma and log2(e)/gamma: from the loop's control mirror, or computed
+    // on the host (exp(t / g) = exp2(t * log2(e) / g))
+    if (scale_dev) {
+        const float2 sc = *reinterpret_cast<const float2*>(scale_dev);
+        inv_g = sc.x;
+        l2g = sc.y;
+    }
     const int4 zero = make_int4(0, 0, 0, 0);
     float wsum = 0.0f, hsum = 0.0f;
     if (!pairs) {
@@ -354,140 +358,146 @@ k_wa(int nslabs, int pairs, const int4* __restrict__ slabs, WaIo io, float gamma
 }
 
 // ------------------------------------------------ slabs of degree 7..64
-// One warp per slab.  The slab's pin records (32 d words per field, the
-// warp's own lanes' slots) are copied into the warp's share of shared memory
-// with asynchronous 4-byte copies, all of them in flight at once; the
-// cell-centre gathers then go out kGather at a time and the pin coordinates
-// replace the offsets in shared memory, where the exponential sums and the
-// gradients read them.  So a slab costs about three memory latencies
-// whatever its degree, where the register path's loop over d pins would pay
-// one per few pins.  The per-net arithmetic is that of wa_net_any, pin by
-// pin in the same order.
-constexpr int kGather = 8;
-
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                     (uint32_t)__cvta_generic_to_shared(smem_dst)),
-                 "l"(gsrc)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-template <bool CSR, bool LSE>
-__device__ __forceinline__ void wa_net_big(const WaIo& io, int d, const int* sc, float* sx,
-                                           float* sy, const int* sq, int lane, float l2g,
-                                           float inv_g, float& wsum, float& hsum) {
+// L = grp_lanes(d) lanes per net (2 up to degree 8, 4 up to 16, 8 up to 32,
+// 16 up to 64), 32 / L nets per warp, R = ceil(d / L) <= 4 pins per lane: lane
+// g L + j of the slab holds pins j, j + L, ... of net g (slots base + 32 r +
+// lane), so all of a net's record loads and centre gathers are in flight at
+// once.  Each lane reduces its pins, then the L lanes of a net combine the
+// maxima, minima and the exponential sums with xor shuffles (lanes of other
+// nets are never mixed: the groups are aligned).  Lanes past the net's
+// degree or past the slab's net count hold padding and take no part.
+template <int L, int R, bool CSR, bool LSE>
+__device__ __forceinline__ void wa_group(const WaIo& io, const int4& sl, int lane, float l2g,
+                                         float inv_g, float& wsum, float& hsum) {
+    const int j = lane % L;
+    const bool live = lane / L < sl.z;
+    const int d = sl.y;
+    int cr[R];
+    float ox[R], oy[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int slot = sl.x + 32 * r + lane;
+        cr[r] = io.pin_cell[slot];
+        ox[r] = io.pin_dx[slot];
+        oy[r] = io.pin_dy[slot];
+    }
+    float px[R], py[R];
+    bool ok[R];
     float Mx = -INFINITY, My = -INFINITY, mx = INFINITY, my = INFINITY;
-    for (int k0 = 0; k0 < d; k0 += kGather) {
-        float2 g[kGather];
 #pragma unroll
-        for (int t = 0; t < kGather; ++t) {
-            g[t] = make_float2(0.0f, 0.0f);
-            if (k0 + t < d) {
-                const int c = sc[32 * (k0 + t) + lane];
-                if (c >= 0) g[t] = __ldg(io.pos + c);
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < kGather; ++t) {
-            if (k0 + t < d) {
-                const int i = 32 * (k0 + t) + lane;
-                const float px = __fadd_rn(g[t].x, sx[i]), py = __fadd_rn(g[t].y, sy[i]);
-                sx[i] = px;
-                sy[i] = py;
-                Mx = fmaxf(Mx, px); mx = fminf(mx, px);
-                My = fmaxf(My, py); my = fminf(my, py);
-            }
+    for (int r = 0; r < R; ++r) {
+        ok[r] = live && r * L + j < d;
+        const float2 p = pin_xy(io, cr[r], ox[r], oy[r]);
+        px[r] = p.x;
+        py[r] = p.y;
+        if (ok[r]) {
+            Mx = fmaxf(Mx, px[r]); mx = fminf(mx, px[r]);
+            My = fmaxf(My, py[r]); my = fminf(my, py[r]);
         }
     }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        Mx = fmaxf(Mx, __shfl_xor_sync(0xffffffffu, Mx, o));
+        mx = fminf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        My = fmaxf(My, __shfl_xor_sync(0xffffffffu, My, o));
+        my = fminf(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    float apx[R], amx[R], apy[R], amy[R];
     float Spx = 0, Tpx = 0, Smx = 0, Tmx = 0, Spy = 0, Tpy = 0, Smy = 0, Tmy = 0;
-#pragma unroll 4
-    for (int k = 0; k < d; ++k) {
-        const int i = 32 * k + lane;
-        float tpx = sx[i] - Mx, tmx = sx[i] - mx, tpy = sy[i] - My, tmy = sy[i] - my;
-        float apx = exp2f(tpx * l2g), amx = exp2f(-tmx * l2g);
-        float apy = exp2f(tpy * l2g), amy = exp2f(-tmy * l2g);
-        Spx += apx; Tpx = fmaf(tpx, apx, Tpx); Smx += amx; Tmx = fmaf(tmx, amx, Tmx);
-        Spy += apy; Tpy = fmaf(tpy, apy, Tpy); Smy += amy; Tmy = fmaf(tmy, amy, Tmy);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float tpx = px[r] - Mx, tmx = px[r] - mx, tpy = py[r] - My, tmy = py[r] - my;
+        apx[r] = ok[r] ? exp2f(tpx * l2g) : 0.0f;
+        amx[r] = ok[r] ? exp2f(-tmx * l2g) : 0.0f;
+        apy[r] = ok[r] ? exp2f(tpy * l2g) : 0.0f;
+        amy[r] = ok[r] ? exp2f(-tmy * l2g) : 0.0f;
+        Spx += apx[r]; Tpx = fmaf(tpx, apx[r], Tpx); Smx += amx[r]; Tmx = fmaf(tmx, amx[r], Tmx);
+        Spy += apy[r]; Tpy = fmaf(tpy, apy[r], Tpy); Smy += amy[r]; Tmy = fmaf(tmy, amy[r], Tmy);
     }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        Spx += __shfl_xor_sync(0xffffffffu, Spx, o);
+        Tpx += __shfl_xor_sync(0xffffffffu, Tpx, o);
+        Smx += __shfl_xor_sync(0xffffffffu, Smx, o);
+        Tmx += __shfl_xor_sync(0xffffffffu, Tmx, o);
+        Spy += __shfl_xor_sync(0xffffffffu, Spy, o);
+        Tpy += __shfl_xor_sync(0xffffffffu, Tpy, o);
+        Smy += __shfl_xor_sync(0xffffffffu, Smy, o);
+        Tmy += __shfl_xor_sync(0xffffffffu, Tmy, o);
+    }
+    if (!live) return;
+    // every S is in [1, d] (its largest term is exp(0) = 1)
     const float isx = __fdividef(1.0f, Spx), imx = __fdividef(1.0f, Smx);
     const float isy = __fdividef(1.0f, Spy), imy = __fdividef(1.0f, Smy);
     const float Wpx = Tpx * isx, Wmx = Tmx * imx, Wpy = Tpy * isy, Wmy = Tmy * imy;
-    const float span = (Mx - mx) + (My - my);
-    hsum += span;
-    if (LSE)
-        wsum += span + __fdividef(1.0f, inv_g) * ((logf(Spx) + logf(Smx)) +
-                                                  (logf(Spy) + logf(Smy)));
-    else
-        wsum += span + ((Wpx - Wmx) + (Wpy - Wmy));
+    if (j == 0) {
+        const float span = (Mx - mx) + (My - my);
+        hsum += span;
+        if (LSE)
+            wsum += span + __fdividef(1.0f, inv_g) * ((logf(Spx) + logf(Smx)) +
+                                                      (logf(Spy) + logf(Smy)));
+        else
+            wsum += span + ((Wpx - Wmx) + (Wpy - Wmy));
+    }
     const float P0x = isx * fmaf(-Wpx, inv_g, 1.0f), P1x = isx * inv_g;
     const float Q0x = imx * fmaf(Wmx, inv_g, 1.0f), Q1x = imx * inv_g;
     const float P0y = isy * fmaf(-Wpy, inv_g, 1.0f), P1y = isy * inv_g;
     const float Q0y = imy * fmaf(Wmy, inv_g, 1.0f), Q1y = imy * inv_g;
-#pragma unroll 4
-    for (int k = 0; k < d; ++k) {
-        const int i = 32 * k + lane;
-        float tpx = sx[i] - Mx, tmx = sx[i] - mx, tpy = sy[i] - My, tmy = sy[i] - my;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (!ok[r]) continue;
+        const float tpx = px[r] - Mx, tmx = px[r] - mx, tpy = py[r] - My, tmy = py[r] - my;
         float gxj, gyj;
         if (LSE) {
-            gxj = exp2f(tpx * l2g) * isx - exp2f(-tmx * l2g) * imx;
-            gyj = exp2f(tpy * l2g) * isy - exp2f(-tmy * l2g) * imy;
+            gxj = apx[r] * isx - amx[r] * imx;
+            gyj = apy[r] * isy - amy[r] * imy;
         } else {
-            gxj = exp2f(tpx * l2g) * fmaf(tpx, P1x, P0x) - exp2f(-tmx * l2g) * fmaf(-tmx, Q1x, Q0x);
-            gyj = exp2f(tpy * l2g) * fmaf(tpy, P1y, P0y) - exp2f(-tmy * l2g) * fmaf(-tmy, Q1y, Q0y);
+            gxj = apx[r] * fmaf(tpx, P1x, P0x) - amx[r] * fmaf(-tmx, Q1x, Q0x);
+            gyj = apy[r] * fmaf(tpy, P1y, P0y) - amy[r] * fmaf(-tmy, Q1y, Q0y);
         }
+        const int slot = sl.x + 32 * r + lane;
         if (CSR) {
-            const int q = sq[i];
+            const int q = io.pin_slot[slot];
             if (q >= 0) io.gpin[q] = make_float2(gxj, gyj);
-        } else {
-            const int c = sc[i];
-            if (c >= 0) red_add_f2(io.gW + c, gxj, gyj);
+        } else if (cr[r] >= 0) {
+            red_add_f2(io.gW + cr[r], gxj, gyj);
         }
     }
 }
 
-// Shared memory of one warp of k_wa_big: (3 or, with the deterministic
-// slots, 4) fields x 32 lanes x dmax words.
-__host__ __device__ inline size_t big_warp_words(bool csr, int dmax) {
-    return (csr ? 4 : 3) * 32 * (size_t)dmax;
-}
-
+// One warp per slab of degree kBigMin..kBigMax.  Runs after k_wa on the same
+// stream and adds to its totals.
 template <bool CSR, bool LSE>
-__global__ void __launch_bounds__(kBigWarps * 32)
-k_wa_big(int nbig, int dmax, const int4* __restrict__ slabs, WaIo io, float gamma,
-         const double* __restrict__ gamma_dev, double* __restrict__ acc,
-         const double* __restrict__ done, DetRed dr) {
-    extern __shared__ __align__(16) int wa_sm[];
-    if (done && *done != 0.0) return;
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int warp = blockIdx.x * kBigWarps + wib;
-    if (gamma_dev) gamma = (float)*gamma_dev;
-    const float inv_g = 1.0f / gamma;
-    const float l2g = (float)(1.4426950408889634 / (double)gamma);
+__global__ void __launch_bounds__(kWaThreads)
+k_wa_grp(int nbig, const int4* __restrict__ slabs, WaIo io, float inv_g, float l2g,
+         const float* __restrict__ scale_dev, double* __restrict__ acc,
+         const float* __restrict__ done, DetRed dr, int* __restrict__ err) {
+    if (done && *done != 0.0f) return;
+    const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    // 1/gamma and log2(e)/gamma: from the loop's control mirror, or computed
+    // on the host (exp(t / g) = exp2(t * log2(e) / g))
+    if (scale_dev) {
+        const float2 sc = *reinterpret_cast<const float2*>(scale_dev);
+        inv_g = sc.x;
+        l2g = sc.y;
+    }
     float wsum = 0.0f, hsum = 0.0f;
     if (warp < nbig) {
         const int4 sl = slabs[warp];
-        const int d = sl.y, w32 = 32 * dmax;
-        int* sc = wa_sm + (size_t)wib * big_warp_words(CSR, dmax);
-        float* sx = reinterpret_cast<float*>(sc + w32);
-        float* sy = reinterpret_cast<float*>(sc + 2 * w32);
-        int* sq = sc + 3 * w32;   // deterministic mode only
-        // every lane copies (and later reads) only its own slots; the slab
-        // has all 32 lanes' slots (padding: cell -1, offsets 0)
-        for (int k = 0; k < d; ++k) {
-            const int slot = sl.x + 32 * k + lane, i = 32 * k + lane;
-            cp_async4(sc + i, io.pin_cell + slot);
-            cp_async4(sx + i, io.pin_dx + slot);
-            cp_async4(sy + i, io.pin_dy + slot);
-            if (CSR) cp_async4(sq + i, io.pin_slot + slot);
+        // (L, R) is the same for the whole warp: no divergence
+        switch (sl.w * 8 + (sl.y + sl.w - 1) / sl.w) {
+            case 2 * 8 + 4: wa_group<2, 4, CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum); break;
+            case 4 * 8 + 2: wa_group<4, 2, CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum); break;
+            case 4 * 8 + 3: wa_group<4, 3, CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum); break;
+            case 4 * 8 + 4: wa_group<4, 4, CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum); break;
+            case 8 * 8 + 3: wa_group<8, 3, CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum); break;
+            case 8 * 8 + 4: wa_group<8, 4, CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum); break;
+            case 16 * 8 + 3: wa_group<16, 3, CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum); break;
+            case 16 * 8 + 4: wa_group<16, 4, CSR, LSE>(io, sl, lane, l2g, inv_g, wsum, hsum); break;
+            default: if (lane == 0) atomicOr(err, ERR_BOUNDS); break;   // no such layout
         }
-        cp_async_wait_all();
-        if (lane < sl.z) wa_net_big<CSR, LSE>(io, d, sc, sx, sy, sq, lane, l2g, inv_g, wsum, hsum);
     }
-    // after k_wa on the same stream: add to its totals
     reduce2(wsum, hsum, acc, ACC_W, ACC_HPWL, dr, true);
 }
 
@@ -504,8 +514,8 @@ k_cells(Grid g, int m, const float* __restrict__ x, const float* __restrict__ y,
         float* __restrict__ gWx, float* __restrict__ gWy, const int* __restrict__ rank,
         const int* __restrict__ cell_pin_ptr, const float2* __restrict__ gpin,
         const float2* __restrict__ gW2, double* __restrict__ acc,
-        const double* __restrict__ done, DetRed dr) {
-    if (done && *done != 0.0) return;
+        const float* __restrict__ done, DetRed dr) {
+    if (done && *done != 0.0f) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float nx = 0.0f, ny = 0.0f, wx = 0.0f, wy = 0.0f;
     if (i < m) {
@@ -578,25 +588,8 @@ int wa_pairs(const Ctx& c) {
     return (c.nslabs - c.nbig) >= 2LL * c.num_sms * 4 * (kWaThreads / 32) ? 1 : 0;
 }
 
-cudaError_t prepare_wa(const Ctx& c) {
-    if (c.nbig <= 0) return cudaSuccess;
-    // the opt-in is per kernel, not per handle: always the largest any
-    // handle can ask for, so that no later handle lowers it under another
-    const int bytes = (int)(kBigWarps * big_warp_words(true, kBigMax) * 4);
-    cudaError_t e = cudaSuccess;
-    auto set = [&](const void* f) {
-        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e == cudaSuccess) e = r;
-    };
-    set((const void*)k_wa_big<false, false>);
-    set((const void*)k_wa_big<false, true>);
-    set((const void*)k_wa_big<true, false>);
-    set((const void*)k_wa_big<true, true>);
-    return e;
-}
-
 cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
-                           const double* gamma_dev, const double* done, bool interleave,
+                           const float* scale_dev, const float* done, bool interleave,
                            cudaStream_t s) {
     if (c.nslabs <= 0) return cudaSuccess;
     if (c.m_mov > 0 && interleave) {
@@ -608,16 +601,18 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
                   c.opt.deterministic ? nullptr : c.gW2, c.pin_slot, c.gpin};
     const bool lse = c.opt.wirelength == FFTPL_WL_LSE;
     const bool det = c.opt.deterministic != 0;
+    float inv_g = 0.0f, l2g = 0.0f;
+    if (!scale_dev) wa_scale(gamma, &inv_g, &l2g);
     // k_wa: the slabs after the first nbig (degree 2..6 and above kBigMax);
-    // it stores the deterministic totals, k_wa_big (next, same stream) adds
+    // it stores the deterministic totals, k_wa_grp (next, same stream) adds
     const int nsmall = c.nslabs - c.nbig;
     if (nsmall > 0) {
         const int wpb = kWaThreads / 32;
         const int pairs = wa_pairs(c);
         const int nb = std::max(1, nblk(pairs ? (nsmall + 1) / 2 : nsmall, wpb));
         auto go = [&](auto kern) {
-            kern<<<nb, kWaThreads, 0, s>>>(nsmall, pairs, c.slabs + c.nbig, io, gamma, gamma_dev,
-                                           c.acc, done, det_red(c, 1));
+            kern<<<nb, kWaThreads, 0, s>>>(nsmall, pairs, c.slabs + c.nbig, io, inv_g, l2g,
+                                           scale_dev, c.acc, done, det_red(c, 1));
         };
         if (det) {
             if (lse) go(k_wa<true, true>);
@@ -629,18 +624,17 @@ cudaError_t launch_wa_impl(Ctx& c, const float* x, const float* y, float gamma,
         c.launches++;
     }
     if (c.nbig > 0) {
-        const size_t smem = kBigWarps * big_warp_words(det, c.big_dmax) * 4;
-        const int nb = nblk(c.nbig, kBigWarps);
+        const int nb = nblk(c.nbig, kWaThreads / 32);
         auto go = [&](auto kern) {
-            kern<<<nb, kBigWarps * 32, smem, s>>>(c.nbig, c.big_dmax, c.slabs, io, gamma,
-                                                  gamma_dev, c.acc, done, det_red(c, 1));
+            kern<<<nb, kWaThreads, 0, s>>>(c.nbig, c.slabs, io, inv_g, l2g, scale_dev, c.acc,
+                                           done, det_red(c, 1), c.err);
         };
         if (det) {
-            if (lse) go(k_wa_big<true, true>);
-            else go(k_wa_big<true, false>);
+            if (lse) go(k_wa_grp<true, true>);
+            else go(k_wa_grp<true, false>);
         } else {
-            if (lse) go(k_wa_big<false, true>);
-            else go(k_wa_big<false, false>);
+            if (lse) go(k_wa_grp<false, true>);
+            else go(k_wa_grp<false, false>);
         }
         c.launches++;
     }
@@ -665,7 +659,7 @@ cudaError_t launch_pin_sum(Ctx& c, float* gx, float* gy, cudaStream_t s) {
 }
 
 cudaError_t launch_cells_impl(Ctx& c, const float* x, const float* y, float* gNx, float* gNy,
-                              float* gWx, float* gWy, const double* done, cudaStream_t s) {
+                              float* gWx, float* gWy, const float* done, cudaStream_t s) {
     if (c.m_mov <= 0) return cudaSuccess;
     int nb = nblk(c.m_mov, kCellThreads);
     if (c.opt.deterministic)

@@ -17,8 +17,46 @@ enum {
     // |d|_inf, restart flag, and the values recorded for iteration k
     C_GG_PREV, C_FK, C_SLOPE, C_DINF, C_RESTART, C_W_K, C_HP_K, C_N_K, C_TAU_K,
     C_ALPHA_CAP,   // ceiling of alpha_max in the Nesterov loop (0: none)
+    // float32 copies of the values the per-element kernels read (F_*),
+    // packed two to a slot
+    C_FMIRROR, C_FMIRROR_LAST = C_FMIRROR + 4,
     C_COUNT
 };
+
+// The per-element kernels read their control values as float32 from this
+// mirror, written by whichever thread last changed the FP64 scalars (the
+// FP64 pipe of the GPU is narrow: a double compare, conversion or division
+// per thread costs more than the kernel's own arithmetic).  The values are
+// those the kernels computed before from the FP64 scalars.
+enum {
+    F_DONE = 0, F_FIRST, F_LAMBDA, F_ALPHA, F_BETA, F_RESTART, F_SCALE_TRIAL, F_SCALE_UPDATE,
+    F_INV_G, F_L2G,   // 1/gamma and log2(e)/gamma (adjacent: one 8-byte load)
+    F_COUNT
+};
+static_assert(F_COUNT <= 2 * (C_FMIRROR_LAST - C_FMIRROR + 1), "control mirror too small");
+static_assert(F_INV_G % 2 == 0, "1/gamma and log2(e)/gamma share an 8-byte word");
+
+__host__ __device__ inline float* ctrl_f(double* ctrl) {
+    return reinterpret_cast<float*>(ctrl + C_FMIRROR);
+}
+__host__ __device__ inline const float* ctrl_f(const double* ctrl) {
+    return reinterpret_cast<const float*>(ctrl + C_FMIRROR);
+}
+
+__host__ __device__ inline void ctrl_mirror(double* ctrl) {
+    float* f = ctrl_f(ctrl);
+    f[F_DONE] = ctrl[C_DONE] != 0.0 ? 1.0f : 0.0f;
+    f[F_FIRST] = ctrl[C_K] == 0.0 ? 1.0f : 0.0f;
+    f[F_LAMBDA] = (float)ctrl[C_LAMBDA];
+    f[F_ALPHA] = (float)ctrl[C_ALPHA];
+    f[F_BETA] = (float)ctrl[C_BETA];
+    f[F_RESTART] = ctrl[C_RESTART] != 0.0 ? 1.0f : 0.0f;
+    const double dinf = ctrl[C_DINF];
+    f[F_SCALE_TRIAL] = dinf > 0.0 ? (float)(ctrl[C_ALPHA_MAX] / dinf) : 0.0f;
+    f[F_SCALE_UPDATE] = dinf > 0.0 ? (float)(ctrl[C_ALPHA] / dinf) : 0.0f;
+    const float g = (float)ctrl[C_GAMMA];
+    if (g > 0.0f) wa_scale(g, &f[F_INV_G], &f[F_L2G]);
+}
 constexpr int kRecFields = 8;
 constexpr int kCounters = 4;   // one ticket counter per loop kernel kind
 
@@ -67,6 +105,7 @@ __device__ __forceinline__ void ctrl_lambda(double* ctrl, const double* acc) {
     }
     ctrl[C_HP_PREV] = hp;
     ctrl[C_LAMBDA] = lam;
+    ctrl_mirror(ctrl);
 }
 
 // After the combined gradient: the step alpha_k and the momentum weight.
@@ -91,6 +130,7 @@ __device__ __forceinline__ void ctrl_alpha(double* ctrl, const double* acc) {
     ctrl[C_ALPHA] = alpha;
     ctrl[C_A_NEXT] = an;
     ctrl[C_BETA] = (a - 1.0) / an;
+    ctrl_mirror(ctrl);
 }
 
 // gamma = 8.0 w_b 10^((20/9)(tau - 0.1) - 1) (Section IV-A).
@@ -127,6 +167,7 @@ __device__ __forceinline__ void ctrl_record(double* ctrl, const double* acc, dou
     if (ctrl[C_GAMMA_FIXED] <= 0.0) ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
     ctrl[C_K] = (double)(k + 1);
     if (ctrl[C_STOP_ON_TAU] != 0.0 && tau <= ctrl[C_TAU_STOP]) ctrl[C_DONE] = 1.0;
+    ctrl_mirror(ctrl);
 }
 
 // ------------------------------------------------ conjugate-gradient loop
@@ -148,6 +189,7 @@ __device__ __forceinline__ void ctrl_cg_g(double* ctrl, const double* acc) {
     ctrl[C_HP_K] = acc_sum(acc, ACC_HPWL);
     ctrl[C_N_K] = N;
     ctrl[C_TAU_K] = acc_sum(acc, ACC_TAU) / ctrl[C_MOV_AREA];
+    ctrl_mirror(ctrl);
 }
 
 // After d_k: restart to -g_k unless g_k . d_k < 0; |d|_inf and the slope.
@@ -161,6 +203,7 @@ __device__ __forceinline__ void ctrl_cg_dir(double* ctrl, const double* acc) {
     ctrl[C_RESTART] = restart ? 1.0 : 0.0;
     ctrl[C_DINF] = dinf;
     ctrl[C_SLOPE] = dinf > 0.0 ? gd / dinf : 0.0;
+    ctrl_mirror(ctrl);
 }
 
 // After the trial evaluation at a_max: the step a_k from the parabola
@@ -175,6 +218,7 @@ __device__ __forceinline__ void ctrl_cg_alpha(double* ctrl, const double* acc) {
         alpha = fmin(amax, fmax(0.01 * amax, as));
     }
     ctrl[C_ALPHA] = alpha;
+    ctrl_mirror(ctrl);
 }
 
 // After the position update: record iteration k, then a_max_{k+1} =
@@ -198,6 +242,7 @@ __device__ __forceinline__ void ctrl_record_cg(double* ctrl, double* recs) {
     if (ctrl[C_GAMMA_FIXED] <= 0.0) ctrl[C_GAMMA] = gamma_schedule(tau, ctrl[C_WB]);
     ctrl[C_K] = (double)(k + 1);
     if (ctrl[C_STOP_ON_TAU] != 0.0 && tau <= ctrl[C_TAU_STOP]) ctrl[C_DONE] = 1.0;
+    ctrl_mirror(ctrl);
 }
 
 }  // namespace fftpl
