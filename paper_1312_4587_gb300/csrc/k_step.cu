@@ -4,6 +4,8 @@
 // conjugate-gradient step (control of Section IV-A in loop_ctrl.cuh).
 //
 // Vectors hold x coordinates in [0, m) and y coordinates in [m, 2m).
+#include <algorithm>
+
 #include "loop_ctrl.cuh"
 
 namespace fftpl {
@@ -16,8 +18,8 @@ struct LoopBufs {
     DetRed dr;
 };
 
-// gather + pin sums at v (like k_cells, 48 warps per SM) and, in the last
-// CTA, lambda_k.
+// gather + pin sums at v (like k_cells, 48 warps per SM); k_ctrl_lambda
+// then forms lambda_k.
 template <bool CSR>
 __global__ void __launch_bounds__(kCellThreads, 6)
 k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
@@ -51,59 +53,119 @@ k_loop_cells(Grid gr, int m, LoopBufs b, const float2* __restrict__ E2,
         b.gW[m + i] = wy;
     }
     reduce2(fabsf(nx) + fabsf(ny), fabsf(wx) + fabsf(wy), b.acc, ACC_GN_L1, ACC_GW_L1, b.dr);
-    if (last_cta(b.counters + 0) && threadIdx.x == 0) ctrl_lambda(b.ctrl, b.acc);
 }
 
+// lambda_k from the cell kernel's sums (one thread, launched after it: a
+// ticket at the end of each of the cell kernel's 8.6K blocks cost more)
+__global__ void k_ctrl_lambda(double* ctrl, const double* acc) {
+    if (ctrl_f(ctrl)[F_DONE] != 0.0f) return;
+    ctrl_lambda(ctrl, acc);
+}
+
+// The vector kernels of the loop (2m coordinates) run on a fixed grid of
+// kVecBlocksPerSm blocks per SM, each thread striding over the coordinates
+// in batches of four (all loads of a batch before its stores, through
+// restrict-qualified pointers, so that they are in flight together) with
+// its sums kept as double-float pairs: each block ends with block
+// reductions and a ticket (an atomic round trip) that a block per 256
+// coordinates paid 17K times per kernel at 2.2M cells.
+constexpr int kVecBlocksPerSm = 6;
+
 // g = gW + lambda gN; sums for alpha_k; last CTA: alpha_k and beta_k.
-__global__ void __launch_bounds__(kCellThreads) k_loop_g(int m2, LoopBufs b) {
+__global__ void __launch_bounds__(kCellThreads, kVecBlocksPerSm) k_loop_g(int m2, LoopBufs b) {
     const float* cf = ctrl_f(b.ctrl);
     if (cf[F_DONE] != 0.0f) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float lam = cf[F_LAMBDA];
     const bool first = cf[F_FIRST] != 0.0f;
-    float dg = 0.0f, dv = 0.0f, gi = 0.0f;
-    if (i < m2) {
-        float gg = fmaf(lam, b.gN[i], b.gW[i]);
-        b.g[i] = gg;
-        gi = fabsf(gg);
-        if (!first) {
-            float a = gg - b.gprev[i], c = b.v[i] - b.vprev[i];
-            dg = a * a;
-            dv = c * c;
+    dfloat dg = df_zero(), dv = df_zero();
+    float gi = 0.0f;
+    const int stride = gridDim.x * blockDim.x;
+    const float* __restrict__ GN = b.gN;
+    const float* __restrict__ GW = b.gW;
+    const float* __restrict__ GP = b.gprev;
+    const float* __restrict__ V = b.v;
+    const float* __restrict__ VP = b.vprev;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m2; i0 += 4 * stride) {
+        float gn[4], gw[4], gp[4], v[4], vp[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < m2) {
+                gn[k] = GN[i];
+                gw[k] = GW[i];
+                if (!first) {
+                    gp[k] = GP[i];
+                    v[k] = V[i];
+                    vp[k] = VP[i];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < m2) {
+                const float gg = fmaf(lam, gn[k], gw[k]);
+                b.g[i] = gg;
+                gi = fmaxf(gi, fabsf(gg));
+                if (!first) {
+                    const float a = gg - gp[k], c = v[k] - vp[k];
+                    dg = df_add(dg, a * a);
+                    dv = df_add(dv, c * c);
+                }
+            }
         }
     }
-    reduce2(dg, dv, b.acc, ACC_DG2, ACC_DV2, b.dr);
+    reduce2(df_val(dg), df_val(dv), b.acc, ACC_DG2, ACC_DV2, b.dr);
     block_max(gi, b.acc, ACC_GINF);
     if (last_cta(b.counters + 1) && threadIdx.x == 0) ctrl_alpha(b.ctrl, b.acc);
 }
 
 // u_{k+1} = clamp(v_k - alpha g_k); v_{k+1} = clamp(u_{k+1} + beta (u_{k+1} - u_k));
 // clamp keeps the cell inside the region.  Last CTA: record and advance.
-__global__ void __launch_bounds__(kCellThreads)
+__global__ void __launch_bounds__(kCellThreads, kVecBlocksPerSm)
 k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
     const float* cf = ctrl_f(b.ctrl);
     if (cf[F_DONE] != 0.0f) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float alpha = cf[F_ALPHA], beta = cf[F_BETA];
-    float step = 0.0f, uphill = 0.0f;
-    if (i < 2 * m) {
-        bool isx = i < m;
-        int c = isx ? i : i - m;
-        float half = __fmul_rn(0.5f, isx ? b.w[c] : b.h[c]);
-        float lo = __fadd_rn(isx ? gr.x0 : gr.y0, half), hi = __fsub_rn(isx ? x1 : y1, half);
-        float vi = b.v[i], gi = b.g[i], ui = b.u[i];
-        float un = fminf(hi, fmaxf(lo, vi - alpha * gi));
-        step = fabsf(un - vi);
-        uphill = gi * (un - ui);
-        float vn = fminf(hi, fmaxf(lo, un + beta * (un - ui)));
-        b.vprev[i] = vi;
-        b.gprev[i] = gi;
-        b.u[i] = un;
-        b.v[i] = vn;
+    float step = 0.0f;
+    dfloat uphill = df_zero();
+    const int stride = gridDim.x * blockDim.x, n2 = 2 * m;
+    const float* __restrict__ V = b.v;
+    const float* __restrict__ G = b.g;
+    const float* __restrict__ U = b.u;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n2; i0 += 4 * stride) {
+        float vv[4], gg[4], uu[4], hw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < n2) {
+                const bool isx = i < m;
+                hw[k] = isx ? b.w[i] : b.h[i - m];
+                vv[k] = V[i];
+                gg[k] = G[i];
+                uu[k] = U[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < n2) {
+                const bool isx = i < m;
+                float half = __fmul_rn(0.5f, hw[k]);
+                float lo = __fadd_rn(isx ? gr.x0 : gr.y0, half), hi = __fsub_rn(isx ? x1 : y1, half);
+                float un = fminf(hi, fmaxf(lo, vv[k] - alpha * gg[k]));
+                step = fmaxf(step, fabsf(un - vv[k]));
+                uphill = df_add(uphill, gg[k] * (un - uu[k]));
+                float vn = fminf(hi, fmaxf(lo, un + beta * (un - uu[k])));
+                b.vprev[i] = vv[k];
+                b.gprev[i] = gg[k];
+                b.u[i] = un;
+                b.v[i] = vn;
+            }
+        }
     }
     block_max(step, b.acc, ACC_STEPMAX);
-    // g_k . (u_{k+1} - u_k) for the adaptive restart (ctrl_record)
-    reduce2(uphill, 0.0f, b.acc, ACC_GD, -1, b.dr);
+    reduce2(df_val(uphill), 0.0f, b.acc, ACC_GD, -1, b.dr);
     if (last_cta(b.counters + 2) && threadIdx.x == 0) ctrl_record(b.ctrl, b.acc, b.recs);
 }
 
@@ -113,42 +175,79 @@ k_loop_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
 
 // g = gW + lambda gN; sums |g|^2 and g . g_prev, max |g|; last CTA: beta,
 // f_k and the values recorded for iteration k.
-__global__ void __launch_bounds__(kCellThreads) k_cg_g(int m2, LoopBufs b) {
+__global__ void __launch_bounds__(kCellThreads, kVecBlocksPerSm) k_cg_g(int m2, LoopBufs b) {
     const float* cf = ctrl_f(b.ctrl);
     if (cf[F_DONE] != 0.0f) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float lam = cf[F_LAMBDA];
     const bool first = cf[F_FIRST] != 0.0f;
-    float sq = 0.0f, gp = 0.0f, gi = 0.0f;
-    if (i < m2) {
-        float gg = fmaf(lam, b.gN[i], b.gW[i]);
-        b.g[i] = gg;
-        sq = gg * gg;
-        gp = first ? 0.0f : gg * b.gprev[i];
-        gi = fabsf(gg);
+    dfloat sq = df_zero(), gp = df_zero();
+    float gi = 0.0f;
+    const int stride = gridDim.x * blockDim.x;
+    const float* __restrict__ GN = b.gN;
+    const float* __restrict__ GW = b.gW;
+    const float* __restrict__ GP = b.gprev;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m2; i0 += 4 * stride) {
+        float gn[4], gw[4], pr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < m2) {
+                gn[k] = GN[i];
+                gw[k] = GW[i];
+                pr[k] = first ? 0.0f : GP[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < m2) {
+                const float gg = fmaf(lam, gn[k], gw[k]);
+                b.g[i] = gg;
+                sq = df_add(sq, gg * gg);
+                if (!first) gp = df_add(gp, gg * pr[k]);
+                gi = fmaxf(gi, fabsf(gg));
+            }
+        }
     }
-    reduce2(sq, gp, b.acc, ACC_DG2, ACC_DV2, b.dr);
+    reduce2(df_val(sq), df_val(gp), b.acc, ACC_DG2, ACC_DV2, b.dr);
     block_max(gi, b.acc, ACC_GINF);
     if (last_cta(b.counters + 3) && threadIdx.x == 0) ctrl_cg_g(b.ctrl, b.acc);
 }
 
 // d = -g + beta d; sum g . d and max |d|; last CTA: restart test, |d|_inf
 // and the slope.
-__global__ void __launch_bounds__(kCellThreads) k_cg_dir(int m2, LoopBufs b) {
+__global__ void __launch_bounds__(kCellThreads, kVecBlocksPerSm) k_cg_dir(int m2, LoopBufs b) {
     const float* cf = ctrl_f(b.ctrl);
     if (cf[F_DONE] != 0.0f) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float beta = cf[F_BETA];
     const bool first = cf[F_FIRST] != 0.0f;
-    float gd = 0.0f, da = 0.0f;
-    if (i < m2) {
-        float gi = b.g[i];
-        float dn = first ? -gi : fmaf(beta, b.vprev[i], -gi);
-        b.vprev[i] = dn;
-        gd = gi * dn;
-        da = fabsf(dn);
+    dfloat gd = df_zero();
+    float da = 0.0f;
+    const int stride = gridDim.x * blockDim.x;
+    const float* __restrict__ G = b.g;
+    const float* __restrict__ D = b.vprev;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m2; i0 += 4 * stride) {
+        float g[4], d[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < m2) {
+                g[k] = G[i];
+                d[k] = first ? 0.0f : D[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < m2) {
+                const float dn = first ? -g[k] : fmaf(beta, d[k], -g[k]);
+                b.vprev[i] = dn;
+                gd = df_add(gd, g[k] * dn);
+                da = fmaxf(da, fabsf(dn));
+            }
+        }
     }
-    reduce2(gd, 0.0f, b.acc, ACC_GD, -1, b.dr);
+    reduce2(df_val(gd), 0.0f, b.acc, ACC_GD, -1, b.dr);
     block_max(da, b.acc, ACC_DINF);
     if (last_cta(b.counters + 4) && threadIdx.x == 0) ctrl_cg_dir(b.ctrl, b.acc);
 }
@@ -186,20 +285,43 @@ __global__ void k_cg_alpha(double* ctrl, const double* acc) {
 
 // u = v = clamp(u + a_k dir / |d|_inf); d = dir; g_prev = g.  Last CTA:
 // record and advance.
-__global__ void __launch_bounds__(kCellThreads)
+__global__ void __launch_bounds__(kCellThreads, kVecBlocksPerSm)
 k_cg_update(int m, Grid gr, float x1, float y1, LoopBufs b) {
     const float* cf = ctrl_f(b.ctrl);
     if (cf[F_DONE] != 0.0f) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 2 * m) {
-        const float scale = cf[F_SCALE_UPDATE];
-        float dir, lo, hi;
-        cg_coord(i, m, gr, x1, y1, b, dir, lo, hi);
-        const float un = fminf(hi, fmaxf(lo, fmaf(scale, dir, b.u[i])));
-        b.u[i] = un;
-        b.v[i] = un;
-        b.vprev[i] = dir;
-        b.gprev[i] = b.g[i];
+    const float scale = cf[F_SCALE_UPDATE];
+    const bool restart = cf[F_RESTART] != 0.0f;
+    const int stride = gridDim.x * blockDim.x, n2 = 2 * m;
+    const float* __restrict__ G = b.g;
+    const float* __restrict__ D = b.vprev;
+    const float* __restrict__ U = b.u;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n2; i0 += 4 * stride) {
+        float g[4], dir[4], u[4], hw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < n2) {
+                hw[k] = i < m ? b.w[i] : b.h[i - m];
+                g[k] = G[i];
+                dir[k] = restart ? -g[k] : D[i];
+                u[k] = U[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * stride;
+            if (i < n2) {
+                const bool isx = i < m;
+                const float half = __fmul_rn(0.5f, hw[k]);
+                const float lo = __fadd_rn(isx ? gr.x0 : gr.y0, half);
+                const float hi = __fsub_rn(isx ? x1 : y1, half);
+                const float un = fminf(hi, fmaxf(lo, fmaf(scale, dir[k], u[k])));
+                b.u[i] = un;
+                b.v[i] = un;
+                b.vprev[i] = dir[k];
+                b.gprev[i] = g[k];
+            }
+        }
     }
     if (last_cta(b.counters + 5) && threadIdx.x == 0) ctrl_record_cg(b.ctrl, b.recs);
 }
@@ -231,6 +353,11 @@ __global__ void k_gamma0(double* ctrl, const double* acc) {
 
 static inline int nblk(long long m, int t) { return (int)((m + t - 1) / t); }
 
+// blocks of a vector kernel over n coordinates (grid-stride)
+static inline int vec_blocks(const Ctx& c, long long n) {
+    return std::max(1, std::min(nblk(n, kCellThreads), c.num_sms * kVecBlocksPerSm));
+}
+
 LoopBufs loop_bufs(Ctx& c) {
     LoopBufs b;
     b.u = c.u; b.v = c.v; b.vprev = c.vprev; b.g = c.g; b.gprev = c.gprev;
@@ -250,18 +377,19 @@ cudaError_t launch_loop_cells(Ctx& c, cudaStream_t s) {
     else
         k_loop_cells<false><<<nb, kCellThreads, 0, s>>>(c.grid, c.m_mov, b, c.E2, c.cell_rank,
                                                         nullptr, nullptr, c.gW2);
-    c.launches++;
+    k_ctrl_lambda<<<1, 1, 0, s>>>(c.ctrl, c.acc);
+    c.launches += 2;
     return cudaGetLastError();
 }
 
 cudaError_t launch_loop_g(Ctx& c, cudaStream_t s) {
-    k_loop_g<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
+    k_loop_g<<<vec_blocks(c, 2LL * c.m_mov), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
     c.launches++;
     return cudaGetLastError();
 }
 
 cudaError_t launch_loop_update(Ctx& c, cudaStream_t s) {
-    k_loop_update<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
+    k_loop_update<<<vec_blocks(c, 2LL * c.m_mov), kCellThreads, 0, s>>>(
         c.m_mov, c.grid, (float)c.x1, (float)c.y1, loop_bufs(c));
     c.launches++;
     return cudaGetLastError();
@@ -275,13 +403,13 @@ cudaError_t launch_place_init(Ctx& c, const float* x0, const float* y0, cudaStre
 }
 
 cudaError_t launch_cg_g(Ctx& c, cudaStream_t s) {
-    k_cg_g<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
+    k_cg_g<<<vec_blocks(c, 2LL * c.m_mov), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
     c.launches++;
     return cudaGetLastError();
 }
 
 cudaError_t launch_cg_dir(Ctx& c, cudaStream_t s) {
-    k_cg_dir<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
+    k_cg_dir<<<vec_blocks(c, 2LL * c.m_mov), kCellThreads, 0, s>>>(2 * c.m_mov, loop_bufs(c));
     c.launches++;
     return cudaGetLastError();
 }
@@ -300,7 +428,7 @@ cudaError_t launch_cg_alpha(Ctx& c, cudaStream_t s) {
 }
 
 cudaError_t launch_cg_update(Ctx& c, cudaStream_t s) {
-    k_cg_update<<<nblk(2LL * c.m_mov, kCellThreads), kCellThreads, 0, s>>>(
+    k_cg_update<<<vec_blocks(c, 2LL * c.m_mov), kCellThreads, 0, s>>>(
         c.m_mov, c.grid, (float)c.x1, (float)c.y1, loop_bufs(c));
     c.launches++;
     return cudaGetLastError();

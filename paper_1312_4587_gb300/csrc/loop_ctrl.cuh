@@ -60,19 +60,26 @@ __host__ __device__ inline void ctrl_mirror(double* ctrl) {
 constexpr int kRecFields = 8;
 constexpr int kCounters = 4;   // one ticket counter per loop kernel kind
 
-// All threads fence their atomics, then thread 0 takes a ticket; the CTA that
-// draws the last ticket resets the counter and returns true.
+// After a block barrier (which orders every thread's earlier reductions
+// before thread 0's next operations), thread 0 fences at device scope and
+// takes a ticket; the CTA that draws the last ticket resets the counter,
+// fences again (its later reads see every CTA's reductions) and returns
+// true.  One fence per block: a fence in every thread held each thread
+// until its own stores had completed, which doubled the loop's vector
+// kernels.
 __device__ __forceinline__ bool last_cta(unsigned int* counter) {
     __shared__ bool is_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         unsigned int t = atomicAdd(counter, 1u);
         is_last = (t == gridDim.x - 1);
-        if (is_last) *counter = 0u;
+        if (is_last) {
+            *counter = 0u;
+            __threadfence();
+        }
     }
     __syncthreads();
-    if (is_last) __threadfence();
     return is_last;
 }
 
