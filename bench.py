@@ -56,13 +56,13 @@ STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "ce
 # source it was taken from is unchanged: key = first 16 hex digits of the
 # SHA-256 of the kernel file followed by fftpl_internal.cuh.
 STAGE_TRAFFIC = {
-    "scatter": ("k_density.cu", "4c14c008544e7a94", 50785280 + 617984),
-    "rows_fwd": ("k_spectral.cu", "2b363b92fb434061", 33648640 + 26368),
-    "cols": ("k_spectral.cu", "2b363b92fb434061", 17366272 + 496128),
-    "rows_inv": ("k_spectral.cu", "2b363b92fb434061", 33613824 + 412928),
-    # k_wa and k_wa_big
-    "wa": ("k_wire.cu", "f43e1c29439a9042", 103016704 + 3927552 + 65446912 + 525312),
-    "cells": ("k_wire.cu", "f43e1c29439a9042", 76428032 + 13393408),
+    "scatter": ("k_density.cu", "38eb409da2ddd197", 50765312 + 579328),
+    "rows_fwd": ("k_spectral.cu", "d4820b8b5c4d125c", 33647360 + 12800),
+    "cols": ("k_spectral.cu", "d4820b8b5c4d125c", 17127424 + 252160),
+    "rows_inv": ("k_spectral.cu", "d4820b8b5c4d125c", 33614080 + 557056),
+    # k_wa and k_wa_grp
+    "wa": ("k_wire.cu", "2aa8c0c677d0b1d1", 103031808 + 3973632 + 70471936 + 944128),
+    "cells": ("k_wire.cu", "2aa8c0c677d0b1d1", 76417280 + 14675968),
 }
 
 
