@@ -500,6 +500,15 @@ fftpl_status fftpl_debug_tc_gemm(const void* a_hi, const void* a_lo, const void*
                                  const void* b_lo, int32_t M, int32_t N, int32_t K, float* d,
                                  int32_t nsplit, int32_t no_loads, int32_t* err, void* stream);
 
+/* Selects how the transform path's row and column passes write their
+ * transposed outputs: tma != 0 through the tensor-memory-access unit (the
+ * default, when the driver could encode the tensor maps at create), 0 with
+ * plain per-thread stores.  Both write the same values; the captured
+ * graphs of the handle are dropped so that the next call takes the choice.
+ * Returns FFTPL_EINVAL for a null handle, FFTPL_ESTATE if tma != 0 was asked
+ * for and the tensor maps are not available. */
+fftpl_status fftpl_debug_transpose_stores(fftpl_t h, int32_t tma);
+
 #ifdef __cplusplus
 }
 #endif

@@ -498,6 +498,23 @@ fftpl_status fftpl_fillers(const fftpl_region* R, const fftpl_cells* cells,
 
 void fftpl_debug_fail_alloc_after(int32_t k) { g_fail_after.store(k > 0 ? k : 0); }
 
+fftpl_status fftpl_debug_transpose_stores(fftpl_t h, int32_t tma) {
+    if (!h) return FFTPL_EINVAL;
+    Ctx& c = *h;
+    if (tma && !c.spec_maps_ok) return set_err(c, FFTPL_ESTATE, "tensor maps not available");
+    CK(cudaStreamSynchronize(c.stream));
+    if (c.eval_graph) {
+        cudaGraphExecDestroy(c.eval_graph);
+        c.eval_graph = nullptr;
+    }
+    if (c.loop_graph) {
+        cudaGraphExecDestroy(c.loop_graph);
+        c.loop_graph = nullptr;
+    }
+    c.spec_tma = tma != 0;
+    return FFTPL_OK;
+}
+
 fftpl_status fftpl_debug_tc_gemm(const void* a_hi, const void* a_lo, const void* b_hi,
                                  const void* b_lo, int32_t M, int32_t N, int32_t K, float* d,
                                  int32_t nsplit, int32_t no_loads, int32_t* err, void* stream) {

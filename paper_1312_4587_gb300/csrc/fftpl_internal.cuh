@@ -415,7 +415,8 @@ struct Ctx {
     // 256 rows (n if smaller): the transposed tiles of the row and column
     // passes leave shared memory through the tensor-memory-access unit
     CUtensorMap map_t1{}, map_pt{}, map_rt{};
-    bool spec_tma = false;
+    bool spec_tma = false;      // the transposed stores go through the maps
+    bool spec_maps_ok = false;  // the maps could be encoded
     float *psi = nullptr, *ex = nullptr, *ey = nullptr, *rho = nullptr;
     float2* E2 = nullptr;       // interleaved field (E_x, E_y) [n][n]
     float2 *tw = nullptr, *ph = nullptr;

@@ -1051,10 +1051,11 @@ static cudaError_t dispatch(Ctx& c, int which, cudaStream_t s) {
 
 void spec_maps_init(Ctx& c) {
     const int n = c.n, box = n < 256 ? n : 256;
-    c.spec_tma = c.T1 && c.PT && c.RT && n >= 16 &&
-                 make_map_f32(&c.map_t1, c.T1, n, n, 8, box) &&
-                 make_map_f32(&c.map_pt, c.PT, n, n, 4, box) &&
-                 make_map_f32(&c.map_rt, c.RT, n, n, 4, box);
+    c.spec_maps_ok = c.T1 && c.PT && c.RT && n >= 16 &&
+                     make_map_f32(&c.map_t1, c.T1, n, n, 8, box) &&
+                     make_map_f32(&c.map_pt, c.PT, n, n, 4, box) &&
+                     make_map_f32(&c.map_rt, c.RT, n, n, 4, box);
+    c.spec_tma = c.spec_maps_ok;
 }
 
 cudaError_t launch_rows_fwd(Ctx& c, cudaStream_t s) { return dispatch(c, 0, s); }

@@ -157,6 +157,7 @@ def lib():
             "fftpl_stage_times": (S, [_H, _P, _P, C.c_int32]),
             "fftpl_launch_count": (C.c_int64, [_H]),
             "fftpl_debug_fail_alloc_after": (None, [C.c_int32]),
+            "fftpl_debug_transpose_stores": (S, [_H, C.c_int32]),
             "fftpl_fillers": (S, [_P, _P, C.c_double, _P, _P, _P]),
             "fftpl_debug_tc_gemm": (S, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P,
                                         C.c_int32, C.c_int32, _P, _P]),
@@ -511,6 +512,10 @@ def fftpl_fillers(region, w, h, m_mov, fix_x=None, fix_y=None, target_density=1.
 
 def fftpl_debug_fail_alloc_after(k):
     lib().fftpl_debug_fail_alloc_after(C.c_int32(int(k)))
+
+
+def fftpl_debug_transpose_stores(h, tma):
+    _check(lib().fftpl_debug_transpose_stores(h, C.c_int32(1 if tma else 0)), h)
 
 
 def fftpl_debug_tc_gemm(a_hi, a_lo, b_hi, b_lo, d, err, nsplit=3, no_loads=0, stream=None):

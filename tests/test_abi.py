@@ -103,6 +103,7 @@ def test_null_handle_calls_are_safe(F):
     assert F.fftpl_launch_count(None) == 0
     assert F.fftpl_device_bytes(None) == 0
     assert F.lib().fftpl_check(None) == F.FFTPL_EINVAL
+    assert F.lib().fftpl_debug_transpose_stores(None, 1) == F.FFTPL_EINVAL
 
 
 def test_tensor_core_path_validation(F):
