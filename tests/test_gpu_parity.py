@@ -216,11 +216,13 @@ def test_wa_alone(F):
                    np.concatenate([ref["gcx"], ref["gcy"]])) < TOL_MAP
 
 
-def degree_instance(seed=11):
-    """Nets of every degree at the boundaries of the WA kernel's bodies (2..6
-    in registers, 7..64 in the shared-memory kernel, above 64 the
-    runtime-degree path), 70 nets of each (several slabs, one ragged), with
-    pins on fixed cells and non-zero offsets."""
+def degree_instance(seed=11, degrees=(2, 3, 4, 5, 6, 7, 8, 9, 12, 13, 16, 17, 24, 25, 32, 33, 48,
+                                       49, 63, 64, 65, 100, 300)):
+    """Nets of every degree at the boundaries of the WA kernels' bodies (2..6
+    one lane per net with the pins in registers; 7..64 several lanes per net,
+    at each change of the lane count (2, 4, 8, 16) and of the pins per lane
+    (2..4); above 64 the runtime-degree path), 70 nets of each (several
+    slabs, one ragged), with pins on fixed cells and non-zero offsets."""
     rng = np.random.default_rng(seed)
     base = synth.make_instance("tiny")
     m, nf = base.m_mov, 5
@@ -231,7 +233,7 @@ def degree_instance(seed=11):
     base.w = np.concatenate([base.w[:m], np.full(nf, 2.0, np.float32)])
     base.h = np.concatenate([base.h[:m], np.full(nf, 2.0, np.float32)])
     net_ptr, pc = [0], []
-    for d in [2, 3, 5, 6, 7, 8, 33, 63, 64, 65, 100, 300]:
+    for d in degrees:
         for _ in range(70):
             cells = rng.choice(m + nf, d, replace=False)
             pc += list(cells); net_ptr.append(len(pc))
@@ -265,6 +267,28 @@ def test_wa_degree_boundaries(F, det, model):
     assert rel(np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()]), want) < TOL_MAP
     assert abs(rep2["W"] - ref["W"]) / ref["W"] < 1e-6
     assert rel(np.concatenate([g[2].cpu().numpy(), g[3].cpu().numpy()]), want) < TOL_MAP
+
+
+@pytest.mark.parametrize("model", ["wa", "lse"])
+@pytest.mark.parametrize("d", [7, 8, 9, 12, 13, 16, 17, 24, 25, 32, 33, 48, 49, 64])
+def test_wa_grouped_degree(F, d, model):
+    """One degree at a time through the several-lanes-per-net kernel: each
+    lane count (2, 4, 8, 16) with its fewest and most pins per lane."""
+    import torch
+    inst = degree_instance(seed=100 + d, degrees=(d,))
+    wl = oracle.WL_WA if model == "wa" else oracle.WL_LSE
+    ref = oracle.wa(inst.net_ptr, inst.pin_cell, inst.pin_dx, inst.pin_dy, inst.m_mov,
+                    inst.x, inst.y, inst.gamma, inst.fix_x, inst.fix_y, model=wl)
+    opts = dict(wirelength=F.FFTPL_WL_WA if model == "wa" else F.FFTPL_WL_LSE)
+    with F.Problem(inst, **opts) as p:
+        gx = torch.empty(inst.m_mov, device="cuda"); gy = torch.empty_like(gx)
+        W = F.fftpl_wa(p.h, cuda(inst.x), cuda(inst.y), inst.gamma, gx, gy)
+        rep = F.fftpl_report(p.h)
+        F.fftpl_check(p.h)
+    assert abs(W - ref["W"]) / ref["W"] < 1e-6
+    assert abs(rep["hpwl"] - ref["hpwl"]) / ref["hpwl"] < 1e-6
+    want = np.concatenate([ref["gcx"], ref["gcy"]])
+    assert rel(np.concatenate([gx.cpu().numpy(), gy.cpu().numpy()]), want) < TOL_MAP
 
 
 def test_adjoint_parity(F):
