@@ -650,13 +650,7 @@ static fftpl_status build_slabs(Ctx& c, const fftpl_nets* nets, const fftpl_pins
     // after them in the same order (k_wa); the slot layout is unchanged
     auto is_big = [](const int4& sl) { return sl.y >= kBigMin && sl.y <= kBigMax; };
     std::stable_partition(slabs.begin(), slabs.end(), is_big);
-    c.nbig = 0;
-    c.big_dmax = 0;
-    for (const int4& sl : slabs)
-        if (is_big(sl)) {
-            c.nbig++;
-            c.big_dmax = std::max(c.big_dmax, sl.y);
-        }
+    c.nbig = (int)std::count_if(slabs.begin(), slabs.end(), is_big);
     // cell-ordered slots (by internal cell number) for the deterministic
     // reduction
     std::vector<int32_t> cslot;

@@ -40,7 +40,6 @@ constexpr int kBigMax = 64;
 __host__ __device__ constexpr int grp_lanes(int d) {
     return d <= 8 ? 2 : (d <= 16 ? 4 : (d <= 32 ? 8 : 16));
 }
-constexpr int kWaPinCap = 2048;     // pins staged in shared memory per WA CTA
 
 // accumulator slots (FP64 sums written by the kernels)
 enum {
@@ -425,7 +424,6 @@ struct Ctx {
                                 // net per lane)}
     int nslabs = 0;
     int nbig = 0;               // the first nbig slabs: degree kBigMin..kBigMax (k_wa_grp)
-    int big_dmax = 0;           // their largest degree
     int num_sms = 1;            // of the handle's device
     int64_t slab_slots = 0;
     int32_t *pin_cell = nullptr, *pin_slot = nullptr, *cell_pin_ptr = nullptr;
