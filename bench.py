@@ -56,13 +56,13 @@ STAGE_IDS = {"scatter": 0, "rows_fwd": 1, "cols": 2, "rows_inv": 3, "wa": 4, "ce
 # source it was taken from is unchanged: key = first 16 hex digits of the
 # SHA-256 of the kernel file followed by fftpl_internal.cuh.
 STAGE_TRAFFIC = {
-    "scatter": ("k_density.cu", "38eb409da2ddd197", 50765312 + 579328),
-    "rows_fwd": ("k_spectral.cu", "d4820b8b5c4d125c", 33647360 + 12800),
-    "cols": ("k_spectral.cu", "d4820b8b5c4d125c", 17127424 + 252160),
-    "rows_inv": ("k_spectral.cu", "d4820b8b5c4d125c", 33614080 + 557056),
+    "scatter": ("k_density.cu", "fd2949651050cefb", 50778624 + 627968),
+    "rows_fwd": ("k_spectral.cu", "a85e897b6059aa28", 33647616 + 16384),
+    "cols": ("k_spectral.cu", "a85e897b6059aa28", 17206528 + 331520),
+    "rows_inv": ("k_spectral.cu", "a85e897b6059aa28", 33614080 + 526336),
     # k_wa and k_wa_grp
-    "wa": ("k_wire.cu", "2aa8c0c677d0b1d1", 103031808 + 3973632 + 70471936 + 944128),
-    "cells": ("k_wire.cu", "2aa8c0c677d0b1d1", 76417280 + 14675968),
+    "wa": ("k_wire.cu", "a06baad7461894fc", 103047680 + 4505856 + 70472448 + 968704),
+    "cells": ("k_wire.cu", "a06baad7461894fc", 76424960 + 14908672),
 }
 
 
