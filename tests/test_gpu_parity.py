@@ -200,6 +200,33 @@ def test_deterministic_map_bit_exact(F):
     assert np.array_equal(got, ref)
 
 
+def test_deterministic_repeatable(F):
+    """Deterministic mode, an instance with nets of degree 2..50 (both WA
+    kernels): two evaluations give bit-identical outputs, and so do two
+    20-iteration placement runs from the same start on separate handles."""
+    import torch
+    inst = synth.make_instance("medium")
+    x, y = cuda(inst.x), cuda(inst.y)
+    outs, pos = [], []
+    for _ in range(2):
+        with F.Problem(inst, deterministic=1) as p:
+            g = [torch.empty_like(x) for _ in range(4)]
+            rep = F.fftpl_eval(p.h, x, y, inst.gamma, *g)
+            outs.append((rep, [t.cpu().numpy() for t in g]))
+            F.fftpl_place_init(p.h, x, y)
+            F.fftpl_step(p.h, 20)
+            px, py = torch.empty_like(x), torch.empty_like(y)
+            F.fftpl_place_positions(p.h, px, py)
+            F.fftpl_check(p.h)
+            pos.append((px.cpu().numpy(), py.cpu().numpy()))
+    (r0, g0), (r1, g1) = outs
+    for k in ("N", "W", "hpwl", "tau"):
+        assert r0[k] == r1[k], k
+    for a, b in zip(g0, g1):
+        assert np.array_equal(a, b)
+    assert np.array_equal(pos[0][0], pos[1][0]) and np.array_equal(pos[0][1], pos[1][1])
+
+
 def test_wa_alone(F):
     import torch
     inst = synth.make_instance("medium")
